@@ -1,0 +1,236 @@
+"""Seeded synthetic workloads: bathymetry, initial states and gauge positions.
+
+This module holds initial data only (closed-form solitary waves, Gaussians,
+synthetic bathymetries); none of the solver's arithmetic.  It is the one module
+that both the CUDA path's tests/benchmarks and the CPU oracle's tests draw their
+inputs from.
+
+State layout everywhere: float64 array of shape (nvar, ny, nx), fields
+eta, hu, hv [, hw] [, h sigma], hp [, h p_b]; eta = h + b relative to the still
+level eta0 = 0.  Bathymetry b is negative under water.
+"""
+import math
+
+import numpy as np
+
+SWE, MBHSGN, HSGN = 0, 1, 2
+NVAR = {SWE: 3, MBHSGN: 5, HSGN: 7}
+G = 9.81
+
+
+def field_index(model):
+    """Field positions of the auxiliary variables for a model (None if absent)."""
+    if model == MBHSGN:
+        return dict(hw=3, hs=None, hp=4, hpb=None)
+    if model == HSGN:
+        return dict(hw=3, hs=4, hp=5, hpb=6)
+    return dict(hw=None, hs=None, hp=None, hpb=None)
+
+
+def cell_centres(nx, ny, dx, dy, x0=0.0, y0=0.0):
+    x = x0 + (np.arange(nx) + 0.5) * dx
+    y = y0 + (np.arange(ny) + 0.5) * dy
+    return np.meshgrid(x, y)
+
+
+def rest_state(b, model):
+    """Lake at rest: eta = max(0, b), everything else zero."""
+    q = np.zeros((NVAR[model],) + b.shape)
+    q[0] = np.maximum(0.0, b)
+    return q
+
+
+# --------------------------------------------------------------------------
+# App. B: solitary wave of SGN (flat bottom, depth H).  The printed pressure has
+# prefactor 1/2 and ((2H-h) sech')^2; the form used here, 2/3 * ... *
+# [(2H-h) sech'^2 + h sech sech''], is the one that satisfies the travelling-wave
+# momentum balance of SGN (checked symbolically).  Over a flat bottom the SGN
+# constraints give sigma = 2w and the bottom pressure p_b = 3p/2.
+def sgn_soliton(xi_coord, t, a, H, x0, nu=1.0, g=G):
+    ell = math.sqrt((H ** 3 / a + H ** 2) * 4.0 / 3.0)
+    c0 = nu * math.sqrt(0.75) * ell / H * math.sqrt(g * H ** 3 / (0.75 * ell ** 2 - H ** 2))
+    xi = (xi_coord - c0 * t - x0) / ell
+    sech = 1.0 / np.cosh(xi)
+    tanh = np.tanh(xi)
+    d1 = -sech * tanh                       # sech'
+    d2 = sech * tanh ** 2 - sech ** 3       # sech''
+    h = H + a * sech ** 2
+    u = c0 * (1.0 - H / h)
+    w = -a * c0 * H / (ell * h) * sech * d1
+    p = (2.0 / 3.0) * a * c0 ** 2 * H ** 2 / (ell ** 2 * h ** 2) * ((2.0 * H - h) * d1 ** 2 + h * sech * d2)
+    return dict(h=h, u=u, w=w, p=p, sigma=2.0 * w, pb=1.5 * p, ell=ell, c0=c0)
+
+
+def soliton_state(model, x, y, b, a, H, x0, direction=0, nu=1.0, t=0.0):
+    """Planar SGN soliton on depth H travelling along x (direction 0) or y (1)."""
+    coord = x if direction == 0 else y
+    s = sgn_soliton(coord, t, a, H, x0, nu)
+    q = np.zeros((NVAR[model],) + x.shape)
+    h = s["h"]
+    q[0] = h + b
+    q[1 + direction] = h * s["u"]
+    fi = field_index(model)
+    if fi["hw"] is not None:
+        q[fi["hw"]] = h * s["w"]
+        q[fi["hp"]] = h * s["p"]
+    if fi["hs"] is not None:
+        q[fi["hs"]] = h * s["sigma"]
+        q[fi["hpb"]] = h * s["pb"]
+    return q
+
+
+def apply_surface(b, bump):
+    """Add a surface perturbation over the ocean (b < 0) keeping h >= 0 (eta >= b);
+    land keeps eta = b."""
+    eta = np.where(b < 0.0, np.maximum(bump, b), b)
+    return eta
+
+
+# --------------------------------------------------------------------------
+# Config 1: 256 x 256, dx = 0.05 m, flat bottom depth 1 m, planar SGN soliton
+# a = 0.1 m at x0 = 4.8 m travelling in +x, reflective walls, CFL 0.9, 200 steps.
+def config1(model=HSGN, nx=256, ny=256, dx=0.05, a=0.1, H=1.0, x0=4.8):
+    x, y = cell_centres(nx, ny, dx, dx)
+    b = np.full((ny, nx), -H)
+    q = soliton_state(model, x, y, b, a, H, x0)
+    return dict(b=b, q=q, dx=dx, dy=dx, x0=0.0, y0=0.0, bc=(0, 0, 0, 0), model=model,
+                alpha=3.0, h_star=0.0, cfl=0.9, steps=200, dry_tol=1e-3, gauges=None)
+
+
+# --------------------------------------------------------------------------
+# Config 2: 4096 x 4096, dx = 10 m.  b = -200 m for x < 26 km, then a 1:50 beach
+# (shoreline at 36 km, dry land up to +99 m), plus a Gaussian seamount of height
+# 100 m and radius 500 m (centre seeded, seed 2001).  Initial surface: Gaussian
+# depression of -5 m, radius 1 km (centre seeded on the slope, seed 2002).
+# Extrapolation boundaries, h* = 20 m, 1000 steps, 64 gauges within 3 km of the
+# source (seed 2003).
+def config2_bathymetry(nx=4096, ny=4096, dx=10.0, seamount=None):
+    x, y = cell_centres(nx, ny, dx, dx)
+    L = nx * dx
+    scale = L / 40960.0
+    xs = 26000.0 * scale
+    b = np.where(x < xs, -200.0, -200.0 + (x - xs) / 50.0)
+    if seamount is None:
+        rng = np.random.default_rng(2001)
+        seamount = (rng.uniform(5000, 20000) * scale, rng.uniform(5000, 36000) * scale)
+    r2 = (x - seamount[0]) ** 2 + (y - seamount[1]) ** 2
+    b = b + 100.0 * np.exp(-r2 / 500.0 ** 2)
+    return b, x, y
+
+
+def config2(model=HSGN, nx=4096, ny=4096, dx=10.0, ngauges=64):
+    b, x, y = config2_bathymetry(nx, ny, dx)
+    L = nx * dx
+    scale = L / 40960.0
+    rng = np.random.default_rng(2002)
+    cx, cy = rng.uniform(33500, 35000) * scale, rng.uniform(8000, 33000) * scale
+    r2 = (x - cx) ** 2 + (y - cy) ** 2
+    q = np.zeros((NVAR[model], ny, nx))
+    q[0] = apply_surface(b, -5.0 * np.exp(-r2 / 1000.0 ** 2))
+    grng = np.random.default_rng(2003)
+    wet = (q[0] - b) > 1.0
+    near = wet & (r2 < 3000.0 ** 2)
+    jj, ii = np.nonzero(near)
+    pick = grng.choice(len(ii), size=min(ngauges, len(ii)), replace=False)
+    gxy = np.stack([x[jj[pick], ii[pick]], y[jj[pick], ii[pick]]], axis=1)
+    return dict(b=b, q=q, dx=dx, dy=dx, x0=0.0, y0=0.0, bc=(1, 1, 1, 1), model=model,
+                alpha=3.0, h_star=20.0, cfl=0.9, steps=1000, dry_tol=1e-3, gauges=gxy,
+                source=(cx, cy))
+
+
+# --------------------------------------------------------------------------
+# Config 3: 8192 x 8192, dx = 500 m, fractal bathymetry: isotropic Gaussian
+# random field with power spectrum |k|^-2 (seed 3001), mapped so that the 80th
+# percentile is 0 (about 20 % land) and the minimum is -6000 m, land capped at
+# +500 m; Gaussian uplift 2 m, radius 30 km at a cell deeper than 3000 m (seed
+# 3002); h* = 20 m, extrapolation boundaries, 2000 steps, 64 gauges (seed 3003).
+def fractal_bathymetry(n, seed, depth=6000.0, land_frac=0.2, land_cap=500.0):
+    rng = np.random.default_rng(seed)
+    kx = np.fft.fftfreq(n)
+    k = np.sqrt(kx[None, :] ** 2 + kx[:, None] ** 2)
+    k[0, 0] = 1.0
+    amp = 1.0 / k
+    amp[0, 0] = 0.0
+    spec = amp * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    f = np.real(np.fft.ifft2(spec))
+    q80 = np.quantile(f, 1.0 - land_frac)
+    fmin = f.min()
+    b = (f - q80) / (q80 - fmin) * depth
+    return np.minimum(b, land_cap)
+
+
+def config3(model=HSGN, n=8192, dx=500.0, ngauges=64, crop=None):
+    b = fractal_bathymetry(n, 3001)
+    x, y = cell_centres(n, n, dx, dx)
+    rng = np.random.default_rng(3002)
+    deep = np.argwhere(b < -3000.0)
+    j, i = deep[rng.integers(len(deep))]
+    cx, cy = x[j, i], y[j, i]
+    if crop is not None:
+        # a crop of size crop x crop centred on the source (kept inside the grid)
+        i0 = int(min(max(i - crop // 2, 0), n - crop))
+        j0 = int(min(max(j - crop // 2, 0), n - crop))
+        b = b[j0:j0 + crop, i0:i0 + crop]
+        x = x[j0:j0 + crop, i0:i0 + crop]
+        y = y[j0:j0 + crop, i0:i0 + crop]
+        xo, yo = i0 * dx, j0 * dx
+    else:
+        xo, yo = 0.0, 0.0
+    r2 = (x - cx) ** 2 + (y - cy) ** 2
+    q = np.zeros((NVAR[model],) + b.shape)
+    q[0] = apply_surface(b, 2.0 * np.exp(-r2 / 30000.0 ** 2))
+    grng = np.random.default_rng(3003)
+    jj, ii = np.nonzero((q[0] - b) > 1.0)
+    pick = grng.choice(len(ii), size=min(ngauges, len(ii)), replace=False)
+    gxy = np.stack([x[jj[pick], ii[pick]], y[jj[pick], ii[pick]]], axis=1)
+    return dict(b=b, q=q, dx=dx, dy=dx, x0=xo, y0=yo, bc=(1, 1, 1, 1), model=model,
+                alpha=3.0, h_star=20.0, cfl=0.9, steps=2000, dry_tol=1e-3, gauges=gxy,
+                source=(cx, cy))
+
+
+# --------------------------------------------------------------------------
+# Small seeded cases used by the parity tests.
+def smooth_random_bathymetry(nx, ny, seed, lo=-2.0, hi=0.6, modes=4):
+    """Smooth random bathymetry crossing the still level (wet/dry shoreline)."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+    f = np.zeros_like(X)
+    for _ in range(modes):
+        kx, ky = rng.integers(1, 4, size=2)
+        ph = rng.uniform(0, 2 * np.pi, size=2)
+        f += rng.uniform(0.3, 1.0) * np.cos(np.pi * kx * X + ph[0]) * np.cos(np.pi * ky * Y + ph[1])
+    f = (f - f.min()) / (f.max() - f.min() + 1e-300)
+    return lo + (hi - lo) * f
+
+
+def gaussian_hump_state(model, b, x, y, xc, yc, amp, radius):
+    q = np.zeros((NVAR[model],) + b.shape)
+    q[0] = apply_surface(b, amp * np.exp(-((x - xc) ** 2 + (y - yc) ** 2) / radius ** 2))
+    return q
+
+
+def random_small_case(model, nx, ny, seed, dx=0.1, wetdry=True, amp=0.2):
+    """A seeded small case: smooth random bathymetry (crossing the still level when
+    wetdry), a Gaussian hump plus random small velocities and auxiliaries."""
+    rng = np.random.default_rng(seed)
+    x, y = cell_centres(nx, ny, dx, dx)
+    if wetdry:
+        b = smooth_random_bathymetry(nx, ny, seed + 1)
+    else:
+        b = -1.0 - 0.3 * smooth_random_bathymetry(nx, ny, seed + 1, 0.0, 1.0)
+    xc, yc = rng.uniform(0.3, 0.7) * nx * dx, rng.uniform(0.3, 0.7) * ny * dx
+    q = gaussian_hump_state(model, b, x, y, xc, yc, amp, 0.2 * min(nx, ny) * dx)
+    h = q[0] - b
+    wet = h > 1e-3
+    q[1] = np.where(wet, h * rng.uniform(-0.2, 0.2) * np.sin(x), 0.0)
+    q[2] = np.where(wet, h * rng.uniform(-0.2, 0.2) * np.cos(y), 0.0)
+    fi = field_index(model)
+    if fi["hw"] is not None:
+        q[fi["hw"]] = np.where(wet, h * 0.01 * np.sin(2 * x + y), 0.0)
+        q[fi["hp"]] = np.where(wet, h * 0.05 * np.cos(x - 2 * y), 0.0)
+    if fi["hs"] is not None:
+        q[fi["hs"]] = np.where(wet, h * 0.02 * np.cos(x + y), 0.0)
+        q[fi["hpb"]] = np.where(wet, h * 0.03 * np.sin(x * y), 0.0)
+    return b, q
