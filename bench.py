@@ -1,0 +1,392 @@
+"""Benchmark of the explicit hyperbolic-SGN step on one GB300 (or N replicas).
+
+Workload: the second configuration -- 4096 x 4096 cells, dx = 10 m, 1:50 beach
+from 200 m depth to dry land plus a Gaussian seamount, landslide-like Gaussian
+depression (-5 m, radius 1 km), wet/dry shoreline with the SWE switch (h* = 20 m),
+HSGN with alpha = 3, 64 gauges.  A step is one time step of the whole method over
+the grid.  Prints one JSON line (driver contract).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision mixed|fp64] [--model hsgn|mbhsgn] [--nx 4096]
+
+Under torchrun every rank runs an independent replica on its own GPU (the method
+needs no exchange between replicas); rank 0 prints the aggregate.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s and % of HBM roofline; FP64 plain vs mixed/batched/learned"
+UNIT = "cell-updates/s"
+HBM_FALLBACK_GBS = 6800.0
+# FP64 CUDA-core peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (the nominal
+# 1.25 TFLOP/s of the part; 1.19 TFLOP/s measured with a DFMA loop at 1.99 GHz)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 CUDA-core peak: 152 SMs x 128 FFMA/clk/SM x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# FP64 / FP32 flops per cell-update of each kernel (ncu instruction counts on the
+# 1024^2 case: dadd + dmul + 2 dfma, fadd + fmul + 2 ffma; divided by the cells
+# of one launch).  Filled from profiles/; None means not measured.
+FLOPS_PER_CELL = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--model", default="hsgn", choices=["hsgn", "mbhsgn", "swe"])
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64-line", action="store_true")
+    return ap.parse_args()
+
+
+def model_id(name):
+    return {"swe": 0, "mbhsgn": 1, "hsgn": 2}[name]
+
+
+def workload(args):
+    from paper_2606_12162_gb300 import workloads as W
+    m = model_id(args.model)
+    dx = 10.0 * 4096 / args.nx
+    c = W.config2(model=m, nx=args.nx, ny=args.nx, dx=dx)
+    return c
+
+
+def cfg_kwargs(c):
+    return dict(dx=c["dx"], model=c["model"], bc=c["bc"], h_star=c["h_star"], alpha=c["alpha"],
+                cfl=c["cfl"], dry_tol=c["dry_tol"])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    """Max over ranks (the slowest replica sets the time)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# Compulsory bytes per cell-update of each kernel of the step: every plane it
+# reads or writes, once, for element size s, nvar fields nv (the depth plane and
+# the positivity factors are FP64 in both precisions).
+def kernel_bytes(name, nv, s):
+    if name == "k_prep":        # q, b, c2 -> W, P (nv + 1 planes), depth
+        return (nv + 2) * s + (2 * nv + 1) * s + 8
+    if name in ("k_face_x", "k_face_y"):   # W, P, b, c2, psi, depth -> face planes
+        return (2 * nv + 4) * s + 8 + (2 * nv + 9) * s
+    if name in ("k_trans_x", "k_trans_y"):  # other direction's Lv, Rv; Roe data, M -> T
+        return (2 * nv + 9) * s + nv * s
+    if name == "k_theta":       # two mass fluxes, eta, b -> theta
+        return 4 * s + 8
+    if name == "k_update":      # W, 4 face vectors, transverse fluxes, theta, b, c2 -> q
+        return (nv + 4 * (nv - 1) + 2 * nv + 2 + nv) * s + 8
+    return 0
+
+
+def cpu_baseline(args, budget_s=15.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded crop of the
+    same workload (a 384 x 384 window around the source, as many steps as fit)."""
+    from oracle import oracle as O
+    from paper_2606_12162_gb300 import workloads as W
+    c = workload(args)
+    cx, cy = c["source"]
+    n = min(384, args.nx)
+    i0 = int(min(max(cx / c["dx"] - n // 2, 0), args.nx - n))
+    j0 = int(min(max(cy / c["dx"] - n // 2, 0), args.nx - n))
+    sl = (slice(j0, j0 + n), slice(i0, i0 + n))
+    b = c["b"][sl]
+    q = c["q"][(slice(None),) + sl]
+    o = O.Oracle(b, **cfg_kwargs(c))
+    o.set_state(q)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-6)
+    k = max(1, int(budget_s / per))
+    t0 = time.perf_counter()
+    o.step(k)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * n * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%dx%d crop of the 4096^2 workload around the source, %d steps, FP64 oracle" % (n, n, k),
+            "seconds": el}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, on the same workload,
+    metric and unit (a bounded 256 x 256 crop per step)."""
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    c = workload(args)
+    cx, cy = c["source"]
+    n = 256
+    i0 = int(min(max(cx / c["dx"] - n // 2, 0), args.nx - n))
+    j0 = int(min(max(cy / c["dx"] - n // 2, 0), args.nx - n))
+    sl = (slice(j0, j0 + n), slice(i0, i0 + n))
+    o = O.Oracle(c["b"][sl], **cfg_kwargs(c))
+    o.set_state(c["q"][(slice(None),) + sl])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = n * n * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "config2 %dx%d beach+seamount landslide, %s (oracle: %dx%d crop per step)"
+                       % (args.nx, args.nx, args.model.upper(), n, n)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%dx%d crop around the source, %d steps" % (n, n, args.steps)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_path(S, c, args, precision, profile):
+    """Warm-up, then exactly K steps between CUDA events on the solver stream."""
+    import torch
+    s = S.Solver(c["b"], precision=precision, **cfg_kwargs(c))
+    s.set_state(c["q"])
+    s.add_gauges(c["gauges"], args.steps + args.warmup + 8)
+    s.step(args.warmup)
+    if profile:
+        s.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = s.kernel_times() if profile else {}
+    f, dt, cr = s.status()
+    return s, ms, kt, f
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_2606_12162_gb300 import build, sgn as S
+    ws, rank, local = dist_setup()
+    build.build()
+    S.load()
+    c = workload(args)
+    prec = 1 if args.precision == "mixed" else 0
+    nv = S.NVAR[c["model"]]
+    cells = args.nx * args.nx
+    esize = 4 if prec == 1 else 8
+    hbm, hbm_src = peaks()
+
+    clk = ClockSampler(local)
+    barrier(ws)
+    clk.start()
+    s, ms, kt, flags = time_path(S, c, args, prec, profile=True)
+    clocks = clk.stop()
+    ms = reduce_max(ms, ws)
+    value = cells * args.steps * ws / (ms / 1e3)
+    launches = s.launches_per_step() * args.steps
+
+    # dominant kernel and its roofline
+    dom = max(kt.items(), key=lambda kv: kv[1][0]) if kt else None
+    roof = None
+    if dom:
+        name, (kms, kn) = dom
+        per_launch_s = kms / 1e3 / max(kn, 1)
+        fl = FLOPS_PER_CELL.get((args.model, args.precision, name))
+        if fl:
+            peak = FP64_PEAK_TFLOPS if prec == 0 else FP32_PEAK_TFLOPS
+            ach = fl * cells / per_launch_s / 1e12
+            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_source": "derived from SM count x FP64/FP32 FMA rate x max clock"}
+        else:
+            byts = kernel_bytes(name, nv, esize) * cells
+            ach = byts / per_launch_s / 1e9
+            roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "peak_source": hbm_src}
+        roof["launch_ms"] = per_launch_s * 1e3
+        roof["share"] = kms / sum(v[0] for v in kt.values())
+    b_alg = (nv * 2 * esize + esize + 1)
+    step_hbm_frac = value / ws * b_alg / (hbm * 1e9)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        ke = max(1, min(args.steps, 10))
+        hq = torch.from_numpy(np.ascontiguousarray(c["q"])).pin_memory()
+        out = torch.empty_like(hq).pin_memory()
+        s.set_state_ptr(hq.data_ptr())
+        s.step(1)
+        s.get_state_ptr(out.data_ptr(), out.numel())
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            s.set_state_ptr(hq.data_ptr())
+            s.step(1)
+            s.get_state_ptr(out.data_ptr(), out.numel())
+        torch.cuda.synchronize()
+        el = reduce_max(time.perf_counter() - t0, ws)
+        nb = nv * cells * 8
+        e2e = {"value": cells * ke * ws / el, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+               "steps": ke}
+
+    # FP64 plain path beside the mixed one (same workload, fewer steps)
+    extra = None
+    if prec == 1 and not args.no_fp64_line:
+        import copy
+        a2 = copy.copy(args)
+        a2.steps = max(3, min(args.steps, 20))
+        s2, ms2, kt2, f2 = time_path(S, c, a2, 0, profile=True)
+        ms2 = reduce_max(ms2, ws)
+        v2 = cells * a2.steps * ws / (ms2 / 1e3)
+        extra = {"value": v2, "unit": UNIT, "steps": a2.steps, "ms_per_step": ms2 / a2.steps,
+                 "hbm_fraction_step": v2 / ws * (nv * 16 + 9) / (hbm * 1e9),
+                 "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt2.items() if v[1]}}
+        del s2
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": "config2: %dx%d, dx=%.1f m, 1:50 beach + seamount, -5 m landslide "
+                                   "depression, wet/dry + SWE switch (h*=20 m), 64 gauges"
+                                   % (args.nx, args.nx, c["dx"]),
+                       "model": args.model.upper(), "precision": args.precision, "alpha": 3.0,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (state %.0f MB per buffer)" % (nv * cells * esize / 1e6)},
+            "roofline": roof,
+            "hbm_fraction_step": step_hbm_frac,
+            "algorithmic_bytes_per_cell": b_alg,
+            "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt.items() if v[1]},
+            "status_flags": flags,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "fp64": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * sgn.h -- C ABI of the GB300 (sm_103a) explicit finite-volume step for the
+ * hyperbolic Serre-Green-Naghdi systems with the transition to the shallow water
+ * equations near shore.
+ *
+ * The method (paper Sec. 3-4): the state q = (h, hu, hv, ...) of one of
+ *   SWE    (Eq. NSWEs)   3 fields: eta, hu, hv
+ *   mbHSGN (Eq. mbHSGN)  5 fields: eta, hu, hv, hw, hp
+ *   HSGN   (Eq. HSGN)    7 fields: eta, hu, hv, hw, h sigma, hp, h p_b
+ * advances by operator splitting (Sec. 4): a relaxation-source half step
+ * (SDIRK(2,2)), the wave-propagation step (f-wave normal Riemann solver with
+ * Roe averages, Einfeldt speeds, well-balanced bathymetry quadrature with the
+ * sharpness sensor psi, MC/minmod limiters, transverse Riemann solver), a second
+ * source half step, the switch to SWE where phi_T = 0 (Eq. transition_function)
+ * and a CFL time step from the maximum wave speed (Eq. eigenvalue_bound).
+ * The relaxation parameter is c^2 = alpha^2 g H phi_T (Sec. 3.3).
+ *
+ * Conventions for every entry point:
+ *  - Return 0 on success or a negative SGN_E* code; no entry point aborts.
+ *  - Host arrays passed in are copied before the call returns; output arrays
+ *    are caller-owned and must hold the stated number of elements.
+ *  - Device memory belongs to the handle and comes from the allocator given to
+ *    sgn_create (NULL: cudaMalloc/cudaFree).  All work is issued on the stream
+ *    given to sgn_create (NULL: the legacy default stream).
+ *  - Dense field layout ("SoA"): field-major, each field ny*nx doubles, row-major
+ *    with x fastest: q[(k*ny + j)*nx + i].  eta = h + b is the surface elevation
+ *    above the still level 0; b < 0 under water.
+ *  - A handle is not thread-safe; separate handles are independent.
+ *  - Every computation runs in this library's CUDA kernels; there is no CPU path.
+ */
+#ifndef SGN_H
+#define SGN_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define SGN_OK          0
+#define SGN_EINVAL     -1   /* invalid argument (null pointer, size, enum value) */
+#define SGN_ENOMEM     -2   /* the allocator returned NULL */
+#define SGN_ECUDA      -3   /* a CUDA runtime call failed (no device, launch error) */
+#define SGN_ENEGDEPTH  -4   /* a depth below -tolerance appeared (positivity lost) */
+#define SGN_ENONFINITE -5   /* NaN or Inf in the state */
+#define SGN_ECFL       -6   /* a face Courant number above 1 */
+#define SGN_ENONHYP    -7   /* g h + p + c^2 < 0 at a wet cell (loss of hyperbolicity) */
+#define SGN_EALLDRY    -8   /* no wet cell: no time step can be computed */
+#define SGN_ERANGE     -9   /* output buffer too small / gauge outside the grid */
+
+/* status bits reported by sgn_status (set on the device, never cleared by a step) */
+#define SGN_ST_NEGDEPTH   1u
+#define SGN_ST_NONFINITE  2u
+#define SGN_ST_CFL        4u
+#define SGN_ST_NONHYP     8u
+#define SGN_ST_ALLDRY    16u
+#define SGN_ST_GAUGEFULL 32u
+
+typedef enum { SGN_SWE = 0, SGN_MBHSGN = 1, SGN_HSGN = 2 } sgn_model;
+typedef enum { SGN_BC_WALL = 0, SGN_BC_EXTRAP = 1, SGN_BC_PERIODIC = 2 } sgn_bc;
+typedef enum { SGN_FP64 = 0, SGN_MIXED = 1 } sgn_precision;
+typedef enum { SGN_LIM_MINMOD = 0, SGN_LIM_MC = 1, SGN_LIM_NONE = 2 } sgn_limiter;
+
+/* Logically rectangular grid of nx*ny cells of size dx*dy with lower-left corner
+ * (x0, y0); cell (i, j) has centre (x0 + (i+1/2) dx, y0 + (j+1/2) dy).
+ * bc: boundary condition on the sides x-, x+, y-, y+ (periodic must be paired). */
+typedef struct {
+  int nx, ny;
+  double x0, y0, dx, dy;
+  int bc[4];
+} sgn_grid;
+
+/* Method parameters (Sec. 4, last paragraph: alpha = 3, xi0 = 0.01, xi1 = 0.05,
+ * Courant 0.9-1, n = 1).  precision: SGN_FP64 computes and stores everything in
+ * FP64; SGN_MIXED stores the state in FP32 (eta as deviation from the still level)
+ * and computes the fluxes and sources in FP32, keeping FP64 for the depth
+ * h = eta - b and the hydrostatic term g h_hat d(eta), the positivity guard, the
+ * conservative mass update and the mass reduction. */
+typedef struct {
+  double alpha;        /* dimensionless relaxation parameter, c = alpha sqrt(g H) */
+  double h_star;       /* transition depth of phi_T [m] */
+  int n_transition;    /* neighbourhood radius n of phi_T in cells, 0..2 */
+  double xi0, xi1;     /* sensor parameters */
+  double cfl;          /* Courant number of the time step, (0, 1] */
+  double g;            /* gravity [m/s^2] */
+  double dry_tol;      /* a cell is wet when h > dry_tol [m] */
+  int limiter;         /* sgn_limiter */
+  int strang;          /* 1: Strang splitting, 0: Lie-Trotter */
+  int precision;       /* sgn_precision */
+} sgn_params;
+
+/* Device memory provider: alloc(bytes, ctx) returns device memory or NULL,
+ * free(ptr, ctx) releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} sgn_allocator;
+
+typedef struct sgn_solver sgn_solver;
+
+/* Fill *p with the defaults: alpha 3, h_star 0, n 1, xi0 0.01, xi1 0.05, cfl 0.9,
+ * g 9.81, dry_tol 1e-3, MC limiter, Strang, FP64. */
+void sgn_default_params(sgn_params* p);
+
+/* Number of state fields of a model (3, 5, 7) or SGN_EINVAL. */
+int sgn_nvar(int model);
+
+/* Human-readable text of an error code (static storage). */
+const char* sgn_strerror(int code);
+
+/* Create a solver.  bathymetry: ny*nx doubles (copied).  phi_override: NULL, or
+ * ny*nx bytes replacing the computed transition mask phi_T (0: SWE, else
+ * dispersive), copied.  The initial state is the lake at rest eta = max(0, b).
+ * Needs nx, ny >= 2, dx, dy > 0, 0 < cfl <= 1, n_transition in 0..2.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int sgn_create(const sgn_grid* grid, const double* bathymetry, int model,
+               const sgn_params* params, const unsigned char* phi_override,
+               const sgn_allocator* allocator, void* cuda_stream, sgn_solver** out);
+
+/* Replace the state: q is nvar*ny*nx doubles in host memory (pinned memory makes
+ * the copy asynchronous-capable); t is the new time.  The SWE/dry switch is
+ * applied (auxiliaries zeroed where phi_T = 0 or h <= dry_tol, momenta zeroed
+ * where h <= dry_tol), the status word and the gauge records are cleared and the
+ * CFL time step of the new state is computed.  Errors: EINVAL, ECUDA. */
+int sgn_set_state(sgn_solver* s, const double* q, double t);
+
+/* As sgn_set_state with q in device memory (nvar*ny*nx doubles, dense layout). */
+int sgn_set_state_device(sgn_solver* s, const double* q_dev, double t);
+
+/* Advance nsteps CFL-limited time steps (CUDA-graph replays of the kernel
+ * sequence; the time step lives on the device, no host synchronisation inside
+ * the batch).  Synchronises once at the end, reads the status word and returns
+ * the error of the first set bit (ENEGDEPTH, ENONFINITE, ECFL, ENONHYP, EALLDRY).
+ * t_out (may be NULL) receives the time reached. */
+int sgn_step(sgn_solver* s, int nsteps, double* t_out);
+
+/* Advance one step with the prescribed time step dt > 0 instead of the CFL one
+ * (the next CFL step is recomputed from the new state).  Errors as sgn_step. */
+int sgn_step_dt(sgn_solver* s, double dt);
+
+/* Copy fields of the state to host memory.  field_mask: bit k selects field k
+ * (0: all fields); the selected fields are written consecutively (ny*nx doubles
+ * each) into out, which holds out_len doubles.  t_out may be NULL.
+ * Synchronises the stream.  Errors: EINVAL, ERANGE, ECUDA. */
+int sgn_get_state(sgn_solver* s, int field_mask, double* out, size_t out_len, double* t_out);
+
+/* As sgn_get_state into device memory (all fields, nvar*ny*nx doubles); does not
+ * synchronise. */
+int sgn_get_state_device(sgn_solver* s, double* out_dev, size_t out_len);
+
+/* Gauges: xy holds n (x, y) pairs (copied); each step appends, per gauge, the
+ * record (t, eta, hu, hv) of the cell containing the gauge, up to capacity
+ * steps (then SGN_ST_GAUGEFULL is set and records stop).  Replaces earlier
+ * gauges.  Errors: EINVAL, ERANGE (gauge outside the grid), ENOMEM. */
+int sgn_add_gauges(sgn_solver* s, const double* xy, int n, int capacity);
+
+/* Copy the gauge records [rec][gauge][4] (cap doubles available in out) and
+ * report the number of records in *nrec; the records stay until the next
+ * sgn_set_state / sgn_add_gauges / sgn_clear_gauges.  Errors: EINVAL, ERANGE. */
+int sgn_gauges(sgn_solver* s, double* out, size_t cap, int* nrec);
+int sgn_clear_gauges(sgn_solver* s);
+
+/* Status word, the last time step taken and the largest face Courant number of
+ * the last step (any pointer may be NULL).  Synchronises the stream. */
+int sgn_status(sgn_solver* s, unsigned* flags, double* last_dt, double* max_courant);
+
+/* Total mass sum(h) dx dy over the grid by a deterministic two-stage FP64
+ * reduction.  Synchronises the stream. */
+int sgn_mass(sgn_solver* s, double* mass);
+
+/* Relaxation parameter c^2 (ny*nx doubles) and transition mask phi_T (ny*nx
+ * bytes) of the interior cells; either pointer may be NULL. */
+int sgn_get_aux(sgn_solver* s, double* c2, unsigned char* phi);
+
+/* Per-kernel timing: when enabled, steps launch kernels without CUDA graphs and
+ * bracket each launch with CUDA events on the solver stream.  sgn_kernel_times
+ * returns, for up to n kernels, the name, the accumulated time [ms] and the
+ * number of launches since profiling was enabled; the return value is the
+ * number of kernel kinds. */
+int sgn_set_profiling(sgn_solver* s, int enable);
+int sgn_kernel_times(sgn_solver* s, const char** names, double* ms, long* launches, int n);
+
+/* Number of kernel launches one time step issues (for launch accounting). */
+int sgn_launches_per_step(sgn_solver* s);
+
+/* Release all device memory and the handle (NULL is ignored). */
+void sgn_destroy(sgn_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGN_H */

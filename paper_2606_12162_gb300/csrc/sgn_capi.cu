@@ -1,0 +1,189 @@
+// sgn_capi.cu -- the extern "C" entry points of include/sgn.h: argument checks,
+// then dispatch to the solver object of the model and precision.
+#include <math.h>
+#include <new>
+
+#include "sgn_solver.cuh"
+
+struct sgn_solver {
+  sgn::SolverBase* impl;
+  int model;
+};
+
+extern "C" {
+
+void sgn_default_params(sgn_params* p) {
+  if (!p) return;
+  p->alpha = 3.0;
+  p->h_star = 0.0;
+  p->n_transition = 1;
+  p->xi0 = 0.01;
+  p->xi1 = 0.05;
+  p->cfl = 0.9;
+  p->g = 9.81;
+  p->dry_tol = 1e-3;
+  p->limiter = SGN_LIM_MC;
+  p->strang = 1;
+  p->precision = SGN_FP64;
+}
+
+int sgn_nvar(int model) {
+  switch (model) {
+    case SGN_SWE: return 3;
+    case SGN_MBHSGN: return 5;
+    case SGN_HSGN: return 7;
+  }
+  return SGN_EINVAL;
+}
+
+const char* sgn_strerror(int code) {
+  switch (code) {
+    case SGN_OK: return "ok";
+    case SGN_EINVAL: return "invalid argument";
+    case SGN_ENOMEM: return "device allocation failed";
+    case SGN_ECUDA: return "CUDA runtime error";
+    case SGN_ENEGDEPTH: return "negative water depth";
+    case SGN_ENONFINITE: return "non-finite value in the state";
+    case SGN_ECFL: return "face Courant number above 1";
+    case SGN_ENONHYP: return "loss of hyperbolicity (g h + p + c^2 < 0)";
+    case SGN_EALLDRY: return "no wet cell";
+    case SGN_ERANGE: return "buffer too small or gauge outside the grid";
+  }
+  return "unknown error";
+}
+
+static int check_args(const sgn_grid* g, const double* b, int model, const sgn_params* p) {
+  if (!g || !b || !p) return SGN_EINVAL;
+  if (g->nx < 2 || g->ny < 2) return SGN_EINVAL;
+  if ((long long)g->nx * g->ny > (1LL << 31)) return SGN_EINVAL;
+  if (!(g->dx > 0) || !(g->dy > 0) || !isfinite(g->dx) || !isfinite(g->dy)) return SGN_EINVAL;
+  for (int i = 0; i < 4; i++)
+    if (g->bc[i] < SGN_BC_WALL || g->bc[i] > SGN_BC_PERIODIC) return SGN_EINVAL;
+  if ((g->bc[0] == SGN_BC_PERIODIC) != (g->bc[1] == SGN_BC_PERIODIC)) return SGN_EINVAL;
+  if ((g->bc[2] == SGN_BC_PERIODIC) != (g->bc[3] == SGN_BC_PERIODIC)) return SGN_EINVAL;
+  if (sgn_nvar(model) < 0) return SGN_EINVAL;
+  if (!(p->cfl > 0) || p->cfl > 1.0) return SGN_EINVAL;
+  if (!(p->g > 0) || !(p->dry_tol >= 0) || !(p->alpha >= 0)) return SGN_EINVAL;
+  if (p->n_transition < 0 || p->n_transition > 2) return SGN_EINVAL;
+  if (p->limiter < SGN_LIM_MINMOD || p->limiter > SGN_LIM_NONE) return SGN_EINVAL;
+  if (p->precision != SGN_FP64 && p->precision != SGN_MIXED) return SGN_EINVAL;
+  if (!(p->xi0 >= 0) || !(p->xi1 > 0)) return SGN_EINVAL;
+  return SGN_OK;
+}
+
+int sgn_create(const sgn_grid* grid, const double* bathymetry, int model, const sgn_params* params,
+               const unsigned char* phi_override, const sgn_allocator* allocator, void* cuda_stream,
+               sgn_solver** out) {
+  if (!out) return SGN_EINVAL;
+  *out = nullptr;
+  int r = check_args(grid, bathymetry, model, params);
+  if (r) return r;
+  if (allocator && (!allocator->alloc || !allocator->free)) return SGN_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SGN_ECUDA;
+  sgn::SolverBase* impl = params->precision == SGN_MIXED ? sgn::make_solver_mixed(model)
+                                                          : sgn::make_solver_f64(model);
+  if (!impl) return SGN_ENOMEM;
+  sgn::CreateArgs a;
+  a.grid = *grid;
+  a.prm = *params;
+  a.model = model;
+  a.b = bathymetry;
+  a.phi = phi_override;
+  a.alloc = allocator;
+  a.stream = (cudaStream_t)cuda_stream;
+  r = impl->init(a);
+  if (r) {
+    delete impl;
+    return r;
+  }
+  sgn_solver* s = new (std::nothrow) sgn_solver;
+  if (!s) { delete impl; return SGN_ENOMEM; }
+  s->impl = impl;
+  s->model = model;
+  *out = s;
+  return SGN_OK;
+}
+
+int sgn_set_state(sgn_solver* s, const double* q, double t) {
+  if (!s || !q || !isfinite(t)) return SGN_EINVAL;
+  return s->impl->set_state(q, t, false);
+}
+
+int sgn_set_state_device(sgn_solver* s, const double* q_dev, double t) {
+  if (!s || !q_dev || !isfinite(t)) return SGN_EINVAL;
+  return s->impl->set_state(q_dev, t, true);
+}
+
+int sgn_step(sgn_solver* s, int nsteps, double* t_out) {
+  if (!s || nsteps < 0) return SGN_EINVAL;
+  return s->impl->step(nsteps, t_out);
+}
+
+int sgn_step_dt(sgn_solver* s, double dt) {
+  if (!s || !(dt > 0) || !isfinite(dt)) return SGN_EINVAL;
+  return s->impl->step_dt(dt);
+}
+
+int sgn_get_state(sgn_solver* s, int field_mask, double* out, size_t out_len, double* t_out) {
+  if (!s || !out || field_mask < 0) return SGN_EINVAL;
+  return s->impl->get_state(field_mask, out, out_len, t_out, false);
+}
+
+int sgn_get_state_device(sgn_solver* s, double* out_dev, size_t out_len) {
+  if (!s || !out_dev) return SGN_EINVAL;
+  return s->impl->get_state(0, out_dev, out_len, nullptr, true);
+}
+
+int sgn_add_gauges(sgn_solver* s, const double* xy, int n, int capacity) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->add_gauges(xy, n, capacity);
+}
+
+int sgn_gauges(sgn_solver* s, double* out, size_t cap, int* nrec) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->gauges(out, cap, nrec);
+}
+
+int sgn_clear_gauges(sgn_solver* s) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->clear_gauges();
+}
+
+int sgn_status(sgn_solver* s, unsigned* flags, double* last_dt, double* max_courant) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->status(flags, last_dt, max_courant);
+}
+
+int sgn_mass(sgn_solver* s, double* mass) {
+  if (!s || !mass) return SGN_EINVAL;
+  return s->impl->mass(mass);
+}
+
+int sgn_get_aux(sgn_solver* s, double* c2, unsigned char* phi) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->get_aux(c2, phi);
+}
+
+int sgn_set_profiling(sgn_solver* s, int enable) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->set_profiling(enable);
+}
+
+int sgn_kernel_times(sgn_solver* s, const char** names, double* ms, long* launches, int n) {
+  if (!s || n < 0) return SGN_EINVAL;
+  return s->impl->kernel_times(names, ms, launches, n);
+}
+
+int sgn_launches_per_step(sgn_solver* s) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->launches_per_step();
+}
+
+void sgn_destroy(sgn_solver* s) {
+  if (!s) return;
+  delete s->impl;
+  delete s;
+}
+
+}  // extern "C"

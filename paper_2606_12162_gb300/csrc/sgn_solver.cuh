@@ -1,0 +1,429 @@
+// sgn_solver.cuh -- host-side solver object: device buffers, the launch sequence
+// of one time step, CUDA-graph replay of that sequence, per-kernel timing.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+#include <vector>
+
+#include "../../include/sgn.h"
+#include "sgn_kernels.cuh"
+
+namespace sgn {
+
+struct CreateArgs {
+  sgn_grid grid;
+  sgn_params prm;
+  int model;
+  const double* b;
+  const unsigned char* phi;
+  const sgn_allocator* alloc;
+  cudaStream_t stream;
+};
+
+struct SolverBase {
+  virtual ~SolverBase() {}
+  virtual int init(const CreateArgs& a) = 0;
+  virtual int set_state(const double* q, double t, bool device) = 0;
+  virtual int step(int n, double* t_out) = 0;
+  virtual int step_dt(double dt) = 0;
+  virtual int get_state(int mask, double* out, size_t len, double* t_out, bool device) = 0;
+  virtual int add_gauges(const double* xy, int n, int cap) = 0;
+  virtual int gauges(double* out, size_t cap, int* nrec) = 0;
+  virtual int clear_gauges() = 0;
+  virtual int status(unsigned* f, double* dt, double* cr) = 0;
+  virtual int mass(double* m) = 0;
+  virtual int get_aux(double* c2, unsigned char* phi) = 0;
+  virtual int set_profiling(int on) = 0;
+  virtual int kernel_times(const char** names, double* ms, long* launches, int n) = 0;
+  virtual int launches_per_step() = 0;
+};
+
+SolverBase* make_solver_f64(int model);
+SolverBase* make_solver_mixed(int model);
+
+inline int status_to_error(unsigned st) {
+  if (st & ST_NONFINITE) return SGN_ENONFINITE;
+  if (st & ST_NEGDEPTH) return SGN_ENEGDEPTH;
+  if (st & ST_NONHYP) return SGN_ENONHYP;
+  if (st & ST_ALLDRY) return SGN_EALLDRY;
+  if (st & ST_CFL) return SGN_ECFL;
+  return SGN_OK;
+}
+
+#define SGN_CK(x)                        \
+  do {                                   \
+    cudaError_t e_ = (x);                \
+    if (e_ != cudaSuccess) return SGN_ECUDA; \
+  } while (0)
+
+enum { KN_PREP, KN_FACEX, KN_FACEY, KN_TRANSX, KN_TRANSY, KN_THETA, KN_UPDATE, KN_FINAL, KN_GAUGE, KN_COUNT };
+static const char* const kKernelNames[KN_COUNT] = {
+    "k_prep", "k_face_x", "k_face_y", "k_trans_x", "k_trans_y", "k_theta", "k_update", "k_finalize", "k_gauge"};
+
+template <int MODEL, typename Real>
+class Solver : public SolverBase {
+  static constexpr int NV = MT<MODEL>::NV;
+  static constexpr int NP = PT<MODEL>::NP;
+  static constexpr int NF = FT<MODEL>::NF;
+  static constexpr int FXB = 64, FXY = 4;   // x-face block
+  static constexpr int FYB = 32, FYY = 8;   // y-face block
+
+  Dev<Real> d_{};
+  sgn_allocator al_{};
+  bool own_alloc_ = true;
+  cudaStream_t st_ = nullptr, cap_ = nullptr;
+  std::vector<void*> bufs_;
+  int cur_ = 0;
+  double* staging_ = nullptr;   // dense double nv*nx*ny
+  double* hscal_ = nullptr;     // pinned host scalars
+  cudaGraphExec_t gx_[2] = {nullptr, nullptr};
+  bool prof_ = false;
+  struct Ev { int k; cudaEvent_t a, b; };
+  std::vector<Ev> evs_;
+  double kms_[KN_COUNT] = {0};
+  long kcnt_[KN_COUNT] = {0};
+  dim3 gPad_, gInt_, gFX_, gFY_, gTX_, gTY_;
+  int nmass_ = 0;
+
+  void* dalloc(size_t bytes) {
+    void* p = nullptr;
+    if (own_alloc_) {
+      if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    } else {
+      p = al_.alloc(bytes, al_.ctx);
+    }
+    if (p) bufs_.push_back(p);
+    return p;
+  }
+  template <typename T> T* dnew(size_t n) { return (T*)dalloc(n * sizeof(T) + 256); }
+
+  void drop_graphs() {
+    for (int i = 0; i < 2; i++)
+      if (gx_[i]) { cudaGraphExecDestroy(gx_[i]); gx_[i] = nullptr; }
+  }
+
+ public:
+  ~Solver() override {
+    if (st_) cudaStreamSynchronize(st_);
+    drop_graphs();
+    for (auto& e : evs_) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (void* p : bufs_) {
+      if (own_alloc_) cudaFree(p);
+      else al_.free(p, al_.ctx);
+    }
+    if (hscal_) cudaFreeHost(hscal_);
+    if (cap_) cudaStreamDestroy(cap_);
+  }
+
+  int init(const CreateArgs& a) override {
+    st_ = a.stream;
+    if (a.alloc && a.alloc->alloc && a.alloc->free) { al_ = *a.alloc; own_alloc_ = false; }
+    int dev = -1;
+    SGN_CK(cudaGetDevice(&dev));
+    SGN_CK(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+    SGN_CK(cudaMallocHost((void**)&hscal_, 64 * sizeof(double)));
+    const sgn_grid& g = a.grid;
+    const sgn_params& p = a.prm;
+    d_.nx = g.nx; d_.ny = g.ny;
+    d_.nxp = g.nx + 2 * NG; d_.nyp = g.ny + 2 * NG;
+    d_.pitch = ((d_.nxp + 1) + 31) / 32 * 32;
+    d_.fs = (size_t)d_.pitch * (d_.nyp + 1);
+    for (int i = 0; i < 4; i++) d_.bc[i] = g.bc[i];
+    x0_ = g.x0; y0_ = g.y0;
+    d_.dx = g.dx; d_.dy = g.dy; d_.g = p.g; d_.dry_tol = p.dry_tol; d_.cfl = p.cfl;
+    d_.xi0 = p.xi0; d_.xi1 = p.xi1; d_.alpha = p.alpha; d_.h_star = p.h_star;
+    d_.limiter = p.limiter; d_.strang = p.strang; d_.n_transition = p.n_transition;
+    size_t fs = d_.fs;
+    d_.q[0] = dnew<Real>(NV * fs); d_.q[1] = dnew<Real>(NV * fs);
+    d_.b = dnew<Real>(fs); d_.c2 = dnew<Real>(fs); d_.psx = dnew<Real>(fs); d_.psy = dnew<Real>(fs);
+    d_.phi = dnew<unsigned char>(fs);
+    d_.W = dnew<Real>(NV * fs); d_.P = dnew<Real>(NP * fs);
+    d_.FX = dnew<Real>(NF * fs); d_.FY = dnew<Real>(NF * fs);
+    d_.TX = dnew<Real>(NV * fs); d_.TY = dnew<Real>(NV * fs);
+    d_.theta = dnew<Real>(fs);
+    d_.Hd = dnew<double>(fs);
+    double* sc = dnew<double>(16);
+    unsigned* si = dnew<unsigned>(16);
+    staging_ = dnew<double>((size_t)NV * g.nx * g.ny);
+    if (!d_.q[0] || !d_.q[1] || !d_.b || !d_.c2 || !d_.psx || !d_.psy || !d_.phi || !d_.W || !d_.P ||
+        !d_.FX || !d_.FY || !d_.TX || !d_.TY || !d_.theta || !d_.Hd || !sc || !si || !staging_)
+      return SGN_ENOMEM;
+    d_.dt = sc; d_.t = sc + 1; d_.last_dt = sc + 2; d_.courant = sc + 3; d_.mass = sc + 4;
+    d_.lam = sc + 5;                                   // 4 doubles
+    d_.smax = (unsigned long long*)(sc + 10);
+    d_.cmax = (unsigned long long*)(sc + 11);
+    d_.rdry_tol = (Real)p.dry_tol;
+    d_.inv_dx = 1.0 / g.dx;
+    d_.inv_dy = 1.0 / g.dy;
+    d_.status = si; d_.gn = (int*)(si + 1);
+    // launch geometry
+    gPad_ = dim3((d_.nxp + 31) / 32, (d_.nyp + 7) / 8);
+    gInt_ = dim3((g.nx + 31) / 32, (g.ny + 7) / 8);
+    gFX_ = dim3((g.nx + 1 + FXB - 3) / (FXB - 2), (g.ny + 2 + FXY - 1) / FXY);
+    gFY_ = dim3((g.nx + 2 + FYB - 1) / FYB, (g.ny + 1 + FYY - 3) / (FYY - 2));
+    gTX_ = dim3((g.nx + 3 + 31) / 32, (g.ny + 2 + 7) / 8);
+    gTY_ = dim3((g.nx + 2 + 31) / 32, (g.ny + 3 + 7) / 8);
+    nmass_ = 1024;
+    d_.mass_part = dnew<double>(nmass_);
+    if (!d_.mass_part) return SGN_ENOMEM;
+    // zero every buffer (faces outside the computed ranges stay 0), theta = 1
+    for (size_t k = 0; k < 2; k++) SGN_CK(cudaMemsetAsync(d_.q[k], 0, NV * fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.W, 0, NV * fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.P, 0, NP * fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.FX, 0, NF * fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.FY, 0, NF * fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.TX, 0, NV * fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.TY, 0, NV * fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.psx, 0, fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.psy, 0, fs * sizeof(Real), st_));
+    SGN_CK(cudaMemsetAsync(d_.phi, 0, fs, st_));
+    SGN_CK(cudaMemsetAsync(sc, 0, 16 * sizeof(double), st_));
+    SGN_CK(cudaMemsetAsync(si, 0, 16 * sizeof(unsigned), st_));
+    k_fill_one<Real><<<(unsigned)((fs + 255) / 256), 256, 0, st_>>>(d_.theta, fs);
+    // setup: padded b and phi override, phi_T, c^2, psi
+    size_t n = (size_t)g.nx * g.ny;
+    SGN_CK(cudaMemcpyAsync(staging_, a.b, n * sizeof(double), cudaMemcpyHostToDevice, st_));
+    unsigned char* phid = nullptr;
+    if (a.phi) {
+      phid = (unsigned char*)(staging_ + n);
+      SGN_CK(cudaMemcpyAsync(phid, a.phi, n, cudaMemcpyHostToDevice, st_));
+    }
+    k_pack_b<Real><<<gPad_, dim3(32, 8), 0, st_>>>(d_, staging_, phid);
+    k_phi<Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, a.phi ? 1 : 0);
+    k_aux<Real><<<dim3((d_.nxp + 1 + 31) / 32, (d_.nyp + 1 + 7) / 8), dim3(32, 8), 0, st_>>>(d_);
+    SGN_CK(cudaGetLastError());
+    // initial state: lake at rest
+    std::vector<double> q0(n * NV, 0.0);
+    for (size_t i = 0; i < n; i++) q0[i] = a.b[i] > 0 ? a.b[i] : 0.0;
+    SGN_CK(cudaStreamSynchronize(st_));
+    return set_state(q0.data(), 0.0, false);
+  }
+
+  int set_state(const double* q, double t, bool device) override {
+    size_t n = (size_t)d_.nx * d_.ny * NV;
+    SGN_CK(cudaMemcpyAsync(staging_, q, n * sizeof(double), device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));
+    cur_ = 0;
+    k_pack_state<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, staging_, 0);
+    hscal_[0] = t;
+    SGN_CK(cudaMemcpyAsync(d_.t, hscal_, sizeof(double), cudaMemcpyHostToDevice, st_));
+    SGN_CK(cudaMemsetAsync(d_.status, 0, sizeof(unsigned), st_));
+    SGN_CK(cudaMemsetAsync(d_.gn, 0, sizeof(int), st_));
+    SGN_CK(cudaMemsetAsync(d_.last_dt, 0, 2 * sizeof(double), st_));
+    SGN_CK(cudaMemsetAsync(d_.smax, 0, 2 * sizeof(unsigned long long), st_));
+    k_speed<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, 0);
+    k_finalize<Real><<<1, 32, 0, st_>>>(d_, 0);
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaStreamSynchronize(st_));
+    return SGN_OK;
+  }
+
+  // One time step from q[c] into q[1-c]: the kernel sequence of the method.
+  void launch_step(cudaStream_t s, int c) {
+    auto pre = [&](int k) {
+      if (!prof_) return;
+      Ev e; e.k = k; cudaEventCreate(&e.a); cudaEventCreate(&e.b);
+      cudaEventRecord(e.a, s); evs_.push_back(e);
+    };
+    auto post = [&]() { if (prof_) cudaEventRecord(evs_.back().b, s); };
+    pre(KN_PREP);
+    k_prep<MODEL, Real><<<gPad_, dim3(32, 8), 0, s>>>(d_, c); post();
+    pre(KN_FACEX);
+    k_face<MODEL, Real, 0, FXB, FXY><<<gFX_, dim3(FXB, FXY), 0, s>>>(d_); post();
+    pre(KN_FACEY);
+    k_face<MODEL, Real, 1, FYB, FYY><<<gFY_, dim3(FYB, FYY), 0, s>>>(d_); post();
+    pre(KN_TRANSX);
+    k_trans<MODEL, Real, 0><<<gTX_, dim3(32, 8), 0, s>>>(d_); post();
+    pre(KN_TRANSY);
+    k_trans<MODEL, Real, 1><<<gTY_, dim3(32, 8), 0, s>>>(d_); post();
+    pre(KN_THETA);
+    k_theta<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_); post();
+    pre(KN_UPDATE);
+    k_update<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_, c); post();
+    pre(KN_FINAL);
+    k_finalize<Real><<<1, 32, 0, s>>>(d_, 1); post();
+    if (d_.ngauge > 0) {
+      pre(KN_GAUGE);
+      k_gauge<Real><<<1, 256, 0, s>>>(d_, 1 - c); post();
+    }
+  }
+
+  int launches_per_step() override { return d_.ngauge > 0 ? 9 : 8; }
+
+  int build_graph(int c) {
+    cudaGraph_t gr;
+    SGN_CK(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+    launch_step(cap_, c);
+    cudaError_t e = cudaStreamEndCapture(cap_, &gr);
+    if (e != cudaSuccess) return SGN_ECUDA;
+    e = cudaGraphInstantiate(&gx_[c], gr, 0);
+    cudaGraphDestroy(gr);
+    return e == cudaSuccess ? SGN_OK : SGN_ECUDA;
+  }
+
+  int finish_batch(double* t_out) {
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaMemcpyAsync(hscal_, d_.t, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaMemcpyAsync(hscal_ + 1, d_.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    if (t_out) *t_out = hscal_[0];
+    unsigned stv;
+    memcpy(&stv, hscal_ + 1, sizeof(unsigned));
+    return status_to_error(stv);
+  }
+
+  int step(int n, double* t_out) override {
+    if (n < 0) return SGN_EINVAL;
+    for (int i = 0; i < n; i++) {
+      if (prof_) {
+        launch_step(st_, cur_);
+      } else {
+        if (!gx_[cur_]) { int r = build_graph(cur_); if (r) return r; }
+        SGN_CK(cudaGraphLaunch(gx_[cur_], st_));
+      }
+      cur_ ^= 1;
+    }
+    return finish_batch(t_out);
+  }
+
+  int step_dt(double dt) override {
+    hscal_[2] = dt;
+    hscal_[8] = dt / d_.dx;
+    hscal_[9] = dt / d_.dy;
+    hscal_[10] = d_.strang ? 0.5 * dt : 0.0;
+    hscal_[11] = d_.strang ? 0.5 * dt : dt;
+    SGN_CK(cudaMemcpyAsync(d_.dt, hscal_ + 2, sizeof(double), cudaMemcpyHostToDevice, st_));
+    SGN_CK(cudaMemcpyAsync(d_.lam, hscal_ + 8, 4 * sizeof(double), cudaMemcpyHostToDevice, st_));
+    launch_step(st_, cur_);
+    cur_ ^= 1;
+    return finish_batch(nullptr);
+  }
+
+  int get_state(int mask, double* out, size_t len, double* t_out, bool device) override {
+    size_t n = (size_t)d_.nx * d_.ny;
+    if (mask == 0) mask = (1 << NV) - 1;
+    if (mask & ~((1 << NV) - 1)) return SGN_EINVAL;
+    int nsel = 0;
+    for (int k = 0; k < NV; k++) nsel += (mask >> k) & 1;
+    if (len < nsel * n) return SGN_ERANGE;
+    k_unpack_state<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, staging_, cur_);
+    SGN_CK(cudaGetLastError());
+    int o = 0;
+    for (int k = 0; k < NV; k++) {
+      if (!((mask >> k) & 1)) continue;
+      SGN_CK(cudaMemcpyAsync(out + o * n, staging_ + k * n, n * sizeof(double),
+                             device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st_));
+      o++;
+    }
+    if (t_out || !device) {
+      SGN_CK(cudaMemcpyAsync(hscal_, d_.t, sizeof(double), cudaMemcpyDeviceToHost, st_));
+      SGN_CK(cudaStreamSynchronize(st_));
+      if (t_out) *t_out = hscal_[0];
+    }
+    return SGN_OK;
+  }
+
+  int add_gauges(const double* xy, int n, int cap) override {
+    if (n < 0 || cap < 0 || (n > 0 && !xy)) return SGN_EINVAL;
+    std::vector<int> idx(n > 0 ? n : 1);
+    for (int g = 0; g < n; g++) {
+      double fx = (xy[2 * g] - x0_) / d_.dx, fy = (xy[2 * g + 1] - y0_) / d_.dy;
+      if (!(fx >= 0) || !(fy >= 0)) return SGN_ERANGE;
+      long i = (long)fx, j = (long)fy;
+      if (i >= d_.nx || j >= d_.ny) return SGN_ERANGE;
+      idx[g] = (int)((j + NG) * (long)d_.pitch + (i + NG));
+    }
+    drop_graphs();
+    d_.gidx = dnew<int>(idx.size());
+    d_.grec = dnew<double>((size_t)(n > 0 ? n : 1) * 4 * (cap > 0 ? cap : 1));
+    if (!d_.gidx || !d_.grec) return SGN_ENOMEM;
+    SGN_CK(cudaMemcpyAsync(d_.gidx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, st_));
+    SGN_CK(cudaMemsetAsync(d_.gn, 0, sizeof(int), st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    d_.ngauge = n; d_.gcap = cap;
+    return SGN_OK;
+  }
+
+  int gauges(double* out, size_t cap, int* nrec) override {
+    int n = 0;
+    SGN_CK(cudaMemcpyAsync(hscal_ + 3, d_.gn, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    memcpy(&n, hscal_ + 3, sizeof(int));
+    if (nrec) *nrec = n;
+    size_t need = (size_t)n * d_.ngauge * 4;
+    if (!out) return SGN_OK;
+    if (cap < need) return SGN_ERANGE;
+    if (need) SGN_CK(cudaMemcpy(out, d_.grec, need * sizeof(double), cudaMemcpyDeviceToHost));
+    return SGN_OK;
+  }
+
+  int clear_gauges() override {
+    SGN_CK(cudaMemsetAsync(d_.gn, 0, sizeof(int), st_));
+    return SGN_OK;
+  }
+
+  int status(unsigned* f, double* dt, double* cr) override {
+    SGN_CK(cudaMemcpyAsync(hscal_ + 4, d_.last_dt, 2 * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaMemcpyAsync(hscal_ + 6, d_.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    if (dt) *dt = hscal_[4];
+    if (cr) *cr = hscal_[5];
+    if (f) memcpy(f, hscal_ + 6, sizeof(unsigned));
+    return SGN_OK;
+  }
+
+  int mass(double* m) override {
+    int nb = 592;   // 152 SMs x 4
+    k_mass1<Real><<<nb, 256, 0, st_>>>(d_, cur_);
+    k_mass2<Real><<<1, 256, 0, st_>>>(d_, nb);
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaMemcpyAsync(hscal_ + 7, d_.mass, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    *m = hscal_[7];
+    return SGN_OK;
+  }
+
+  int get_aux(double* c2, unsigned char* phi) override {
+    size_t n = (size_t)d_.nx * d_.ny;
+    unsigned char* pd = (unsigned char*)(staging_ + n);
+    k_aux_out<Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, staging_, pd);
+    SGN_CK(cudaGetLastError());
+    if (c2) SGN_CK(cudaMemcpyAsync(c2, staging_, n * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    if (phi) SGN_CK(cudaMemcpyAsync(phi, pd, n, cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    return SGN_OK;
+  }
+
+  int set_profiling(int on) override {
+    SGN_CK(cudaStreamSynchronize(st_));
+    collect();
+    prof_ = on != 0;
+    for (int k = 0; k < KN_COUNT; k++) { kms_[k] = 0; kcnt_[k] = 0; }
+    return SGN_OK;
+  }
+
+  void collect() {
+    for (auto& e : evs_) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) { kms_[e.k] += ms; kcnt_[e.k]++; }
+      cudaEventDestroy(e.a); cudaEventDestroy(e.b);
+    }
+    evs_.clear();
+  }
+
+  int kernel_times(const char** names, double* ms, long* launches, int n) override {
+    SGN_CK(cudaStreamSynchronize(st_));
+    collect();
+    for (int k = 0; k < n && k < KN_COUNT; k++) {
+      if (names) names[k] = kKernelNames[k];
+      if (ms) ms[k] = kms_[k];
+      if (launches) launches[k] = kcnt_[k];
+    }
+    return KN_COUNT;
+  }
+
+  double x0_ = 0, y0_ = 0;
+  void set_origin(double x0, double y0) { x0_ = x0; y0_ = y0; }
+};
+
+}  // namespace sgn
