@@ -187,6 +187,30 @@ int sgn_launches_per_step(sgn_solver* s);
 /* Release all device memory and the handle (NULL is ignored). */
 void sgn_destroy(sgn_solver* s);
 
+/* Total mass without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory where they
+ * need the mass (a host that hands the library a fixed memory pool and forbids
+ * further allocations, or a latency-critical loop where cudaMalloc / cudaFree,
+ * which can synchronise the device, are not acceptable).
+ *
+ * Computes sum over the nx*ny cells of max(0, eta - b) * dx * dy, like
+ * sgn_mass, from caller-owned device arrays: eta_dev and b_dev hold nx*ny
+ * doubles each (row-major, x fastest, e.g. field 0 of sgn_get_state_device and
+ * the bathymetry), mass_dev receives one double.  Work is issued on cuda_stream
+ * (NULL: the legacy default stream) and the call does not synchronise.
+ * The per-block partial sums live in a fixed array compiled into the library:
+ * SGN_MASS_SCRATCH_MAX doubles, one per 4096 cells, so grids above
+ * 4096 * SGN_MASS_SCRATCH_MAX cells are rejected with SGN_ERANGE.  Every call
+ * shares that array (it keeps the last call's partials; each call writes every
+ * slot it reads), so calls that may overlap on the GPU -- on different streams
+ * or from different host threads -- race and must be ordered by the caller.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Errors: EINVAL (null pointer, non-positive size), ERANGE, ECUDA. */
+#define SGN_MASS_SCRATCH_MAX 65536
+int sgn_mass_static(const double* eta_dev, const double* b_dev, int nx, int ny, double dx, double dy,
+                    double* mass_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,7 +81,19 @@ SIGNATURES = [
                                         ctypes.POINTER(ctypes.c_long), ctypes.c_int]),
     ("sgn_launches_per_step", ctypes.c_int, [ctypes.c_void_p]),
     ("sgn_destroy", None, [ctypes.c_void_p]),
+    ("sgn_mass_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
 ]
+MASS_SCRATCH_MAX = 65536
+
+
+def mass_static(eta, b, dx, dy, out, stream=None):
+    """Allocation-free mass of eta/b (CUDA float64 tensors, (ny, nx)) into out (a
+    CUDA float64 tensor with one element); returns the C ABI's error code."""
+    ny, nx = eta.shape[-2], eta.shape[-1]
+    return load().sgn_mass_static(ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(b.data_ptr()), nx, ny,
+                                  float(dx), float(dy), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(stream) if stream else None)
 
 
 def load():

@@ -1,0 +1,71 @@
+"""The allocation-free mass entry point (sgn_mass_static).
+
+It is meant for callers that may not allocate device memory where they need the
+total mass -- a host that gives the library a fixed memory pool and forbids
+further allocations, or a latency-critical loop where cudaMalloc / cudaFree
+(which can synchronise the device) are not acceptable.  Its partial sums live in
+a fixed array compiled into the library, shared by every call.  This test calls
+it through the C ABI twice in a row, on different grids and states, and checks
+each result against sgn_mass (the solver's own reduction in allocated scratch).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2606_12162_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_12162_gb300 import build, sgn
+    build.build()
+    sgn.load()
+    return sgn
+
+
+def _dense_state(torch, s):
+    q = torch.empty((s.nvar, s.ny, s.nx), dtype=torch.float64, device="cuda")
+    s.get_state_device(q)
+    return q
+
+
+def test_mass_static_matches_sgn_mass_on_two_calls(S):
+    import torch
+    out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    cases = [(300, 170, 3), (1100, 700, 4)]      # 51 000 and 770 000 cells
+    for nx, ny, seed in cases:
+        b, q = W.random_small_case(2, nx, ny, seed=seed, dx=0.05, wetdry=True)
+        s = S.Solver(b, model=2, dx=0.05, bc=(0, 0, 0, 0), h_star=0.6)
+        s.set_state(q)
+        s.step(3)
+        qd = _dense_state(torch, s)
+        bd = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        stream = torch.cuda.current_stream().cuda_stream
+        rc = S.mass_static(qd[0], bd, 0.05, 0.05, out, stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        ref = s.mass()
+        got = out.item()
+        assert abs(got - ref) <= REL_TOL * ref, (got, ref)
+
+
+def test_mass_static_rejects_bad_arguments(S):
+    import torch
+    L = S.load()
+    buf = torch.zeros(4, dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    # a grid needing more partial sums than the fixed array holds (checked before any access)
+    nx = 65536
+    ny = S.MASS_SCRATCH_MAX * 4096 // nx + 1
+    assert L.sgn_mass_static(p, p, nx, ny, 1.0, 1.0, p, None) == -9
+    assert L.sgn_mass_static(None, p, 2, 2, 1.0, 1.0, p, None) == -1
+    assert L.sgn_mass_static(p, p, 0, 2, 1.0, 1.0, p, None) == -1
+    assert L.sgn_mass_static(p, p, 2, 2, 0.0, 1.0, p, None) == -1
