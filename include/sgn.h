@@ -187,6 +187,14 @@ int sgn_launches_per_step(sgn_solver* s);
 /* Release all device memory and the handle (NULL is ignored). */
 void sgn_destroy(sgn_solver* s);
 
+/* Diagnostic: the FP64 reciprocal and square root used inside the kernels (a
+ * hardware approximation refined by Newton-Raphson steps) against CUDA's IEEE
+ * division and sqrt.  x_dev: n positive doubles in device memory; err_dev: 2n
+ * doubles in device memory receiving, per input, the error of the reciprocal and
+ * of the square root in units in the last place.  Synchronises the device.
+ * Errors: EINVAL, ECUDA. */
+int sgn_math_check(const double* x_dev, int n, double* err_dev);
+
 /* Total mass without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory where they
  * need the mass (a host that hands the library a fixed memory pool and forbids

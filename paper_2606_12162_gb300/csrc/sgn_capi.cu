@@ -10,7 +10,31 @@ struct sgn_solver {
   int model;
 };
 
+// Error of the kernels' FP64 reciprocal and square root against the IEEE
+// results of CUDA's division and sqrt, in units in the last place of the IEEE
+// result: err[2i] for rcp(x[i]), err[2i+1] for sqrt(x[i]).
+__global__ void k_math_check(const double* x, int n, double* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = x[i];
+  double r0 = 1.0 / v, r1 = sgn::rcp(v);
+  double q0 = sqrt(v), q1 = sgn::sqrt_nr(v);
+  // one unit in the last place: the distance to the next representable double
+  double ur = fabs(__longlong_as_double(__double_as_longlong(r0) + 1) - r0);
+  double uq = fabs(__longlong_as_double(__double_as_longlong(q0) + 1) - q0);
+  err[2 * i] = ur > 0 ? fabs(r1 - r0) / ur : 0.0;
+  err[2 * i + 1] = uq > 0 ? fabs(q1 - q0) / uq : 0.0;
+}
+
 extern "C" {
+
+int sgn_math_check(const double* x_dev, int n, double* err_dev) {
+  if (!x_dev || !err_dev || n < 0) return SGN_EINVAL;
+  if (n == 0) return SGN_OK;
+  k_math_check<<<(n + 255) / 256, 256>>>(x_dev, n, err_dev);
+  if (cudaGetLastError() != cudaSuccess) return SGN_ECUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? SGN_OK : SGN_ECUDA;
+}
 
 void sgn_default_params(sgn_params* p) {
   if (!p) return;

@@ -67,7 +67,7 @@ class Solver : public SolverBase {
   static constexpr int NP = PT<MODEL>::NP;
   static constexpr int NF = FT<MODEL>::NF;
   static constexpr int FXB = 64, FXY = 4;   // x-face block
-  static constexpr int FYB = 32, FYY = 8;   // y-face block
+  static constexpr int FYB = 16, FYY = 16;  // y-face block
 
   Dev<Real> d_{};
   sgn_allocator al_{};
@@ -142,18 +142,19 @@ class Solver : public SolverBase {
     d_.FX = dnew<Real>(NF * fs); d_.FY = dnew<Real>(NF * fs);
     d_.TX = dnew<Real>(NV * fs); d_.TY = dnew<Real>(NV * fs);
     d_.theta = dnew<Real>(fs);
-    d_.Hd = dnew<double>(fs);
+    d_.G2 = dnew<double>(fs);
     double* sc = dnew<double>(16);
     unsigned* si = dnew<unsigned>(16);
     staging_ = dnew<double>((size_t)NV * g.nx * g.ny);
     if (!d_.q[0] || !d_.q[1] || !d_.b || !d_.c2 || !d_.psx || !d_.psy || !d_.phi || !d_.W || !d_.P ||
-        !d_.FX || !d_.FY || !d_.TX || !d_.TY || !d_.theta || !d_.Hd || !sc || !si || !staging_)
+        !d_.FX || !d_.FY || !d_.TX || !d_.TY || !d_.theta || !d_.G2 || !sc || !si || !staging_)
       return SGN_ENOMEM;
     d_.dt = sc; d_.t = sc + 1; d_.last_dt = sc + 2; d_.courant = sc + 3; d_.mass = sc + 4;
     d_.lam = sc + 5;                                   // 4 doubles
     d_.smax = (unsigned long long*)(sc + 10);
     d_.cmax = (unsigned long long*)(sc + 11);
     d_.rdry_tol = (Real)p.dry_tol;
+    d_.two_over_g = 2.0 / p.g;
     d_.inv_dx = 1.0 / g.dx;
     d_.inv_dy = 1.0 / g.dy;
     d_.status = si; d_.gn = (int*)(si + 1);

@@ -265,3 +265,100 @@ def test_errors_reported(sgn):
     assert s2.step_rc(1) == -8           # all dry
     with pytest.raises(sgn.SGNError):
         s.get_state_ptr(0, 1) if False else s.add_gauges([[1e9, 0.0]], 4)
+
+
+def test_fp64_reciprocal_and_sqrt_against_ieee(sgn):
+    """The kernels' FP64 reciprocal and square root (hardware approximation plus
+    Newton-Raphson steps) stay within 2 ulp of CUDA's IEEE division and sqrt over
+    a wide range of magnitudes."""
+    import ctypes
+    import torch
+    rng = np.random.default_rng(0)
+    x = np.concatenate([10.0 ** rng.uniform(-200, 200, 20000), rng.uniform(0.5, 2.0, 20000),
+                        np.array([1.0, 2.0, 3.0, 1e-300, 1e300, 7.0 / 3.0])])
+    xd = torch.from_numpy(x).cuda()
+    err = torch.empty(2 * len(x), dtype=torch.float64, device="cuda")
+    rc = sgn.load().sgn_math_check(ctypes.c_void_p(xd.data_ptr()), len(x), ctypes.c_void_p(err.data_ptr()))
+    assert rc == 0
+    e = err.cpu().numpy().reshape(-1, 2)
+    assert e[:, 0].max() <= 2.0 and e[:, 1].max() <= 2.0, e.max(axis=0)
+
+
+def _arrival_times(rec, frac=0.01):
+    """First time at which |eta| reaches frac of the gauge's maximum |eta|."""
+    t = rec[:, 0, 0]
+    eta = np.abs(rec[:, :, 1])
+    thr = frac * eta.max(axis=0)
+    out = []
+    for g in range(eta.shape[1]):
+        idx = np.nonzero(eta[:, g] >= thr[g])[0]
+        out.append(t[idx[0]] if len(idx) and thr[g] > 0 else np.nan)
+    return np.array(out)
+
+
+def test_config3_crop_fp64_and_mixed(sgn, oracle_mod):
+    """1024 x 1024 crop of the third configuration (fractal bathymetry, ~20 % land,
+    2 m uplift), 200 steps: the GPU FP64 path within 1e-12 of the oracle; the mixed
+    path against the GPU FP64 path within relative L2 1e-3 (eta, hu, hv over wet
+    cells), max |eta| error 1e-2 of the initial amplitude, gauge arrival times
+    within one time step."""
+    c = W.config3(model=2, crop=1024, ngauges=32)
+    cfg = dict(dx=c["dx"], x0=c["x0"], y0=c["y0"], model=2, bc=c["bc"], h_star=c["h_star"], alpha=3.0)
+    steps = 200
+    # gauges on rings of 10-30 km around the source, where the wave arrives within
+    # the run (wet cells only)
+    cx, cy = c["source"]
+    ring = []
+    for r in (10e3, 20e3, 30e3):
+        for a in np.linspace(0, 2 * np.pi, 8, endpoint=False):
+            x, y = cx + r * np.cos(a), cy + r * np.sin(a)
+            i, j = int((x - c["x0"]) / c["dx"]), int((y - c["y0"]) / c["dx"])
+            if 0 <= i < 1024 and 0 <= j < 1024 and c["b"][j, i] < -50.0:
+                ring.append((x, y))
+    c["gauges"] = np.array(ring)
+    s = sgn.Solver(c["b"], **cfg)
+    s.set_state(c["q"])
+    s.add_gauges(c["gauges"], steps + 4)
+    s.step(steps)
+    q64, t64 = s.get_state()
+    g64 = s.gauges()
+    o = oracle_mod.Oracle(c["b"], **cfg)
+    o.set_state(c["q"])
+    assert o.step(steps) == 0
+    qo, to = o.get_state()
+    assert (rel_l2(q64, qo) <= FP64_TOL).all(), rel_l2(q64, qo)
+    sm = sgn.Solver(c["b"], precision=1, **cfg)
+    sm.set_state(c["q"])
+    sm.add_gauges(c["gauges"], steps + 4)
+    sm.step(steps)
+    qm, _ = sm.get_state()
+    gm = sm.gauges()
+    wet = (q64[0] - c["b"]) > 1e-3
+    err = rel_l2(qm[:3], q64[:3], wet)
+    assert (err <= 1e-3).all(), err
+    assert np.abs(qm[0] - q64[0]).max() <= 1e-2 * 2.0
+    dt = s.status()[1]
+    ta, tb = _arrival_times(g64), _arrival_times(gm)
+    ok = ~np.isnan(ta) & (np.abs(g64[:, :, 1]).max(axis=0) >= 0.01)
+    assert ok.sum() >= 8
+    assert np.nanmax(np.abs(ta[ok] - tb[ok])) <= dt * 1.0001
+
+
+def test_config2_full_size_mixed_against_fp64(sgn):
+    """Full 4096 x 4096 second configuration, 300 steps: mixed precision against
+    the (oracle-checked) FP64 GPU path: relative L2 of eta <= 1e-4 and of hu, hv
+    <= 1e-3 over wet cells, max |eta| error <= 1e-3 of the 5 m source amplitude."""
+    c = W.config2(model=2)
+    cfg = dict(dx=c["dx"], model=2, bc=c["bc"], h_star=c["h_star"], alpha=3.0)
+    out = []
+    for prec in (0, 1):
+        s = sgn.Solver(c["b"], precision=prec, **cfg)
+        s.set_state(c["q"])
+        s.step(300)
+        out.append(s.get_state()[0])
+        del s
+    q64, qm = out
+    wet = (q64[0] - c["b"]) > 1e-3
+    err = rel_l2(qm[:3], q64[:3], wet)
+    assert err[0] <= 1e-4 and err[1] <= 1e-3 and err[2] <= 1e-3, err
+    assert np.abs(qm[0] - q64[0]).max() <= 1e-3 * 5.0
