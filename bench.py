@@ -34,10 +34,25 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP32 CUDA-core peak: 152 SMs x 128 FFMA/clk/SM x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# FP64 / FP32 flops per cell-update of each kernel (ncu instruction counts on the
-# 1024^2 case: dadd + dmul + 2 dfma, fadd + fmul + 2 ffma; divided by the cells
-# of one launch).  Filled from profiles/; None means not measured.
-FLOPS_PER_CELL = {}
+# FP64 flops per cell-update of each kernel of the FP64 path (ncu thread-instruction
+# counts dadd + dmul + 2 dfma on the 2048^2 case divided by its cells;
+# profiles/step_kernels_2048_counters.md).
+FLOPS_PER_CELL = {
+    ("hsgn", "fp64", "k_prep"): 134.2, ("hsgn", "fp64", "k_face_x"): 307.5,
+    ("hsgn", "fp64", "k_face_y"): 320.1, ("hsgn", "fp64", "k_trans_x"): 127.6,
+    ("hsgn", "fp64", "k_trans_y"): 127.6, ("hsgn", "fp64", "k_theta"): 29.4,
+    ("hsgn", "fp64", "k_update"): 217.4,
+}
+# DRAM bytes (read + write) per cell of one launch, same capture (2048^2 is above
+# L2, so traffic per cell carries over to 4096^2).
+TRAFFIC_PER_CELL = {
+    ("hsgn", "mixed", "k_prep"): 89, ("hsgn", "mixed", "k_face_x"): 138, ("hsgn", "mixed", "k_face_y"): 141,
+    ("hsgn", "mixed", "k_trans_x"): 106, ("hsgn", "mixed", "k_trans_y"): 106, ("hsgn", "mixed", "k_theta"): 17,
+    ("hsgn", "mixed", "k_update"): 221,
+    ("hsgn", "fp64", "k_prep"): 183, ("hsgn", "fp64", "k_face_x"): 279, ("hsgn", "fp64", "k_face_y"): 279,
+    ("hsgn", "fp64", "k_trans_x"): 215, ("hsgn", "fp64", "k_trans_y"): 216, ("hsgn", "fp64", "k_theta"): 37,
+    ("hsgn", "fp64", "k_update"): 441,
+}
 
 
 def parse():
@@ -186,6 +201,34 @@ def kernel_bytes(name, nv, s):
     return 0
 
 
+def roofline(model, prec, kt, cells, b_alg, nv, esize, hbm, hbm_src):
+    """Roofline of the kernel with the largest time in kt (name -> (ms, launches)).
+    FP64 path: bound by the FP64 pipe (flops counted by ncu per cell).  Mixed path:
+    HBM; achieved = the step's algorithmic bytes per cell-update x cells of one
+    launch / that kernel's average launch time; the kernel's own compulsory bytes
+    and the ncu-measured traffic are reported beside it."""
+    if not kt:
+        return None
+    name, (kms, kn) = max(kt.items(), key=lambda kv: kv[1][0])
+    per = kms / 1e3 / max(kn, 1)
+    tr = TRAFFIC_PER_CELL.get((model, prec, name))
+    out = {"kernel": name, "launch_ms": per * 1e3, "share": kms / sum(v[0] for v in kt.values()),
+           "traffic": tr * cells if tr else None}
+    fl = FLOPS_PER_CELL.get((model, prec, name))
+    if prec == "fp64" and fl:
+        ach = fl * cells / per / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "flops_per_cell": fl,
+                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (1.19 measured)"})
+    else:
+        ach = b_alg * cells / per / 1e9
+        kb = kernel_bytes(name, nv, esize)
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "bytes_per_cell": b_alg, "kernel_bytes_per_cell": kb,
+                    "kernel_frac": kb * cells / per / 1e9 / hbm, "peak_source": hbm_src})
+    return out
+
+
 def cpu_baseline(args, budget_s=15.0):
     """The FP64 oracle as it stands, on the host cores, on a bounded crop of the
     same workload (a 384 x 384 window around the source, as many steps as fit)."""
@@ -297,26 +340,8 @@ def main():
     launches = s.launches_per_step() * args.steps
 
     # dominant kernel and its roofline
-    dom = max(kt.items(), key=lambda kv: kv[1][0]) if kt else None
-    roof = None
-    if dom:
-        name, (kms, kn) = dom
-        per_launch_s = kms / 1e3 / max(kn, 1)
-        fl = FLOPS_PER_CELL.get((args.model, args.precision, name))
-        if fl:
-            peak = FP64_PEAK_TFLOPS if prec == 0 else FP32_PEAK_TFLOPS
-            ach = fl * cells / per_launch_s / 1e12
-            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
-                    "peak_source": "derived from SM count x FP64/FP32 FMA rate x max clock"}
-        else:
-            byts = kernel_bytes(name, nv, esize) * cells
-            ach = byts / per_launch_s / 1e9
-            roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": None, "peak_source": hbm_src}
-        roof["launch_ms"] = per_launch_s * 1e3
-        roof["share"] = kms / sum(v[0] for v in kt.values())
-    b_alg = (nv * 2 * esize + esize + 1)
+    b_alg = (nv * 2 * esize + esize + 1)   # algorithmic bytes per cell-update of the step
+    roof = roofline(args.model, args.precision, kt, cells, b_alg, nv, esize, hbm, hbm_src)
     step_hbm_frac = value / ws * b_alg / (hbm * 1e9)
 
     # end to end through the C ABI with pinned host buffers
@@ -351,6 +376,8 @@ def main():
         ms2 = reduce_max(ms2, ws)
         v2 = cells * a2.steps * ws / (ms2 / 1e3)
         extra = {"value": v2, "unit": UNIT, "steps": a2.steps, "ms_per_step": ms2 / a2.steps,
+                 "dtype": "f64",
+                 "roofline": roofline(args.model, "fp64", kt2, cells, nv * 16 + 9, nv, 8, hbm, hbm_src),
                  "hbm_fraction_step": v2 / ws * (nv * 16 + 9) / (hbm * 1e9),
                  "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt2.items() if v[1]}}
         del s2

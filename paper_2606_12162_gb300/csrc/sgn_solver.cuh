@@ -67,7 +67,9 @@ class Solver : public SolverBase {
   static constexpr int NP = PT<MODEL>::NP;
   static constexpr int NF = FT<MODEL>::NF;
   static constexpr int FXB = 64, FXY = 4;   // x-face block
-  static constexpr int FYB = 16, FYY = 16;  // y-face block
+  // y-face block: rows of 128 bytes; the FP64 records would exceed 48 KB of
+  // static shared memory at 32 x 16
+  static constexpr int FYB = sizeof(Real) == 4 ? 32 : 16, FYY = 16;
 
   Dev<Real> d_{};
   sgn_allocator al_{};
