@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsgn_gb300.so")
-UNITS = ["sgn_f64.cu", "sgn_mixed.cu", "sgn_capi.cu", "sgn_noalloc.cu"]
+UNITS = ["sgn_f64.cu", "sgn_mixed.cu", "sgn_capi.cu", "sgn_noalloc.cu", "lc_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -25,8 +25,9 @@ def nvcc():
 
 
 def _sources():
+    inc = os.path.join(os.path.dirname(HERE), "include")
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".map"))] + \
-        [os.path.join(os.path.dirname(HERE), "include", "sgn.h")]
+        [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
 
 
 def up_to_date():

@@ -20,10 +20,10 @@ def lib():
     return sgn, sgn.load()
 
 
-def header_functions():
-    src = open(HEADER).read()
+def header_functions(prefix="sgn_", header=HEADER):
+    src = open(header).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sgn_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(%s[a-z0-9_]+)\s*\(" % prefix, src)))
 
 
 def test_header_declares_the_abi():
@@ -32,14 +32,15 @@ def test_header_declares_the_abi():
         assert required in fns
 
 
-def test_library_exports_exactly_the_header(lib):
-    from paper_2606_12162_gb300 import sgn
+def test_library_exports_exactly_the_headers(lib):
+    from paper_2606_12162_gb300 import corrector, sgn
     out = subprocess.run(["nm", "-D", "--defined-only", sgn.LIB_PATH], capture_output=True, text=True).stdout
-    exported = sorted(set(re.findall(r"\bT (sgn_[a-z_]+)$", out, flags=re.M)))
-    assert exported == header_functions()
+    exported = sorted(set(re.findall(r"\bT ([a-z]+_[a-z0-9_]+)$", out, flags=re.M)))
+    declared = header_functions("sgn_") + header_functions("lc_", os.path.join(ROOT, "include", "lc.h"))
+    assert exported == sorted(declared)
     # every declared entry point resolves through ctypes and has a binding signature
-    names = {n for n, _, _ in sgn.SIGNATURES}
-    for fn in header_functions():
+    names = {n for n, _, _ in sgn.SIGNATURES} | {n for n, _, _ in corrector.LC_SIGS}
+    for fn in declared:
         getattr(lib[1], fn)
         assert fn in names
 

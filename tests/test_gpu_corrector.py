@@ -1,0 +1,95 @@
+"""Learned corrector on the GPU: its forward/backward kernels against the FP64
+NumPy reference, its data kernels against NumPy, and what the trained network
+gains over the plain prolongation on held-out scenarios (with the fallback to
+the fine solve where its error exceeds the bound)."""
+import numpy as np
+import pytest
+
+from paper_2606_12162_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_12162_gb300 import build, corrector
+    build.build()
+    corrector.lib()
+    return corrector
+
+
+def test_gradients_match_fp64_reference(C):
+    import torch
+    from oracle import conv_ref as R
+    rng = np.random.default_rng(3)
+    net = C.Net(cin=5, width=8, depth=3, r=2, nout=3, max_hw=64 * 64, seed=7)
+    p = net.params()
+    x = rng.standard_normal((5, 20, 24)).astype(np.float32)
+    t = rng.standard_normal((3, 40, 48)).astype(np.float32)
+    fw = (1.0, 0.3, 0.3)
+    loss, g = net.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), 0.0, fw, want_grad=True)
+    # the kernels use BF16 weights and FP32 biases
+    pr = p.astype(np.float64)
+    off = 0
+    for ci, co in net.layers():
+        pr[off:off + ci * co * 9] = R.bf16_round(p[off:off + ci * co * 9])
+        off += ci * co * 9 + co
+    lref, gref = R.loss_and_grad(pr, net.layers(), x, t, 2, 3, fw)
+    assert abs(loss - lref) <= 1e-5 * lref
+    assert np.abs(g - gref).max() <= 1e-4 * np.abs(gref).max()
+    # forward alone
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    yref = R.forward(pr, net.layers(), x)[-1]
+    assert np.abs(y - yref).max() <= 1e-5 * np.abs(yref).max()
+
+
+def test_data_kernels(C):
+    import torch
+    L = C.lib()
+    rng = np.random.default_rng(4)
+    nc, r = 12, 4
+    qc = rng.standard_normal((3, nc, nc))
+    qf = rng.standard_normal((3, nc * r, nc * r))
+    b = rng.uniform(-100, 20, (nc, nc))
+    phi = (b < -30).astype(np.uint8)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x = torch.empty((5, nc, nc), dtype=torch.float32, device="cuda")
+    assert L.lc_make_input(C._p(d(qc)), C._p(d(b)), C._p(d(phi)), nc, nc, 2.0, 50.0, 100.0, C._p(x), None) == 0
+    t = torch.empty((3, nc * r, nc * r), dtype=torch.float32, device="cuda")
+    assert L.lc_make_target(C._p(d(qf)), C._p(d(qc)), nc, nc, r, 2.0, 50.0, C._p(t), None) == 0
+    y = torch.from_numpy(rng.standard_normal((3 * r * r, nc, nc)).astype(np.float32)).cuda()
+    out = torch.empty((3, nc * r, nc * r), dtype=torch.float64, device="cuda")
+    assert L.lc_apply(C._p(d(qc)), C._p(y), nc, nc, r, 2.0, 50.0, 1, C._p(out), None) == 0
+    fine = torch.from_numpy(qf[0].copy()).cuda()
+    co = torch.empty((nc, nc), dtype=torch.float64, device="cuda")
+    assert L.lc_restrict(C._p(fine), nc, nc, r, C._p(co), None) == 0
+    torch.cuda.synchronize()
+    xr = np.stack([np.where(b < 0, qc[0], 0) / 2.0, qc[1] / 50.0, qc[2] / 50.0, b / 100.0, phi])
+    assert np.allclose(x.cpu().numpy(), xr, rtol=1e-6, atol=1e-7)
+    P = np.repeat(np.repeat(qc, r, axis=1), r, axis=2)
+    s = np.array([2.0, 50.0, 50.0])[:, None, None]
+    assert np.allclose(t.cpu().numpy(), (qf - P) / s, rtol=1e-6, atol=1e-6)
+    from oracle import conv_ref as R
+    assert np.allclose(out.cpu().numpy(), P + s * R.shuffle(y.cpu().numpy().astype(np.float64), r, 3), rtol=1e-12)
+    assert np.allclose(co.cpu().numpy(), qf[0].reshape(nc, r, nc, r).mean(axis=(1, 3)), rtol=1e-13)
+
+
+def test_trained_corrector_gains_over_prolongation(C):
+    """Coarse 64^2 at 2 km, fine 256^2 at 500 m (ratio 4) over a seeded fractal
+    bathymetry: 6 training scenarios x 3 snapshots, 2 held-out scenarios.  The
+    trained network must bring eta closer to the fine solve than the plain
+    prolongation on every held-out snapshot (relative L2), and the hybrid with
+    the fine solve on the blocks over the bound is no worse than the network."""
+    pairs, meta = C.generate_pairs(nc=64, r=4, dxc=2000.0, scenarios=range(8), times=(60.0, 120.0, 180.0))
+    train = [p for p in pairs if p["scenario"] < 6]
+    held = [p for p in pairs if p["scenario"] >= 6]
+    net = C.Net(cin=5, width=16, depth=4, r=4, nout=3, max_hw=64 * 64, seed=11)
+    losses = C.train(net, train, iters=800, crop=32, lr=2e-3)
+    assert losses[-50:].mean() < 0.5 * losses[:50].mean()
+    rows = C.evaluate(net, held, block=8, bound=0.1)
+    for r_ in rows:
+        assert r_["err_net"] < r_["err_prolong"], r_
+        assert r_["err_hybrid"] <= r_["err_net"] + 1e-12, r_
