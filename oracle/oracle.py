@@ -82,6 +82,17 @@ def lib():
             L.or_source.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.or_psi.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.or_psi.restype = ctypes.c_double
+            L.or_create_frame.restype = ctypes.c_void_p
+            L.or_create_frame.argtypes = [ctypes.POINTER(Config), dp, ctypes.c_void_p]
+            L.or_set_frame.argtypes = [ctypes.c_void_p, dp, ctypes.c_double]
+            L.or_get_frame.argtypes = [ctypes.c_void_p, dp]
+            L.or_step_begin.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.or_step_end.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.or_get_theta.argtypes = [ctypes.c_void_p, dp]
+            L.or_set_theta.argtypes = [ctypes.c_void_p, dp]
+            L.or_face_mass.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+            L.or_max_speed.argtypes = [ctypes.c_void_p]
+            L.or_max_speed.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -183,6 +194,68 @@ class Oracle:
         out = np.empty((max(n, 1), self._ng, 4))
         lib().or_gauges(self.h, _dp(out), out.size)
         return out[:n]
+
+
+
+class Patch:
+    """One patch of a refined level in patch mode: the caller owns the ghost
+    frame.  Frame arrays are (ny+4, nx+4) per field (two ghost layers)."""
+
+    NG = 2
+
+    def __init__(self, b_frame, phi_frame, **cfg):
+        b_frame = np.ascontiguousarray(b_frame, dtype=np.float64)
+        self.nyp, self.nxp = b_frame.shape
+        self.nx, self.ny = self.nxp - 2 * self.NG, self.nyp - 2 * self.NG
+        self.cfg = make_config(self.nx, self.ny, **cfg)
+        self._b = b_frame
+        self._phi = np.ascontiguousarray(phi_frame, dtype=np.uint8)
+        self.h = lib().or_create_frame(ctypes.byref(self.cfg), _dp(self._b), self._phi.ctypes.data)
+        if not self.h:
+            raise ValueError("or_create_frame rejected the configuration")
+        self.nvar = lib().or_nvar(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_destroy(self.h)
+            self.h = None
+
+    def set_frame(self, q, t=0.0):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        assert q.shape == (self.nvar, self.nyp, self.nxp)
+        lib().or_set_frame(self.h, _dp(q), float(t))
+
+    def get_frame(self):
+        q = np.empty((self.nvar, self.nyp, self.nxp))
+        lib().or_get_frame(self.h, _dp(q))
+        return q
+
+    def step_begin(self, dt):
+        return lib().or_step_begin(self.h, float(dt))
+
+    def step_end(self, dt):
+        return lib().or_step_end(self.h, float(dt))
+
+    def get_theta(self):
+        th = np.empty((self.nyp, self.nxp))
+        lib().or_get_theta(self.h, _dp(th))
+        return th
+
+    def set_theta(self, th):
+        th = np.ascontiguousarray(th, dtype=np.float64)
+        lib().or_set_theta(self.h, _dp(th))
+
+    def face_mass(self, d):
+        out = np.empty((self.ny, self.nx + 1) if d == 0 else (self.ny + 1, self.nx))
+        lib().or_face_mass(self.h, d, _dp(out))
+        return out
+
+    def max_speed(self):
+        return lib().or_max_speed(self.h)
+
+    @property
+    def status(self):
+        return lib().or_status(self.h)
 
 
 def eigvecs(model, roe, s1, sN, g=9.81):

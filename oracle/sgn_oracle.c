@@ -69,6 +69,7 @@ struct or_solver {
   double* theta;             /* padded */
   double t, last_dt, max_courant;
   unsigned status;
+  int frame;                 /* ghost frame given by the caller (patch of a refined level) */
   int ngauge, gcap, grec;
   int* gidx;
   double* grec_buf;
@@ -135,6 +136,7 @@ static int bc_map(int i, int n, int bcl, int bcr, int* flip) {
 /* Fill the ghost frame of nf padded arrays; vector fields hu (index 1) and hv
  * (index 2) are negated across reflecting walls when is_state is set. */
 static void fill_ghosts(or_solver* s, double* base, int nf, int is_state) {
+  if (s->frame) return;
   size_t np = (size_t)s->nxp * s->nyp;
   for (int J = 0; J < s->nyp; J++)
     for (int I = 0; I < s->nxp; I++) {
@@ -153,6 +155,7 @@ static void fill_ghosts(or_solver* s, double* base, int nf, int is_state) {
 }
 
 static void fill_ghosts_u8(or_solver* s, unsigned char* a) {
+  if (s->frame) return;
   for (int J = 0; J < s->nyp; J++)
     for (int I = 0; I < s->nxp; I++) {
       int inx = (I >= NG && I < NG + s->c.nx), iny = (J >= NG && J < NG + s->c.ny);
@@ -601,11 +604,14 @@ double or_dt_cfl(or_solver* s) {
   return s->c.cfl / smax;
 }
 
-/* One time step: S(dt/2) H(dt) S(dt/2) (Strang) or H(dt) S(dt) (Lie), Sec. 4. */
-static int step_once(or_solver* s, double dt) {
+/* One time step: S(dt/2) H(dt) S(dt/2) (Strang) or H(dt) S(dt) (Lie), Sec. 4,
+ * in two phases: step_begin runs everything up to the positivity factors,
+ * step_end the update and the second source step.  A patch of a refined level
+ * exchanges the factors of its ghost cells in between. */
+static void step_begin(or_solver* s, double dt) {
   int nx = s->c.nx, ny = s->c.ny, nxp = s->nxp, nyp = s->nyp, nv = s->f.nv;
   double dtdx = dt / s->c.dx, dtdy = dt / s->c.dy;
-  double tau1 = s->c.strang ? 0.5 * dt : 0.0, tau2 = s->c.strang ? 0.5 * dt : dt;
+  double tau1 = s->c.strang ? 0.5 * dt : 0.0;
 
   /* 1. ghost cells, 2. first source half step on every cell */
   fill_ghosts(s, s->q, nv, 1);
@@ -705,6 +711,12 @@ static int step_once(or_solver* s, double dt) {
       double h = fld(s, 0)[id] - s->b[id]; if (h < 0.0) h = 0.0;
       s->theta[id] = out > h ? h / out : 1.0;
     }
+}
+
+static int step_end(or_solver* s, double dt) {
+  int nx = s->c.nx, ny = s->c.ny, nxp = s->nxp, nv = s->f.nv;
+  double dtdx = dt / s->c.dx, dtdy = dt / s->c.dy;
+  double tau2 = s->c.strang ? 0.5 * dt : dt;
 
   /* 7. conservative update of the interior cells (Sec. 4, wave propagation
    * form; the mass row in flux form so that it telescopes) */
@@ -769,6 +781,11 @@ static int step_once(or_solver* s, double dt) {
   return (s->status & (OR_ST_NEGDEPTH | OR_ST_NONFINITE | OR_ST_CFL | OR_ST_NONHYP | OR_ST_ALLDRY)) ? -1 : 0;
 }
 
+static int step_once(or_solver* s, double dt) {
+  step_begin(s, dt);
+  return step_end(s, dt);
+}
+
 int or_step(or_solver* s, int nsteps) {
   for (int n = 0; n < nsteps; n++) {
     double dt = or_dt_cfl(s);
@@ -820,6 +837,124 @@ int or_gauges(const or_solver* s, double* out, size_t cap) {
 }
 
 /* ---- pieces exposed for the pin tests ---------------------------------- */
+/* ------------------------------------------------------------------------- */
+/* Patch mode (block-structured refinement of Sec. 4): the caller owns the
+ * ghost frame.  b_frame and phi_frame cover the padded patch, (ny+4) x (nx+4)
+ * cells; c^2 = alpha^2 g max(-b, 0) phi_T of every cell (reading G1). */
+or_solver* or_create_frame(const or_config* cfg, const double* b_frame, const unsigned char* phi_frame) {
+  if (!cfg || !b_frame || !phi_frame) return NULL;
+  if (cfg->nx < 2 || cfg->ny < 2 || !(cfg->dx > 0) || !(cfg->dy > 0)) return NULL;
+  if (cfg->model < 0 || cfg->model > 2) return NULL;
+  or_solver* s = (or_solver*)calloc(1, sizeof *s);
+  s->c = *cfg;
+  s->frame = 1;
+  s->f = model_fields(cfg->model);
+  s->nxp = cfg->nx + 2 * NG; s->nyp = cfg->ny + 2 * NG;
+  size_t np = (size_t)s->nxp * s->nyp;
+  s->q = (double*)calloc(np * s->f.nv, sizeof(double));
+  s->b = (double*)calloc(np, sizeof(double));
+  s->c2 = (double*)calloc(np, sizeof(double));
+  s->phi = (unsigned char*)calloc(np, 1);
+  s->theta = (double*)calloc(np, sizeof(double));
+  s->fx = (face_t*)calloc((size_t)(s->nxp + 1) * s->nyp, sizeof(face_t));
+  s->fy = (face_t*)calloc((size_t)s->nxp * (s->nyp + 1), sizeof(face_t));
+  if (!s->q || !s->b || !s->c2 || !s->phi || !s->theta || !s->fx || !s->fy) { or_destroy(s); return NULL; }
+  for (size_t i = 0; i < np; i++) {
+    s->b[i] = b_frame[i];
+    s->phi[i] = phi_frame[i] ? 1 : 0;
+    double H = -s->b[i]; if (H < 0.0) H = 0.0;
+    s->c2[i] = s->c.alpha * s->c.alpha * s->c.g * H * (double)s->phi[i];
+    s->q[i] = s->b[i] > 0 ? s->b[i] : 0.0;
+  }
+  return s;
+}
+
+/* The whole padded state (nv fields of (ny+4) x (nx+4)), copied as given. */
+int or_set_frame(or_solver* s, const double* q, double t) {
+  if (!s || !q) return -1;
+  memcpy(s->q, q, sizeof(double) * (size_t)s->f.nv * s->nxp * s->nyp);
+  s->t = t;
+  return 0;
+}
+
+int or_get_frame(const or_solver* s, double* q) {
+  if (!s || !q) return -1;
+  memcpy(q, s->q, sizeof(double) * (size_t)s->f.nv * s->nxp * s->nyp);
+  return 0;
+}
+
+int or_step_begin(or_solver* s, double dt) {
+  if (!s || !(dt > 0)) return -1;
+  step_begin(s, dt);
+  return 0;
+}
+
+int or_step_end(or_solver* s, double dt) {
+  if (!s || !(dt > 0)) return -1;
+  return step_end(s, dt);
+}
+
+/* Positivity factors of the padded cells (1 outside the interior unless set). */
+int or_get_theta(const or_solver* s, double* th) {
+  if (!s || !th) return -1;
+  memcpy(th, s->theta, sizeof(double) * (size_t)s->nxp * s->nyp);
+  return 0;
+}
+
+int or_set_theta(or_solver* s, const double* th) {
+  if (!s || !th) return -1;
+  memcpy(s->theta, th, sizeof(double) * (size_t)s->nxp * s->nyp);
+  return 0;
+}
+
+/* Mass flux through the faces of the interior cells as the update applies it:
+ * theta of the cell the water leaves times (M + the transverse mass term).
+ * dir 0: x faces, ny rows of nx+1 faces (face i between cells i-1 and i);
+ * dir 1: y faces, ny+1 rows of nx faces.  Valid after or_step_begin (and the
+ * exchange of theta), until the next step. */
+int or_face_mass(const or_solver* s, int dir, double* out) {
+  if (!s || !out || dir < 0 || dir > 1) return -1;
+  int nx = s->c.nx, ny = s->c.ny, nxp = s->nxp;
+  if (dir == 0) {
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i <= nx; i++) {
+        int I = i + NG, J = j + NG;
+        const face_t* F = &s->fx[(size_t)J * (nxp + 1) + I];
+        double M = F->M + F->Pt[0];
+        double t = M > 0 ? s->theta[cidx(s, I - 1, J)] : (M < 0 ? s->theta[cidx(s, I, J)] : 1.0);
+        out[(size_t)j * (nx + 1) + i] = t * M;
+      }
+  } else {
+    for (int j = 0; j <= ny; j++)
+      for (int i = 0; i < nx; i++) {
+        int I = i + NG, J = j + NG;
+        const face_t* F = &s->fy[(size_t)J * nxp + I];
+        double M = F->M + F->Pt[0];
+        double t = M > 0 ? s->theta[cidx(s, I, J - 1)] : (M < 0 ? s->theta[cidx(s, I, J)] : 1.0);
+        out[(size_t)j * nx + i] = t * M;
+      }
+  }
+  return 0;
+}
+
+/* Largest cell speed max((|u| + C_e)/dx, (|v| + C_e)/dy) over the wet interior
+ * cells, Eq. (eigenvalue_bound) (0 if none is wet). */
+double or_max_speed(or_solver* s) {
+  double smax = 0.0;
+  for (int J = NG; J < NG + s->c.ny; J++)
+    for (int I = NG; I < NG + s->c.nx; I++) {
+      cell_t c = load_cell(s, I, J);
+      if (!c.wet) continue;
+      double c2e = fast_speed2(s->c.g, c.h, c.p, c.c2);
+      if (c2e < 0) { s->status |= OR_ST_NONHYP; c2e = 0; }
+      double C = sqrt(c2e);
+      double sx = (fabs(c.vel[0]) + C) / s->c.dx, sy = (fabs(c.vel[1]) + C) / s->c.dy;
+      double sp = sx > sy ? sx : sy;
+      if (sp > smax) smax = sp;
+    }
+  return smax;
+}
+
 int or_eigvecs(int model, const double* roe, double g, double s1, double sN, double* R) {
   fields_t f = model_fields(model);
   roe_t r = {roe[0], roe[7], {roe[1], roe[2]}, roe[3], roe[4], roe[5], roe[6]};

@@ -70,6 +70,24 @@ int or_add_gauges(or_solver* s, const double* xy, int n, int capacity);
 /* records: [rec][gauge][t, eta, hu, hv]; returns the number of records. */
 int or_gauges(const or_solver* s, double* out, size_t cap);
 
+/* ---- patch mode: one patch of a refined level (block-structured AMR) ----
+ * The caller owns the ghost frame: arrays cover the padded patch of
+ * (ny+4) x (nx+4) cells (two ghost layers), row-major, field-major for states.
+ * A step is or_step_begin (source, faces, limiters, transverse terms,
+ * positivity factors of the interior) then or_step_end (update, second source
+ * step); ghost-cell factors may be exchanged in between (or_get/set_theta). */
+or_solver* or_create_frame(const or_config* cfg, const double* b_frame, const unsigned char* phi_frame);
+int or_set_frame(or_solver* s, const double* q, double t);
+int or_get_frame(const or_solver* s, double* q);
+int or_step_begin(or_solver* s, double dt);
+int or_step_end(or_solver* s, double dt);
+int or_get_theta(const or_solver* s, double* theta);
+int or_set_theta(or_solver* s, const double* theta);
+/* theta-weighted mass flux at the faces of the interior cells (dir 0: ny x
+ * (nx+1) x faces, dir 1: (ny+1) x nx y faces). */
+int or_face_mass(const or_solver* s, int dir, double* out);
+double or_max_speed(or_solver* s);
+
 /* ---- single-face and single-cell pieces, exposed for the pin tests ---- */
 
 /* Right eigenvector matrix (App. C, columns are the waves, rows the fields in the

@@ -234,3 +234,27 @@ def random_small_case(model, nx, ny, seed, dx=0.1, wetdry=True, amp=0.2):
         q[fi["hs"]] = np.where(wet, h * 0.02 * np.cos(x + y), 0.0)
         q[fi["hpb"]] = np.where(wet, h * 0.03 * np.sin(x * y), 0.0)
     return b, q
+
+
+def amr_small_case(model, nx0, ny0, r, nlevels, seed, dx0=0.2, wetdry=True, amp=0.2):
+    """Seeded input of a small refined hierarchy: random_small_case on the finest
+    grid (nx0 r^(L-1) x ny0 r^(L-1), spacing dx0 / r^(L-1)) and, for every level,
+    the state on that level's full grid as r x r block means of the next finer
+    one.  Returns (b_finest, [q_0, ..., q_{L-1}])."""
+    R = r ** (nlevels - 1)
+    b, q = random_small_case(model, nx0 * R, ny0 * R, seed, dx=dx0 / R, wetdry=wetdry, amp=amp)
+    qs = [q]
+    for _ in range(nlevels - 1):
+        f = qs[0]
+        nv, ny, nx = f.shape
+        qs.insert(0, f.reshape(nv, ny // r, r, nx // r, r).mean(axis=(2, 4)))
+    return b, qs
+
+
+def amr_boxes_small():
+    """A three-level hierarchy (ratio 2) over a 24 x 20 level-0 grid: two level-1
+    patches sharing a face plus a third one touching the domain boundary, and a
+    level-2 patch in each of the first two (boxes in each level's cell indices)."""
+    lvl1 = [(8, 8, 16, 12), (24, 8, 8, 12), (0, 28, 12, 12)]
+    lvl2 = [(20, 20, 16, 12), (52, 20, 8, 8)]
+    return [lvl1, lvl2]

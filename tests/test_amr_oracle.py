@@ -1,0 +1,179 @@
+"""Pins of the refined-hierarchy oracle (oracle/amr_oracle.py) against facts that
+do not depend on it: a one-level hierarchy is the uniform oracle; a finer level
+covering the whole domain is the uniform fine oracle stepped r times as often;
+lake at rest over wet/dry bathymetry; exact mass with walls (and that dropping
+the reflux breaks it); mirror symmetry; a refined patch brings the solution
+closer to the uniform fine grid."""
+import numpy as np
+import pytest
+
+from paper_2606_12162_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def A(oracle_mod):
+    from oracle import amr_oracle
+    return amr_oracle
+
+
+CFG = dict(h_star=0.0, dry_tol=1e-3, alpha=3.0)
+
+
+def _interior(am, l, k):
+    return am.patch_state(l, k)
+
+
+def test_one_level_is_the_uniform_oracle(A, oracle_mod):
+    b, qs = W.amr_small_case(2, 20, 16, 2, 1, seed=1)
+    am = A.AmrOracle(b, 20, 16, 0.1, 2, [], model=2, bc=(0, 1, 0, 1), **CFG)
+    am.set_state(qs)
+    o = oracle_mod.Oracle(b, dx=0.1, model=2, bc=(0, 1, 0, 1), **CFG)
+    o.set_state(qs[0])
+    for _ in range(6):
+        assert am.dt_next == o.dt_cfl()
+        am.step(1)
+        assert o.step(1) == 0
+    assert np.array_equal(_interior(am, 0, 0), o.get_state()[0])
+
+
+@pytest.mark.parametrize("r", [2, 4])
+def test_fine_level_covering_the_domain_is_the_uniform_fine_grid(A, oracle_mod, r):
+    """Level 1 = the whole domain: its ghost cells are all boundary cells, so with
+    a fixed level-0 step dt it must equal the uniform fine oracle taking r steps
+    of dt / r, and level 0 must hold the block means of level 1."""
+    nx0, ny0 = 12, 10
+    b, qs = W.amr_small_case(2, nx0, ny0, r, 2, seed=2)
+    am = A.AmrOracle(b, nx0, ny0, 0.2, r, [[(0, 0, nx0 * r, ny0 * r)]], model=2, bc=(0, 0, 0, 0), **CFG)
+    am.set_state(qs)
+    o = oracle_mod.Oracle(b, dx=0.2 / r, model=2, bc=(0, 0, 0, 0), **CFG)
+    o.set_state(qs[1])
+    dt = 0.5 * am.dt_next
+    for _ in range(4):
+        assert am.step_dt(dt) == 0
+        for _ in range(r):
+            assert o.step_dt(dt / r) == 0
+    fine = _interior(am, 1, 0)
+    assert np.array_equal(fine, o.get_state()[0])
+    coarse = _interior(am, 0, 0)
+    mean = A.block_mean(fine[1], r)
+    assert np.array_equal(coarse[1], mean)
+
+
+def test_lake_at_rest_across_levels(A):
+    """Wet bathymetry under every patch edge (reading A10): eta = 0 and zero
+    momenta stay exact through interpolation, subcycling, reflux and
+    average-down."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
+    rest = []
+    for l, q in enumerate(qs):
+        z = np.zeros_like(q)
+        bl = b
+        for _ in range(2 - l):
+            bl = A.block_mean(bl, 2)
+        z[0] = np.maximum(bl, 0.0)
+        rest.append(z)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, bc=(0, 0, 1, 1), **CFG)
+    am.set_state(rest)
+    for _ in range(5):
+        assert am.step(1) == 0
+    for l, pats in enumerate(am.levels):
+        for k in range(len(pats)):
+            q = _interior(am, l, k)
+            i0, j0, nx, ny = pats[k]["box"]
+            bl = am.b[l][j0:j0 + ny, i0:i0 + nx]
+            assert np.abs(q[0] - np.maximum(bl, 0.0)).max() <= 1e-14
+            assert np.abs(q[1:]).max() <= 1e-14
+
+
+@pytest.mark.parametrize("model,wetdry", [(1, False), (2, True), (2, False)])
+def test_mass_is_exact_with_walls(A, model, wetdry):
+    b, qs = W.amr_small_case(model, 24, 20, 2, 3, seed=4, amp=0.3, wetdry=wetdry)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=model, bc=(0, 0, 0, 0), **CFG)
+    am.set_state(qs)
+    m0 = am.mass()
+    for _ in range(12):
+        assert am.step(1) == 0
+    # exact up to the water added where a refluxed cell would go dry (reading A7)
+    assert abs(am.mass() - m0 - am.clipped) <= 1e-13 * m0
+    if not wetdry:
+        assert am.clipped == 0.0
+    assert am.clipped <= 1e-4 * m0
+
+
+def test_mass_pin_detects_a_missing_reflux(A):
+    """Plant a mistake in the oracle (no reflux): the mass pin must fail."""
+    class NoReflux(A.AmrOracle):
+        def _build_registers(self):
+            super()._build_registers()
+            self.regs = [[] for _ in range(self.L)]
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=4, amp=0.3)
+    am = NoReflux(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, bc=(0, 0, 0, 0), **CFG)
+    am.set_state(qs)
+    m0 = am.mass()
+    for _ in range(12):
+        am.step(1)
+    assert abs(am.mass() - m0) > 1e-9 * m0
+
+
+def test_mirror_symmetry(A):
+    """x-mirror of bathymetry, state and boxes: the solution mirrors (hu flips)."""
+    nx0, ny0, r = 24, 16, 2
+    b, qs = W.amr_small_case(1, nx0, ny0, r, 3, seed=6)
+    bs = 0.5 * (b + b[:, ::-1])
+    qsym = []
+    for q in qs:
+        s = 0.5 * (q + q[:, :, ::-1])
+        s[1] = 0.5 * (q[1] - q[1, :, ::-1])
+        qsym.append(s)
+    # eta must stay above b after symmetrisation: use a rest state plus the symmetric hump
+    hb = []
+    for l in range(3):
+        bl = bs
+        for _ in range(2 - l):
+            bl = A.block_mean(bl, r)
+        hb.append(bl)
+    for l in range(3):
+        qsym[l][0] = np.maximum(qsym[l][0], hb[l])
+    lvl1 = [(8, 8, 12, 12), (28, 8, 12, 12)]
+    lvl2 = [(20, 20, 12, 8), (64, 20, 12, 8)]
+    am = A.AmrOracle(bs, nx0, ny0, 0.2, r, [lvl1, lvl2], model=1, bc=(0, 0, 0, 0), **CFG)
+    am.set_state(qsym)
+    for _ in range(6):
+        assert am.step(1) == 0
+    q0 = _interior(am, 0, 0)
+    assert np.abs(q0[0] - q0[0, :, ::-1]).max() <= 1e-13
+    assert np.abs(q0[1] + q0[1, :, ::-1]).max() <= 1e-13
+    a, c = _interior(am, 1, 0), _interior(am, 1, 1)
+    assert np.abs(a[0] - c[0, :, ::-1]).max() <= 1e-13
+    a, c = _interior(am, 2, 0), _interior(am, 2, 1)
+    assert np.abs(a[0] - c[0, :, ::-1]).max() <= 1e-13
+
+
+def test_refined_patch_approaches_the_fine_grid(A, oracle_mod):
+    """A level-1 patch (ratio 2) over the hump: the surface in the patch is closer
+    to the uniform fine solution than the uniform coarse solution is."""
+    nx0, ny0, r = 24, 24, 2
+    b, qs = W.amr_small_case(1, nx0, ny0, r, 2, seed=7, wetdry=False)
+    hump = np.unravel_index(np.argmax(qs[1][0] - b), b.shape)
+    jc, ic = int(hump[0]) // (2 * r) * r, int(hump[1]) // (2 * r) * r
+    i0 = min(max(ic - 8, 4), nx0 * r - 20)
+    j0 = min(max(jc - 8, 4), ny0 * r - 20)
+    box = (i0 - i0 % r, j0 - j0 % r, 16, 16)
+    am = A.AmrOracle(b, nx0, ny0, 0.2, r, [[box]], model=1, bc=(0, 0, 0, 0), **CFG)
+    am.set_state(qs)
+    fine = oracle_mod.Oracle(b, dx=0.2 / r, model=1, bc=(0, 0, 0, 0), **CFG)
+    fine.set_state(qs[1])
+    coarse = oracle_mod.Oracle(A.block_mean(b, r), dx=0.2, model=1, bc=(0, 0, 0, 0), **CFG)
+    coarse.set_state(qs[0])
+    dt = 0.8 * am.dt_next
+    for _ in range(8):
+        assert am.step_dt(dt) == 0
+        assert coarse.step_dt(dt) == 0
+        for _ in range(r):
+            assert fine.step_dt(dt / r) == 0
+    i0, j0, nx, ny = box
+    ref = fine.get_state()[0][0, j0:j0 + ny, i0:i0 + nx]
+    e_amr = np.linalg.norm(_interior(am, 1, 0)[0] - ref)
+    cprol = np.repeat(np.repeat(coarse.get_state()[0][0], r, 0), r, 1)[j0:j0 + ny, i0:i0 + nx]
+    e_coarse = np.linalg.norm(cprol - ref)
+    assert e_amr < 0.5 * e_coarse
