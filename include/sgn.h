@@ -165,6 +165,12 @@ int sgn_clear_gauges(sgn_solver* s);
  * the last step (any pointer may be NULL).  Synchronises the stream. */
 int sgn_status(sgn_solver* s, unsigned* flags, double* last_dt, double* max_courant);
 
+/* The CFL time step the next sgn_step will take (Eq. (eigenvalue_bound) and the
+ * CFL condition of Sec. 4, from the current state; 0 if every cell is dry), so
+ * that a caller can end a run exactly at an output time with sgn_step_dt.
+ * Synchronises the stream.  Errors: EINVAL. */
+int sgn_next_dt(sgn_solver* s, double* dt);
+
 /* Total mass sum(h) dx dy over the grid by a deterministic two-stage FP64
  * reduction.  Synchronises the stream. */
 int sgn_mass(sgn_solver* s, double* mass);

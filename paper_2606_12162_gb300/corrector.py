@@ -143,12 +143,27 @@ def source_state(model, b, dx, cx, cy, amp, rad):
     return q
 
 
+def scenario_source(bc, dxc, s):
+    """Source of scenario s (seed 5002 + s): centre of a coarse cell deeper than
+    1000 m, amplitude U[0.5, 5] m, radius U[10, 50] km."""
+    rng = np.random.default_rng(5002 + s)
+    deep = np.argwhere(bc < -1000.0)
+    j, i = deep[rng.integers(len(deep))]
+    return (i + 0.5) * dxc, (j + 0.5) * dxc, rng.uniform(0.5, 5.0), rng.uniform(10e3, 50e3)
+
+
 def generate_pairs(nc=512, r=4, dxc=2000.0, scenarios=range(40), times=(60.0, 120.0, 180.0, 240.0, 300.0),
-                   model=W.HSGN, precision=sgn.MIXED, seed=5001):
-    """Coarse/fine solver pairs: for each scenario (source seed 5002 + s: amplitude
-    U[0.5, 5] m, radius U[10, 50] km, centre over water deeper than 1000 m) run the
-    coarse (nc^2, dxc) and fine ((r nc)^2, dxc/r) solvers to each snapshot time and
-    keep (input, target, coarse state, fine state) on the device."""
+                   model=W.HSGN, precision=sgn.MIXED, seed=5001, keep_fine=None, gauges=0, stats=None):
+    """Coarse/fine solver pairs: for each scenario (scenario_source) run the
+    coarse (nc^2, dxc) and fine ((r nc)^2, dxc/r) solvers to each snapshot time
+    and keep (input, target, coarse state[, fine state]) on the device.
+
+    keep_fine(s) -> bool selects the scenarios whose fine eta, hu, hv are kept
+    (default: all).  With gauges > 0 both solvers record that many gauges
+    (gauge_positions, seed 5100 + s), returned per scenario in stats["gauges"].
+    stats (a dict) also receives the wall time and step count of every coarse
+    and fine advance, the scenarios kept ("ok") and those dropped because a
+    solve reported an error ("failed")."""
     import torch
     bf, bc = scenario_bathymetry(nc, r, seed)
     nf = nc * r
@@ -165,45 +180,129 @@ def generate_pairs(nc=512, r=4, dxc=2000.0, scenarios=range(40), times=(60.0, 12
     pairs = []
     L = lib()
     st = _stream()
+    if stats is not None:
+        for k in ("coarse_s", "fine_s", "coarse_steps", "fine_steps", "ok", "failed"):
+            stats.setdefault(k, [])
+        stats.setdefault("gauges", {})
     for s in scenarios:
-        rng = np.random.default_rng(5002 + s)
-        deep = np.argwhere(bc < -1000.0)
-        j, i = deep[rng.integers(len(deep))]
-        cx, cy = (i + 0.5) * dxc, (j + 0.5) * dxc
-        amp, rad = rng.uniform(0.5, 5.0), rng.uniform(10e3, 50e3)
+        cx, cy, amp, rad = scenario_source(bc, dxc, s)
         qf0 = source_state(model, bf, dxf, cx, cy, amp, rad)
         qc0 = np.zeros((nv, nc, nc))
         qc0[0] = qf0[0].reshape(nc, r, nc, r).mean(axis=(1, 3))
         sf.set_state(qf0)
         sc.set_state(qc0)
-        tnow = {id(sc): 0.0, id(sf): 0.0}
-        for T in times:
+        sf.cfl_dt = sc.cfl_dt = 0.0
+        if gauges:
+            gxy = gauge_positions(bc, dxc, cx, cy, gauges, 5100 + s)
             for sv in (sc, sf):
-                tnow[id(sv)] = advance_to(sv, tnow[id(sv)], T)
+                sv.clear_gauges()
+                sv.add_gauges(gxy, 4096)
+        tnow = {id(sc): 0.0, id(sf): 0.0}
+        mine, mypairs, failed = [], [], None
+        for T in times:
+            for sv, key in ((sc, "coarse"), (sf, "fine")):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                try:
+                    tnow[id(sv)], nst = advance_to(sv, tnow[id(sv)], T)
+                except sgn.SGNError as e:
+                    failed = dict(scenario=s, solver=key, target=T, error=str(e))
+                    break
+                torch.cuda.synchronize()
+                mine.append((key, time.perf_counter() - t0, nst))
+            if failed:
+                break
             sc.get_state_device(qc)
             sf.get_state_device(qf)
             x = torch.empty((5, nc, nc), dtype=torch.float32, device="cuda")
             tg = torch.empty((3, nf, nf), dtype=torch.float32, device="cuda")
             _ck(L.lc_make_input(_p(qc), _p(bcd), _p(phid), nc, nc, S_ETA, S_Q, S_B, _p(x), st), "lc_make_input")
             _ck(L.lc_make_target(_p(qf), _p(qc), nc, nc, r, S_ETA, S_Q, _p(tg), st), "lc_make_target")
-            pairs.append(dict(x=x, t=tg, qc=qc[:3].clone(), qf=qf[:3].clone(), scenario=s, time=T))
-    return pairs, dict(bc=bc, bf=bf, dxc=dxc, r=r)
+            keep = keep_fine is None or keep_fine(s)
+            mypairs.append(dict(x=x, t=tg, qc=qc[:3].clone(), qf=qf[:3].clone() if keep else None, scenario=s,
+                                time=T))
+        if failed:
+            # a scenario whose solve reports an error is dropped whole (and counted)
+            if stats is not None:
+                stats["failed"].append(failed)
+            continue
+        pairs.extend(mypairs)
+        if stats is not None:
+            for key, dt_, nst in mine:
+                stats[key + "_s"].append(dt_)
+                stats[key + "_steps"].append(nst)
+            stats["ok"].append(s)
+            if gauges:
+                stats["gauges"][s] = dict(xy=gxy, coarse=sc.gauges(), fine=sf.gauges())
+    sc.close()
+    sf.close()
+    return pairs, dict(bc=bc, bf=bf, dxc=dxc, r=r, phic=phic)
+
+
+def gauge_positions(bc, dxc, cx, cy, n, seed, rmin=20e3, rmax=150e3):
+    """n gauge positions: centres of coarse ocean cells (b < -100 m) 20-150 km
+    from the source, drawn with the given seed."""
+    nc = bc.shape[0]
+    x, y = W.cell_centres(nc, nc, dxc, dxc)
+    d = np.hypot(x - cx, y - cy)
+    jj, ii = np.nonzero((bc < -100.0) & (d > rmin) & (d < rmax))
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(len(ii), size=min(n, len(ii)), replace=False)
+    return np.stack([x[jj[pick], ii[pick]], y[jj[pick], ii[pick]]], axis=1)
+
+
+def arrival_times(rec, frac=0.1, floor=0.01):
+    """First recorded time at which |eta| at a gauge reaches max(frac x its
+    largest |eta|, floor [m]); NaN where it never does.
+    rec: [record][gauge][t, eta, hu, hv]."""
+    t = rec[:, :, 0]
+    e = np.abs(rec[:, :, 1])
+    thr = np.maximum(frac * e.max(axis=0), floor)
+    out = np.full(rec.shape[1], np.nan)
+    for g in range(rec.shape[1]):
+        k = np.nonzero(e[:, g] >= thr[g])[0]
+        if len(k) and e[:, g].max() >= floor:
+            out[g] = t[k[0], g]
+    return out
 
 
 def advance_to(sv, t, T):
-    """Step a solver from time t to exactly T: CFL steps while more than two
-    steps remain, then equal fixed steps of at most 0.9 x the last CFL step."""
+    """Step a solver from time t to exactly T without exceeding the CFL step.
+    Far from T, batches of CFL steps, each batch at most half the remaining
+    interval over the largest step seen (the step shrinks briefly when a thin
+    layer runs up a shore and then recovers, so the last step is no bound);
+    within two CFL steps of T, fixed steps no longer than the solver's next CFL
+    step.  A fresh state (cfl_dt reset to 0 on the solver object after
+    set_state) starts with a few single steps.  Returns (T, steps taken)."""
+    n = 0
+    dmax = getattr(sv, "cfl_dt", 0.0)
+    warm = 4 if dmax <= 0.0 else 0
     while T - t > 1e-9:
-        dtl = sv.status()[1]
-        if dtl <= 0.0 or T - t > 2.0 * dtl:
-            t = sv.step(1)
+        rem = T - t
+        if warm == 0 and dmax > 0.0 and rem > 4.0 * dmax:
+            k = max(1, int(0.5 * rem / dmax) - 1)
+            t = sv.step(k)
+            n += k
+            dmax = max(dmax, sv.status()[1])
+            if t > T + 1e-9:
+                raise RuntimeError("advance_to passed the target time (%.6g > %.6g)" % (t, T))
             continue
-        k = int(math.ceil((T - t) / (0.9 * dtl)))
-        h = (T - t) / k
-        for _ in range(k):
-            sv.step_dt(h)
-        t = T
-    return t
+        dn = sv.next_dt()
+        if dn <= 0.0:
+            raise RuntimeError("advance_to: no CFL step (every cell dry)")
+        if rem <= dn:
+            sv.step_dt(rem)
+            t = T
+        elif rem <= 2.0 * dn:
+            sv.step_dt(0.5 * rem)
+            t += 0.5 * rem
+        else:
+            t = sv.step(1)
+            dmax = max(dmax, sv.status()[1])
+            warm = max(0, warm - 1)
+        n += 1
+    sv.cfl_dt = dmax
+    return T, n
 
 
 def train(net, pairs, iters=2000, crop=64, lr=1e-3, seed=0, fw=(1.0, 1.0, 1.0), log=None):
@@ -286,3 +385,190 @@ def evaluate(net, pairs, block=8, bound=0.05, indicator_thr=0.02):
                          gain=e_p / max(e_n, 1e-300), fallback_frac=over.float().mean().item(),
                          indicator_frac=fb.float().mean().item(), indicator_recall=recall))
     return rows
+
+
+def correct(net, qc, bcd, phid, out=None):
+    """Fine-level eta, hu, hv (3, r nc, r nc) from a coarse device state qc (its
+    first three fields are read): input assembly, the network and the corrected
+    prolongation, all library kernels on the current stream."""
+    import torch
+    nc = qc.shape[-1]
+    r = net.r
+    x = torch.empty((5, nc, nc), dtype=torch.float32, device="cuda")
+    st = _stream()
+    L = lib()
+    _ck(L.lc_make_input(_p(qc), _p(bcd), _p(phid), nc, nc, S_ETA, S_Q, S_B, _p(x), st), "lc_make_input")
+    y = net.forward(x)
+    if out is None:
+        out = torch.empty((3, nc * r, nc * r), dtype=torch.float64, device="cuda")
+    _ck(L.lc_apply(_p(qc), _p(y), nc, nc, r, S_ETA, S_Q, 1, _p(out), st), "lc_apply")
+    return out
+
+
+def _rel_l2(a, b):
+    import torch
+    return (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+
+
+def experiment(nc=1024, r=4, dxc=2000.0, n_train=32, n_held=8, times=(60.0, 120.0, 180.0, 240.0, 300.0),
+               iters=6000, crop=128, lr=1e-3, width=32, depth=5, block=16, bound=0.1, gauges=64, fp64_check=True,
+               log=print):
+    """Generate the coarse/fine pairs, train the corrector on scenarios below
+    n_train, evaluate it on the others, and time the ways of getting the
+    fine-level surface at the snapshot times: the plain fine solve (mixed
+    precision), the plain fine solve in FP64 (first held-out scenario) and the
+    coarse solve plus the corrector.  Returns a dict of results."""
+    import torch
+    res = dict(nc=nc, r=r, nf=nc * r, dxc=dxc, n_train=n_train, n_held=n_held, times=list(times), iters=iters,
+               crop=crop, width=width, depth=depth, block=block, bound=bound)
+    stats = {}
+    t0 = time.perf_counter()
+    pairs, meta = generate_pairs(nc, r, dxc, range(n_train + n_held), times, keep_fine=lambda s: s >= n_train,
+                                 gauges=gauges, stats=stats)
+    res["generate_s"] = time.perf_counter() - t0
+    res["failed"] = stats["failed"]
+    ok = stats["ok"]
+    log("pairs: %d in %.1f s, dropped scenarios: %d" % (len(pairs), res["generate_s"], len(stats["failed"])))
+    trn = [p for p in pairs if p["scenario"] < n_train]
+    held = [p for p in pairs if p["scenario"] >= n_train]
+    if not trn or not held:
+        raise RuntimeError("no usable scenarios: %s" % res["failed"])
+    net = Net(cin=5, width=width, depth=depth, r=r, max_hw=nc * nc, seed=5000)
+    res["params"] = int(net.n)
+    t0 = time.perf_counter()
+    losses = train(net, trn, iters, crop, lr, log=log)
+    res["train_s"] = time.perf_counter() - t0
+    res["loss_first50"] = float(losses[:50].mean())
+    res["loss_last50"] = float(losses[-50:].mean())
+    rows = evaluate(net, held, block, bound)
+    res["rows"] = rows
+    for k in ("err_prolong", "err_net", "err_hybrid", "gain", "fallback_frac", "indicator_frac",
+              "indicator_recall"):
+        v = np.array([row[k] for row in rows])
+        res[k + "_median"] = float(np.median(v))
+        res[k + "_min"] = float(v.min())
+        res[k + "_max"] = float(v.max())
+    rel_p = [_rel_l2(predict_fine(net, p, False)[0], p["qf"][0]) for p in held]
+    rel_n = [_rel_l2(predict_fine(net, p, True)[0], p["qf"][0]) for p in held]
+    res["rel_l2_eta_prolong_median"] = float(np.median(rel_p))
+    res["rel_l2_eta_net_median"] = float(np.median(rel_n))
+    res["rel_l2_eta_net_max"] = float(np.max(rel_n))
+    # inference time per snapshot (input assembly, network, corrected prolongation)
+    bcd = torch.from_numpy(np.ascontiguousarray(meta["bc"])).cuda()
+    phid = torch.from_numpy(np.ascontiguousarray(meta["phic"])).cuda()
+    out = torch.empty((3, nc * r, nc * r), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        correct(net, held[0]["qc"], bcd, phid, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for k in range(reps):
+        correct(net, held[k % len(held)]["qc"], bcd, phid, out)
+    e1.record()
+    torch.cuda.synchronize()
+    t_inf = e0.elapsed_time(e1) / reps * 1e-3
+    res["inference_ms"] = t_inf * 1e3
+    res["inference_gflop"] = 2.0 * sum(ci * co * 9 for ci, co in net.layers()) * nc * nc * 1e-9
+    # throughput: fine-level cell-updates delivered per second of wall time
+    nt = len(times)
+    nsc = len(ok)
+    cs = np.array(stats["coarse_s"]).reshape(nsc, nt).sum(axis=1)
+    fs = np.array(stats["fine_s"]).reshape(nsc, nt).sum(axis=1)
+    cst = np.array(stats["coarse_steps"]).reshape(nsc, nt).sum(axis=1)
+    fst = np.array(stats["fine_steps"]).reshape(nsc, nt).sum(axis=1)
+    nf2 = float(nc * r) ** 2
+    fine_updates = nf2 * fst
+    res["fine_steps_median"] = float(np.median(fst))
+    res["coarse_steps_median"] = float(np.median(cst))
+    res["fine_mixed_cups"] = float(np.sum(fine_updates) / np.sum(fs))
+    learned_s = cs + nt * t_inf
+    res["learned_cups"] = float(np.sum(fine_updates) / np.sum(learned_s))
+    # fallback cost model: the fine solve over the fallback share of the domain
+    ff = res["fallback_frac_median"]
+    res["learned_with_fallback_cups"] = float(np.sum(fine_updates) / np.sum(learned_s + ff * fs))
+    # gauge arrival times, coarse vs fine (held-out scenarios)
+    if gauges:
+        d, dtc = [], []
+        for s in [v for v in ok if v >= n_train]:
+            g = stats["gauges"][s]
+            ta, tb = arrival_times(g["coarse"]), arrival_times(g["fine"])
+            keep = np.isfinite(ta) & np.isfinite(tb)
+            d.extend(np.abs(ta[keep] - tb[keep]).tolist())
+            dtc.append(float(np.median(np.diff(g["coarse"][:, 0, 0]))))
+        d = np.array(d)
+        res["arrival_gauges"] = int(d.size)
+        res["arrival_abs_diff_median_s"] = float(np.median(d)) if d.size else None
+        res["arrival_abs_diff_max_s"] = float(d.max()) if d.size else None
+        res["coarse_dt_median_s"] = float(np.median(dtc)) if dtc else None
+    # FP64 fine solve of the first held-out scenario
+    if fp64_check:
+        s = held[0]["scenario"]
+        cx, cy, amp, rad = scenario_source(meta["bc"], dxc, s)
+        bf = meta["bf"]
+        dxf = dxc / r
+        sv = sgn.Solver(bf, dx=dxf, model=W.HSGN, bc=(1, 1, 1, 1), h_star=20.0, alpha=3.0, precision=sgn.FP64)
+        sv.set_state(source_state(W.HSGN, bf, dxf, cx, cy, amp, rad))
+        sv.cfl_dt = 0.0
+        q64 = torch.empty((W.NVAR[W.HSGN], nc * r, nc * r), dtype=torch.float64, device="cuda")
+        tt, nst, wall = 0.0, 0, 0.0
+        e_mixed, e_net, e_pro = [], [], []
+        try:
+            for T, p in zip(times, [p for p in held if p["scenario"] == s]):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                tt, k = advance_to(sv, tt, T)
+                torch.cuda.synchronize()
+                wall += time.perf_counter() - t0
+                nst += k
+                sv.get_state_device(q64)
+                e_mixed.append(_rel_l2(p["qf"][0], q64[0]))
+                e_net.append(_rel_l2(predict_fine(net, p, True)[0], q64[0]))
+                e_pro.append(_rel_l2(predict_fine(net, p, False)[0], q64[0]))
+        except sgn.SGNError as e:
+            res["fp64_error"] = dict(scenario=s, time=tt, error=str(e))
+        sv.close()
+        if e_mixed:
+            res["fine_fp64_cups"] = nf2 * nst / wall
+            res["fp64_rel_l2_eta_fine_mixed_max"] = float(max(e_mixed))
+            res["fp64_rel_l2_eta_learned_max"] = float(max(e_net))
+            res["fp64_rel_l2_eta_prolong_max"] = float(max(e_pro))
+    res["weights"] = net.params()
+    return res
+
+
+def main(argv=None):
+    """Command line: run the corrector experiment and write a JSON summary
+    (and the trained FP32 parameters as .npy)."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--nc", type=int, default=1024)
+    ap.add_argument("--r", type=int, default=4)
+    ap.add_argument("--dxc", type=float, default=2000.0)
+    ap.add_argument("--train", type=int, default=32)
+    ap.add_argument("--held", type=int, default=8)
+    ap.add_argument("--iters", type=int, default=6000)
+    ap.add_argument("--crop", type=int, default=128)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--bound", type=float, default=0.1)
+    ap.add_argument("--gauges", type=int, default=64)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--out", default=None, help="JSON summary path")
+    ap.add_argument("--weights", default=None, help="trained parameters (.npy)")
+    a = ap.parse_args(argv)
+    res = experiment(nc=a.nc, r=a.r, dxc=a.dxc, n_train=a.train, n_held=a.held, iters=a.iters, crop=a.crop,
+                     lr=a.lr, block=a.block, bound=a.bound, gauges=a.gauges, fp64_check=not a.no_fp64,
+                     log=lambda m: print(m, flush=True))
+    w = res.pop("weights")
+    if a.weights:
+        np.save(a.weights, w)
+    txt = json.dumps(res, indent=1, default=float)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(txt)
+    print(json.dumps({k: v for k, v in res.items() if k != "rows"}, default=float))
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,11 @@ int sgn_status(sgn_solver* s, unsigned* flags, double* last_dt, double* max_cour
   return s->impl->status(flags, last_dt, max_courant);
 }
 
+int sgn_next_dt(sgn_solver* s, double* dt) {
+  if (!s || !s->impl || !dt) return SGN_EINVAL;
+  return s->impl->next_dt(dt);
+}
+
 int sgn_mass(sgn_solver* s, double* mass) {
   if (!s || !mass) return SGN_EINVAL;
   return s->impl->mass(mass);

@@ -32,6 +32,7 @@ struct SolverBase {
   virtual int gauges(double* out, size_t cap, int* nrec) = 0;
   virtual int clear_gauges() = 0;
   virtual int status(unsigned* f, double* dt, double* cr) = 0;
+  virtual int next_dt(double* dt) = 0;
   virtual int mass(double* m) = 0;
   virtual int get_aux(double* c2, unsigned char* phi) = 0;
   virtual int set_profiling(int on) = 0;
@@ -372,6 +373,13 @@ class Solver : public SolverBase {
     if (dt) *dt = hscal_[4];
     if (cr) *cr = hscal_[5];
     if (f) memcpy(f, hscal_ + 6, sizeof(unsigned));
+    return SGN_OK;
+  }
+
+  int next_dt(double* dt) override {
+    SGN_CK(cudaMemcpyAsync(hscal_ + 12, d_.dt, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    *dt = hscal_[12];
     return SGN_OK;
   }
 

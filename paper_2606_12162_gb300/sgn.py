@@ -74,6 +74,7 @@ SIGNATURES = [
     ("sgn_gauges", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
     ("sgn_clear_gauges", ctypes.c_int, [ctypes.c_void_p]),
     ("sgn_status", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint), DP, DP]),
+    ("sgn_next_dt", ctypes.c_int, [ctypes.c_void_p, DP]),
     ("sgn_mass", ctypes.c_int, [ctypes.c_void_p, DP]),
     ("sgn_get_aux", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.c_void_p]),
     ("sgn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -275,6 +276,12 @@ class Solver:
         cr = ctypes.c_double()
         _ck(load().sgn_status(self.h, ctypes.byref(f), ctypes.byref(dt), ctypes.byref(cr)), "sgn_status")
         return f.value, dt.value, cr.value
+
+    def next_dt(self):
+        """The CFL time step the next step() will take."""
+        dt = ctypes.c_double()
+        _ck(load().sgn_next_dt(self.h, ctypes.byref(dt)), "sgn_next_dt")
+        return dt.value
 
     def mass(self):
         m = ctypes.c_double()

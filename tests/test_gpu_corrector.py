@@ -93,3 +93,19 @@ def test_trained_corrector_gains_over_prolongation(C):
     for r_ in rows:
         assert r_["err_net"] < r_["err_prolong"], r_
         assert r_["err_hybrid"] <= r_["err_net"] + 1e-12, r_
+
+
+def test_experiment_pipeline_small(C):
+    """The whole experiment driver at a small size: pairs with gauges, training,
+    evaluation, inference timing, throughput figures and the FP64 fine check."""
+    res = C.experiment(nc=48, r=4, n_train=2, n_held=1, times=(60.0, 120.0), iters=60, crop=16, block=8,
+                       gauges=8, fp64_check=True, log=lambda m: None)
+    for k in ("err_net_median", "gain_median", "inference_ms", "fine_mixed_cups", "learned_cups",
+              "learned_with_fallback_cups", "fine_fp64_cups", "fp64_rel_l2_eta_fine_mixed_max",
+              "fp64_rel_l2_eta_learned_max"):
+        assert np.isfinite(res[k]) and res[k] >= 0.0, (k, res[k])
+    assert len(res["rows"]) == 2
+    assert res["fine_steps_median"] > res["coarse_steps_median"] > 0
+    # the mixed fine solve stays close to the FP64 fine solve
+    assert res["fp64_rel_l2_eta_fine_mixed_max"] < 1e-3
+    assert res["weights"].size == res["params"]

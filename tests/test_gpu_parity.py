@@ -248,6 +248,14 @@ def test_step_dt_matches_oracle(sgn, oracle_mod):
         assert o.step_dt(dt) == 0
     assert (rel_l2(s.get_state()[0], o.get_state()[0]) <= FP64_TOL).all()
 
+    # the next CFL step is reported before it is taken, equal to the oracle's
+    for _ in range(3):
+        dn = s.next_dt()
+        assert abs(dn - o.dt_cfl()) <= 1e-12 * dn
+        s.step(1)
+        assert o.step(1) == 0
+        assert s.status()[1] == dn
+
 
 def test_errors_reported(sgn):
     b, q = W.random_small_case(2, 32, 32, seed=3, dx=0.05, wetdry=False)
