@@ -1,0 +1,87 @@
+/*
+ * sgn_amr.h -- C ABI of the refined hierarchy: block-structured adaptive
+ * refinement (Berger-Oliger-Colella) of the explicit step, as the paper runs
+ * the method in GeoClaw (Sec. 4: patches with refinement ratio r and
+ * subcycling in time; refinement along the advancing front, Sec. 6.3).
+ *
+ * Every patch of a level is laid out in one padded "atlas" grid of that level
+ * (each patch with its own frame of two ghost layers), so that every stage of
+ * the step runs as ONE launch over all patches of the level, whatever their
+ * number and sizes; a level-0 step with all finer substeps is replayed as one
+ * CUDA graph.
+ *
+ * Definitions the paper leaves to GeoClaw (they are the library's readings):
+ *  - level 0 is one patch covering the grid; level l >= 1 holds disjoint boxes
+ *    (i0, j0, nx, ny) in level-l cell indices (spacing dx / r^l), aligned to
+ *    whole parent cells, each inside one level-(l-1) patch and at least two
+ *    parent cells from its edges except along the domain boundary;
+ *  - bathymetry of a coarser level is the mean of the r x r children of the
+ *    next finer level (the finest level's bathymetry is given);
+ *  - ghost cells: boundary condition (outside the domain), copy from another
+ *    patch of the level, or limited interpolation of surface and primitives
+ *    from the parent at the substep's time weight (a dry parent cell gives a
+ *    ghost at the still level);
+ *  - positivity factors of ghost cells copied from a patch are taken from it;
+ *  - mass is refluxed at coarse faces between covered and uncovered cells (a
+ *    correction that would leave a negative depth is clipped to zero depth and
+ *    the water added is reported); covered coarse cells hold the mean of their
+ *    children; dt_0 = min over levels of CFL r^l / (max cell speed of level l).
+ *
+ * Errors as in sgn.h (negative SGN_E* codes).  Periodic boundaries and dx != dy
+ * are rejected (SGN_EINVAL).
+ */
+#ifndef SGN_AMR_H
+#define SGN_AMR_H
+#include "sgn.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgn_amr sgn_amr;
+
+/* grid0: level-0 grid (nx, ny, dx = dy, boundary conditions wall or
+ * extrapolation).  b_finest: bathymetry of the finest level, (ny r^(L-1)) x
+ * (nx r^(L-1)) doubles, row-major (copied).  nlevels L in 1..8, ratio r in
+ * 2..8.  nboxes[l-1] boxes on level l = 1..L-1; boxes: 4 ints (i0, j0, nx, ny)
+ * per box, level by level.  model, params, allocator and stream as for
+ * sgn_create.  Errors: EINVAL (arguments, box rules), ENOMEM, ECUDA. */
+int sgn_amr_create(const sgn_grid* grid0, const double* b_finest, int nlevels, int ratio, const int* nboxes,
+                   const int* boxes, int model, const sgn_params* params, const sgn_allocator* allocator,
+                   void* cuda_stream, sgn_amr** out);
+void sgn_amr_destroy(sgn_amr* a);
+
+/* Number of patches of a level (level 0: 1), or EINVAL. */
+int sgn_amr_npatches(const sgn_amr* a, int level);
+
+/* State of one patch's interior: nvar x ny x nx doubles (field order of
+ * sgn.h), host memory.  set applies the SWE / dry switch; the first step after
+ * a set recomputes the time step from the new states and resets the time, the
+ * status and the clipped water.  Errors: EINVAL. */
+int sgn_amr_set_patch(sgn_amr* a, int level, int patch, const double* q);
+int sgn_amr_get_patch(sgn_amr* a, int level, int patch, double* q);
+
+/* n level-0 steps with the CFL step of all levels (subcycling below), or one
+ * level-0 step of the given dt0.  Return the status of the batch as an error
+ * code; *t_out (may be NULL) receives the level-0 time. */
+int sgn_amr_step(sgn_amr* a, int n, double* t_out);
+int sgn_amr_step_dt(sgn_amr* a, double dt0);
+/* The level-0 step the next sgn_amr_step will take. */
+int sgn_amr_next_dt(sgn_amr* a, double* dt0);
+
+/* Mass sum(h) dx^2 over the uncovered interior cells of every level (FP64,
+ * fixed order), and the water added by clipped reflux corrections since the
+ * last set (either pointer may be NULL).  Synchronises the stream. */
+int sgn_amr_mass(sgn_amr* a, double* mass, double* clipped);
+/* OR of the status words of all levels (bits of sgn.h). */
+int sgn_amr_status(sgn_amr* a, unsigned* flags);
+/* Per level (L entries each, either pointer may be NULL): interior cells of all
+ * patches and cells of the level's atlas grid (padding and frames included). */
+int sgn_amr_info(const sgn_amr* a, long long* cells, long long* atlas_cells);
+/* Kernel launches in one level-0 step (all levels); 0 before the first step. */
+int sgn_amr_launches_per_step(const sgn_amr* a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

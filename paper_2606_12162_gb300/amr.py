@@ -1,0 +1,155 @@
+"""Python binding of include/sgn_amr.h (the refined hierarchy): ctypes
+marshalling only; every stage runs in the library's kernels."""
+import ctypes
+
+import numpy as np
+
+from . import sgn
+
+DP = ctypes.POINTER(ctypes.c_double)
+AMR_SIGS = [
+    ("sgn_amr_create", ctypes.c_int, [ctypes.POINTER(sgn.Grid), DP, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                      ctypes.POINTER(sgn.Params), ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    ("sgn_amr_destroy", None, [ctypes.c_void_p]),
+    ("sgn_amr_npatches", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sgn_amr_set_patch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, DP]),
+    ("sgn_amr_get_patch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, DP]),
+    ("sgn_amr_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, DP]),
+    ("sgn_amr_step_dt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    ("sgn_amr_next_dt", ctypes.c_int, [ctypes.c_void_p, DP]),
+    ("sgn_amr_mass", ctypes.c_int, [ctypes.c_void_p, DP, DP]),
+    ("sgn_amr_status", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint)]),
+    ("sgn_amr_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_longlong)]),
+    ("sgn_amr_launches_per_step", ctypes.c_int, [ctypes.c_void_p]),
+]
+_ready = False
+
+
+def lib():
+    global _ready
+    L = sgn.load()
+    if not _ready:
+        for name, res, args in AMR_SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _ready = True
+    return L
+
+
+def _ck(rc, what):
+    if rc != 0:
+        raise sgn.SGNError(rc, what)
+
+
+class Hierarchy:
+    """Refined hierarchy on the GPU.  boxes: for levels 1..L-1, lists of
+    (i0, j0, nx, ny) in that level's cells; b_finest: bathymetry of the finest
+    level.  Patch states are (nvar, ny, nx) float64 arrays."""
+
+    def __init__(self, b_finest, nx0, ny0, dx0, r, boxes, model=sgn.HSGN, bc=(sgn.WALL,) * 4,
+                 precision=sgn.FP64, stream=None, torch_alloc=True, **params):
+        L = lib()
+        self.L = len(boxes) + 1
+        self.r, self.model = r, model
+        self.nvar = sgn.NVAR[model]
+        b = np.ascontiguousarray(b_finest, dtype=np.float64)
+        R = r ** (self.L - 1)
+        if b.shape != (ny0 * R, nx0 * R):
+            raise ValueError("b_finest must have shape %s" % ((ny0 * R, nx0 * R),))
+        g = sgn.Grid()
+        g.nx, g.ny, g.dx, g.dy = nx0, ny0, dx0, dx0
+        for i in range(4):
+            g.bc[i] = bc[i]
+        self.params = sgn.default_params(precision=precision, **params)
+        self._alloc = None
+        aptr = None
+        if torch_alloc:
+            import torch
+            self._alloc = sgn._TorchAllocator(torch.device("cuda", torch.cuda.current_device()))
+            aptr = ctypes.byref(self._alloc.struct)
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+        self.boxes = [[(0, 0, nx0, ny0)]] + [[tuple(int(v) for v in bx) for bx in bl] for bl in boxes]
+        nb = (ctypes.c_int * max(1, self.L - 1))(*[len(bl) for bl in boxes])
+        flat = [int(v) for bl in boxes for bx in bl for v in bx]
+        bx = (ctypes.c_int * max(1, len(flat)))(*flat)
+        h = ctypes.c_void_p()
+        _ck(L.sgn_amr_create(ctypes.byref(g), b.ctypes.data_as(DP), self.L, r, nb, bx, model,
+                             ctypes.byref(self.params), aptr, ctypes.c_void_p(stream) if stream else None,
+                             ctypes.byref(h)), "sgn_amr_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sgn_amr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def npatches(self, level):
+        return lib().sgn_amr_npatches(self.h, level)
+
+    def set_patch(self, level, k, q):
+        i0, j0, nx, ny = self.boxes[level][k]
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        if q.shape != (self.nvar, ny, nx):
+            raise ValueError("patch state must have shape %s" % ((self.nvar, ny, nx),))
+        _ck(lib().sgn_amr_set_patch(self.h, level, k, q.ctypes.data_as(DP)), "sgn_amr_set_patch")
+
+    def get_patch(self, level, k):
+        i0, j0, nx, ny = self.boxes[level][k]
+        out = np.empty((self.nvar, ny, nx))
+        _ck(lib().sgn_amr_get_patch(self.h, level, k, out.ctypes.data_as(DP)), "sgn_amr_get_patch")
+        return out
+
+    def set_state(self, qs):
+        """qs[l]: dense (nvar, NY_l, NX_l) state of level l; each patch takes its box."""
+        for l, bl in enumerate(self.boxes):
+            for k, (i0, j0, nx, ny) in enumerate(bl):
+                self.set_patch(l, k, qs[l][:, j0:j0 + ny, i0:i0 + nx])
+
+    def step(self, n=1):
+        t = ctypes.c_double()
+        _ck(lib().sgn_amr_step(self.h, int(n), ctypes.byref(t)), "sgn_amr_step")
+        return t.value
+
+    def step_rc(self, n=1):
+        t = ctypes.c_double()
+        return lib().sgn_amr_step(self.h, int(n), ctypes.byref(t))
+
+    def step_dt(self, dt0):
+        _ck(lib().sgn_amr_step_dt(self.h, float(dt0)), "sgn_amr_step_dt")
+
+    def next_dt(self):
+        d = ctypes.c_double()
+        _ck(lib().sgn_amr_next_dt(self.h, ctypes.byref(d)), "sgn_amr_next_dt")
+        return d.value
+
+    def mass(self):
+        """(mass over the uncovered cells of all levels, water added by clipped reflux)."""
+        m, c = ctypes.c_double(), ctypes.c_double()
+        _ck(lib().sgn_amr_mass(self.h, ctypes.byref(m), ctypes.byref(c)), "sgn_amr_mass")
+        return m.value, c.value
+
+    def status(self):
+        f = ctypes.c_uint()
+        _ck(lib().sgn_amr_status(self.h, ctypes.byref(f)), "sgn_amr_status")
+        return f.value
+
+    def info(self):
+        """Per level: interior cells of all patches, cells of the level's atlas."""
+        c = (ctypes.c_longlong * self.L)()
+        a = (ctypes.c_longlong * self.L)()
+        _ck(lib().sgn_amr_info(self.h, c, a), "sgn_amr_info")
+        return list(c), list(a)
+
+    def launches_per_step(self):
+        return lib().sgn_amr_launches_per_step(self.h)

@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsgn_gb300.so")
-UNITS = ["sgn_f64.cu", "sgn_mixed.cu", "sgn_capi.cu", "sgn_noalloc.cu", "lc_kernels.cu"]
+UNITS = ["sgn_f64.cu", "sgn_mixed.cu", "sgn_amr_f64.cu", "sgn_amr_mixed.cu", "sgn_capi.cu", "sgn_noalloc.cu",
+         "lc_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

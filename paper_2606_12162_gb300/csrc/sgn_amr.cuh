@@ -1,0 +1,891 @@
+// sgn_amr.cuh -- refined hierarchy (block-structured AMR, Sec. 4 of the paper:
+// patches, refinement ratio r, subcycling in time).
+//
+// Each level is one padded "atlas" grid holding all of its patches (each with
+// its own two-layer ghost frame, packed on shelves), stepped by the uniform
+// solver's kernels with a kind mask (patch interior / covered): every stage is
+// one launch over all patches of the level.  Around them, per level:
+//   k_amr_fill     ghost cells from siblings (copy) and the parent (limited
+//                  interpolation in space of the surface and primitives, linear
+//                  in time), k_amr_fill_bc the boundary-condition ghosts,
+//   k_amr_theta    positivity factors of sibling ghosts,
+//   k_amr_reg_*    mass-flux registers at coarse/fine faces,
+//   k_amr_avg      average-down, k_amr_reflux the mass correction,
+//   k_amr_finalize the level-0 step from the speeds of all levels.
+// A level-0 step with all substeps is captured once per ping-pong state and
+// replayed as a CUDA graph.
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "../../include/sgn_amr.h"
+#include "sgn_solver.cuh"
+
+namespace sgn {
+
+constexpr int AMR_MAXL = 8;
+
+// ghost-table entry: dst/src padded indices; info: bits 0-1 type, BC: bit 2/3
+// flip hu/hv; PAR: bits 8-15 / 16-23 sub-cell offsets, 24-27 neighbour flags W E S N
+struct GEnt { int dst, src, info; };
+enum { GE_SIB = 0, GE_PAR = 1, GE_BC = 2 };
+
+__device__ __forceinline__ double amr_minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+template <int MODEL, typename Real>
+__global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t, int n, int cc, int pold, int pnew,
+                           double a, int r) {
+  constexpr int NV = MT<MODEL>::NV;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const GEnt g = t[e];
+  Real* qc = c.q[cc];
+  if ((g.info & 3) == GE_SIB) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) qc[k * c.fs + g.dst] = qc[k * c.fs + g.src];
+    return;
+  }
+  const int sx = (g.info >> 8) & 255, sy = (g.info >> 16) & 255, nb = (g.info >> 24) & 15;
+  const Real* qo = p.q[pold];
+  const Real* qn = p.q[pnew];
+  const double dry = c.dry_tol;
+  // surface and primitives of a parent cell at the time weight (false: dry)
+  auto prim = [&](size_t id, double* o) -> bool {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = (1.0 - a) * (double)qo[k * p.fs + id] + a * (double)qn[k * p.fs + id];
+    double h = v[0] - (double)p.b[id];
+    if (!(h > dry)) return false;
+    o[0] = v[0];
+#pragma unroll
+    for (int k = 1; k < NV; k++) o[k] = v[k] / h;
+    return true;
+  };
+  const double bf = (double)c.b[g.dst];
+  double pc[NV], pw[NV], pe[NV], ps[NV], pn[NV], out[NV];
+  const size_t ic = (size_t)g.src;
+  if (!prim(ic, pc)) {
+    qc[g.dst] = (Real)(bf > 0.0 ? bf : 0.0);
+#pragma unroll
+    for (int k = 1; k < NV; k++) qc[k * c.fs + g.dst] = Real(0);
+    return;
+  }
+  const bool hx = (nb & 1) && (nb & 2) && prim(ic - 1, pw) && prim(ic + 1, pe);
+  const bool hy = (nb & 4) && (nb & 8) && prim(ic - p.pitch, ps) && prim(ic + p.pitch, pn);
+  const double xi = (sx + 0.5) / r - 0.5, yi = (sy + 0.5) / r - 0.5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    double slx = hx ? amr_minmod(pc[k] - pw[k], pe[k] - pc[k]) : 0.0;
+    double sly = hy ? amr_minmod(pc[k] - ps[k], pn[k] - pc[k]) : 0.0;
+    out[k] = pc[k] + xi * slx + yi * sly;
+  }
+  if (out[0] < bf) out[0] = bf;
+  const double hf = out[0] - bf;
+  qc[g.dst] = (Real)out[0];
+#pragma unroll
+  for (int k = 1; k < NV; k++) qc[k * c.fs + g.dst] = (Real)(hf > dry ? hf * out[k] : 0.0);
+}
+
+template <int MODEL, typename Real>
+__global__ void k_amr_fill_bc(Dev<Real> c, const GEnt* __restrict__ t, int n, int cc) {
+  constexpr int NV = MT<MODEL>::NV;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const GEnt g = t[e];
+  Real* q = c.q[cc];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    Real v = q[k * c.fs + g.src];
+    if ((k == 1 && (g.info & 4)) || (k == 2 && (g.info & 8))) v = -v;
+    q[k * c.fs + g.dst] = v;
+  }
+}
+
+template <typename Real>
+__global__ void k_amr_theta(Dev<Real> c, const GEnt* __restrict__ t, int n) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const GEnt g = t[e];
+  if ((g.info & 3) == GE_SIB) c.theta[g.dst] = c.theta[g.src];
+}
+
+// theta-weighted mass flux at a face as k_update applies it (bulk precision)
+template <typename Real>
+__device__ __forceinline__ double face_phi(const Dev<Real>& d, size_t id, int dir) {
+  const Real M = dir == 0 ? d.TX[id] : d.TY[id];
+  const size_t idL = dir == 0 ? id - 1 : id - d.pitch;
+  const Real t = M > Real(0) ? d.theta[idL] : (M < Real(0) ? d.theta[id] : Real(1));
+  return (double)(t * M);
+}
+
+template <typename Real>
+__global__ void k_amr_reg_coarse(Dev<Real> d, const int* __restrict__ face, const signed char* __restrict__ dir,
+                                 const signed char* __restrict__ sgn, double* __restrict__ val, int n) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int dr = dir[g];
+  val[g] = ((double)sgn[g] * d.lam[dr]) * face_phi(d, (size_t)face[g], dr);
+}
+
+template <typename Real>
+__global__ void k_amr_reg_fine(Dev<Real> f, const int* __restrict__ face, const signed char* __restrict__ dir,
+                               const signed char* __restrict__ sgn, double* __restrict__ val, int n, int r) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int dr = dir[g];
+  const size_t stride = dr == 0 ? (size_t)f.pitch : 1;
+  double s = 0.0;
+  for (int m = 0; m < r; m++) s += face_phi(f, (size_t)face[g] + m * stride, dr);
+  const double coef = f.lam[dr] / (double)(r * r);
+  val[g] -= ((double)sgn[g] * coef) * s;
+}
+
+template <int MODEL, typename Real>
+__global__ void k_amr_avg(Dev<Real> cd, Dev<Real> fd, const int* __restrict__ ci, const int* __restrict__ fi, int n,
+                          int cc, int fc, int r) {
+  constexpr int NV = MT<MODEL>::NV;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const size_t f0 = (size_t)fi[g];
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    double s = 0.0;
+    for (int dj = 0; dj < r; dj++)
+      for (int di = 0; di < r; di++) s += (double)fd.q[fc][k * fd.fs + f0 + (size_t)dj * fd.pitch + di];
+    cd.q[cc][k * cd.fs + ci[g]] = (Real)(s / (double)(r * r));
+  }
+}
+
+template <typename Real>
+__global__ void k_amr_reflux(Dev<Real> d, const int* __restrict__ cell, const int* __restrict__ first,
+                             const double* __restrict__ val, int m, int cc, double area, double* clipped) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m) return;
+  double corr = 0.0;
+  for (int i = first[g]; i < first[g + 1]; i++) corr += val[i];
+  const size_t id = (size_t)cell[g];
+  double e = (double)d.q[cc][id] + corr;
+  const double b = (double)d.b[id];
+  if (e < b) {
+    atomicAdd(clipped, (b - e) * area);
+    e = b;
+  }
+  d.q[cc][id] = (Real)e;
+}
+
+// mass partials over uncovered patch interiors (kind == 1)
+template <typename Real>
+__global__ void k_amr_mass1(Dev<Real> d, int cur) {
+  __shared__ double red[256];
+  double s = 0.0;
+  size_t n = (size_t)d.nx * d.ny;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(c % d.nx), j = (int)(c / d.nx);
+    size_t id = at(d.pitch, i + NG, j + NG);
+    if (d.kind[id] != 1) continue;
+    double h = (double)d.q[cur][id] - (double)d.b[id];
+    s += h > 0 ? h : 0.0;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d.mass_part[blockIdx.x] = red[0];
+}
+
+// copy one patch interior between a dense nv x ny x nx buffer and the atlas;
+// (px, py): padded atlas index of the patch frame's corner
+template <int MODEL, typename Real>
+__global__ void k_amr_pack(Dev<Real> d, const double* qd, int px, int py, int nx, int ny, int cur) {
+  constexpr int NV = MT<MODEL>::NV;
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  size_t id = at(d.pitch, px + NG + i, py + NG + j), n = (size_t)nx * ny, s = (size_t)j * nx + i;
+  Real q[NV];
+#pragma unroll
+  for (int k = 0; k < NV; k++) q[k] = (Real)qd[k * n + s];
+  Crit h = (Crit)q[0] - (Crit)d.b[id];
+  h = h > 0 ? h : 0;
+  source_switch<MODEL, Real>(q, h > d.dry_tol, Real(h), d.c2[id], Real(0));
+#pragma unroll
+  for (int k = 0; k < NV; k++) d.q[cur][k * d.fs + id] = q[k];
+}
+
+template <int MODEL, typename Real>
+__global__ void k_amr_unpack(Dev<Real> d, double* qd, int px, int py, int nx, int ny, int cur) {
+  constexpr int NV = MT<MODEL>::NV;
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  size_t id = at(d.pitch, px + NG + i, py + NG + j), n = (size_t)nx * ny, s = (size_t)j * nx + i;
+#pragma unroll
+  for (int k = 0; k < NV; k++) qd[k * n + s] = (double)d.q[cur][k * d.fs + id];
+}
+
+struct AmrDt {
+  int L, strang;
+  double cfl;
+  double R[AMR_MAXL], dx[AMR_MAXL], dy[AMR_MAXL];
+  unsigned long long* smax[AMR_MAXL];
+  unsigned long long* cmax[AMR_MAXL];
+  double* dt[AMR_MAXL];
+  double* lam[AMR_MAXL];
+  unsigned* status;
+  double* sc;   // dt0, t, last_dt, courant, clipped
+};
+
+__device__ __forceinline__ void amr_level_steps(const AmrDt& a, double dt0) {
+  for (int l = 0; l < a.L; l++) {
+    double dtl = dt0 / a.R[l];
+    *a.dt[l] = dtl;
+    a.lam[l][0] = dtl / a.dx[l];
+    a.lam[l][1] = dtl / a.dy[l];
+    a.lam[l][2] = a.strang ? 0.5 * dtl : 0.0;
+    a.lam[l][3] = a.strang ? 0.5 * dtl : dtl;
+  }
+}
+
+// Level-0 step bookkeeping (one thread): dt0 = min_l CFL r^l / smax_l, the
+// level steps dt0 / r^l with their dt/dx, dt/dy and source sub-steps; the
+// accumulators are cleared for the next level-0 step.
+static __global__ void k_amr_finalize(AmrDt a, int advance) {
+  if (threadIdx.x != 0) return;
+  if (advance) {
+    double dt = a.sc[0];
+    a.sc[1] += dt;
+    a.sc[2] = dt;
+    double cr = 0.0;
+    for (int l = 0; l < a.L; l++) cr = fmax(cr, __longlong_as_double((long long)*a.cmax[l]));
+    a.sc[3] = cr;
+    if (cr > 1.0) set_status(a.status, ST_CFL);
+  }
+  double best = 0.0;
+  bool any = false;
+  for (int l = 0; l < a.L; l++) {
+    double sp = __longlong_as_double((long long)*a.smax[l]);
+    if (sp > 0.0) {
+      double d = a.cfl * a.R[l] / sp;
+      if (!any || d < best) best = d;
+      any = true;
+    }
+  }
+  if (!any) set_status(a.status, ST_ALLDRY);
+  a.sc[0] = best;
+  amr_level_steps(a, best);
+  for (int l = 0; l < a.L; l++) {
+    *a.smax[l] = 0ull;
+    *a.cmax[l] = 0ull;
+  }
+}
+
+// a prescribed level-0 step
+static __global__ void k_amr_setdt(AmrDt a, double dt0) {
+  if (threadIdx.x != 0) return;
+  a.sc[0] = dt0;
+  amr_level_steps(a, dt0);
+}
+
+struct AmrArgs {
+  sgn_grid grid;
+  sgn_params prm;
+  int model, L, r;
+  const double* b;
+  std::vector<std::vector<int>> boxes;   // per level >= 1: 4 ints per box
+  const sgn_allocator* alloc;
+  cudaStream_t stream;
+};
+
+struct AmrBase {
+  virtual ~AmrBase() {}
+  virtual int init(const AmrArgs& a) = 0;
+  virtual int npatches(int l) const = 0;
+  virtual int set_patch(int l, int k, const double* q) = 0;
+  virtual int get_patch(int l, int k, double* q) = 0;
+  virtual int step(int n, double* t_out) = 0;
+  virtual int step_dt(double dt0) = 0;
+  virtual int next_dt(double* dt0) = 0;
+  virtual int mass(double* m, double* clipped) = 0;
+  virtual int status(unsigned* f) = 0;
+  virtual int info(long long* cells, long long* atlas) const = 0;
+  virtual int launches_per_step() const = 0;
+};
+
+AmrBase* make_amr_f64(int model);
+AmrBase* make_amr_mixed(int model);
+
+// ---------------------------------------------------------------------------
+// host side: hierarchy geometry, atlas packing, tables
+struct Box { int i0, j0, nx, ny; int px, py; int parent; };   // (px, py): padded index of the frame corner
+
+inline int bc_index(int X, int N, int lo, int hi, bool& flip) {
+  flip = false;
+  if (X < 0) { if (lo == SGN_BC_WALL) { flip = true; return -X - 1; } return 0; }
+  if (X >= N) { if (hi == SGN_BC_WALL) { flip = true; return 2 * N - 1 - X; } return N - 1; }
+  return X;
+}
+
+// spatial buckets of a level's boxes for owner lookups
+struct Owner {
+  int B = 64, nbx = 1, nby = 1;
+  std::vector<std::vector<int>> bk;
+  const std::vector<Box>* bx = nullptr;
+  void build(const std::vector<Box>& boxes, int NX, int NY) {
+    bx = &boxes;
+    nbx = (NX + B - 1) / B; nby = (NY + B - 1) / B;
+    bk.assign((size_t)nbx * nby, {});
+    for (int k = 0; k < (int)boxes.size(); k++) {
+      const Box& b = boxes[k];
+      int x0 = std::max(0, b.i0) / B, x1 = std::min(NX - 1, b.i0 + b.nx - 1) / B;
+      int y0 = std::max(0, b.j0) / B, y1 = std::min(NY - 1, b.j0 + b.ny - 1) / B;
+      for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++) bk[(size_t)y * nbx + x].push_back(k);
+    }
+  }
+  int find(int X, int Y, int skip = -1) const {
+    if (X < 0 || Y < 0 || X / B >= nbx || Y / B >= nby) return -1;
+    for (int k : bk[(size_t)(Y / B) * nbx + X / B]) {
+      const Box& b = (*bx)[k];
+      if (k != skip && X >= b.i0 && X < b.i0 + b.nx && Y >= b.j0 && Y < b.j0 + b.ny) return k;
+    }
+    return -1;
+  }
+};
+
+template <int MODEL, typename Real>
+class Amr : public AmrBase {
+  static constexpr int NV = MT<MODEL>::NV;
+  int L_ = 1, r_ = 2;
+  sgn_grid g0_{};
+  sgn_params prm_{};
+  std::vector<Solver<MODEL, Real>*> lv_;
+  std::vector<std::vector<Box>> bx_;
+  std::vector<int> NX_, NY_;
+  std::vector<double> dx_;
+  struct Tabs {
+    GEnt* fill = nullptr; int nfill = 0;      // SIB + PAR
+    GEnt* bc = nullptr; int nbc = 0;
+    int* rface_c = nullptr; int* rface_f = nullptr; signed char* rdir = nullptr; signed char* rsgn = nullptr;
+    double* rval = nullptr; int nreg = 0;     // registers of this level (as the coarse side)
+    int* rcell = nullptr; int* rfirst = nullptr; int ncell = 0;
+    int* acoarse = nullptr; int* afine = nullptr; int navg = 0;
+  };
+  std::vector<Tabs> tb_;
+  std::vector<long long> cells_, atlas_;
+  double* sc_ = nullptr;       // dt0, t, last_dt, courant, clipped
+  double* staging_ = nullptr;
+  double* hsc_ = nullptr;      // pinned host scalars
+  cudaStream_t st_ = nullptr, cap_ = nullptr;
+  std::map<unsigned, std::pair<cudaGraphExec_t, unsigned>> graphs_;   // cur bits -> (graph, cur bits after)
+  bool fresh_ = true;
+  int launches_ = 0;
+  AmrDt dt_{};
+
+  template <typename T> T* up(const std::vector<T>& h) {
+    if (h.empty()) return nullptr;
+    T* d = lv_[0]->template alloc_dev<T>(h.size());
+    if (!d) return nullptr;
+    if (cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st_) != cudaSuccess) return nullptr;
+    return d;
+  }
+
+  static unsigned grid1(int n) { return (unsigned)((n + 255) / 256); }
+
+ public:
+  ~Amr() override {
+    if (st_) cudaStreamSynchronize(st_);
+    for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second.first);
+    for (int l = (int)lv_.size() - 1; l >= 0; l--) delete lv_[l];
+    if (hsc_) cudaFreeHost(hsc_);
+    if (cap_) cudaStreamDestroy(cap_);
+  }
+
+  int npatches(int l) const override { return (l >= 0 && l < L_) ? (int)bx_[l].size() : SGN_EINVAL; }
+  int launches_per_step() const override { return launches_; }
+  int info(long long* cells, long long* atlas) const override {
+    for (int l = 0; l < L_; l++) {
+      if (cells) cells[l] = cells_[l];
+      if (atlas) atlas[l] = atlas_[l];
+    }
+    return SGN_OK;
+  }
+
+  int init(const AmrArgs& a) override {
+    L_ = a.L; r_ = a.r; g0_ = a.grid; prm_ = a.prm; st_ = a.stream;
+    const int r = r_, L = L_;
+    SGN_CK(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+    SGN_CK(cudaMallocHost((void**)&hsc_, 16 * sizeof(double)));
+    NX_.resize(L); NY_.resize(L); dx_.resize(L);
+    long long R = 1;
+    for (int l = 0; l < L; l++) {
+      NX_[l] = (int)(g0_.nx * R); NY_[l] = (int)(g0_.ny * R);
+      dx_[l] = g0_.dx / (double)R;
+      R *= r;
+    }
+    // boxes (level 0: the grid)
+    bx_.assign(L, {});
+    bx_[0].push_back(Box{0, 0, g0_.nx, g0_.ny, 0, 0, -1});
+    for (int l = 1; l < L; l++) {
+      const std::vector<int>& v = a.boxes[l - 1];
+      for (size_t k = 0; k + 3 < v.size(); k += 4) bx_[l].push_back(Box{v[k], v[k + 1], v[k + 2], v[k + 3], 0, 0, -1});
+    }
+    // validation (the rules of the header)
+    std::vector<Owner> own(L);
+    for (int l = 1; l < L; l++)
+      for (const Box& b : bx_[l])
+        if (b.i0 < 0 || b.j0 < 0 || b.nx < 2 || b.ny < 2 || b.i0 + b.nx > NX_[l] || b.j0 + b.ny > NY_[l] ||
+            b.i0 % r || b.j0 % r || b.nx % r || b.ny % r)
+          return SGN_EINVAL;
+    for (int l = 0; l < L; l++) own[l].build(bx_[l], NX_[l], NY_[l]);
+    for (int l = 1; l < L; l++) {
+      for (int k = 0; k < (int)bx_[l].size(); k++) {
+        Box& b = bx_[l][k];
+        int c0 = b.i0 / r, c1 = (b.i0 + b.nx) / r, d0 = b.j0 / r, d1 = (b.j0 + b.ny) / r;
+        int pi = -1;
+        for (int q = 0; q < (int)bx_[l - 1].size(); q++) {
+          const Box& p = bx_[l - 1][q];
+          if (p.i0 <= c0 && c1 <= p.i0 + p.nx && p.j0 <= d0 && d1 <= p.j0 + p.ny) { pi = q; break; }
+        }
+        if (pi < 0) return SGN_EINVAL;
+        const Box& p = bx_[l - 1][pi];
+        int gaps[4] = {c0 - p.i0, p.i0 + p.nx - c1, d0 - p.j0, p.j0 + p.ny - d1};
+        bool edge[4] = {c0 == 0, c1 == NX_[l - 1], d0 == 0, d1 == NY_[l - 1]};
+        for (int s = 0; s < 4; s++)
+          if (gaps[s] < 2 && !edge[s]) return SGN_EINVAL;
+        b.parent = pi;
+        // overlap: another box owns a cell on this machine's boundary (covers
+        // partial overlap and containment either way)
+        for (int x = b.i0; x < b.i0 + b.nx; x++)
+          if (own[l].find(x, b.j0, k) >= 0 || own[l].find(x, b.j0 + b.ny - 1, k) >= 0) return SGN_EINVAL;
+        for (int y = b.j0; y < b.j0 + b.ny; y++)
+          if (own[l].find(b.i0, y, k) >= 0 || own[l].find(b.i0 + b.nx - 1, y, k) >= 0) return SGN_EINVAL;
+      }
+    }
+    // bathymetry of every level (finest given; block means upward)
+    std::vector<std::vector<double>> bl(L);
+    bl[L - 1].assign(a.b, a.b + (size_t)NX_[L - 1] * NY_[L - 1]);
+    for (int l = L - 2; l >= 0; l--) {
+      bl[l].assign((size_t)NX_[l] * NY_[l], 0.0);
+      const int NXf = NX_[l + 1];
+      for (int j = 0; j < NY_[l]; j++)
+        for (int i = 0; i < NX_[l]; i++) {
+          double s = 0.0;
+          for (int dj = 0; dj < r; dj++)
+            for (int di = 0; di < r; di++) s += bl[l + 1][(size_t)(j * r + dj) * NXf + (i * r + di)];
+          bl[l][(size_t)j * NX_[l] + i] = s / (double)(r * r);
+        }
+    }
+    auto bval = [&](int l, int X, int Y) {
+      bool f;
+      int Xs = bc_index(X, NX_[l], g0_.bc[0], g0_.bc[1], f), Ys = bc_index(Y, NY_[l], g0_.bc[2], g0_.bc[3], f);
+      return bl[l][(size_t)Ys * NX_[l] + Xs];
+    };
+    // phi_T of a level cell by the uniform-grid rule (boundary-mapped first)
+    auto phival = [&](int l, int X, int Y) -> unsigned char {
+      bool f;
+      int Xs = bc_index(X, NX_[l], g0_.bc[0], g0_.bc[1], f), Ys = bc_index(Y, NY_[l], g0_.bc[2], g0_.bc[3], f);
+      int n = prm_.n_transition;
+      double dx = dx_[l], dy = dx_[l];
+      double r2 = (n * dx) * (n * dx), mn = 1e300;
+      for (int dj = -n; dj <= n; dj++)
+        for (int di = -n; di <= n; di++) {
+          if ((di * dx) * (di * dx) + (dj * dy) * (dj * dy) > r2) continue;
+          double H = -bval(l, Xs + di, Ys + dj);
+          H = H > 0.0 ? H : 0.0;
+          mn = H < mn ? H : mn;
+        }
+      return mn > prm_.h_star ? 1 : 0;
+    };
+    // atlases and level solvers
+    lv_.assign(L, nullptr);
+    cells_.assign(L, 0); atlas_.assign(L, 0);
+    for (int l = 0; l < L; l++) {
+      CreateArgs ca{};
+      ca.prm = prm_; ca.model = a.model; ca.alloc = a.alloc; ca.stream = st_;
+      std::vector<double> bd;
+      std::vector<unsigned char> pd, kd;
+      int nxa, nya;
+      for (auto& b : bx_[l]) cells_[l] += (long long)b.nx * b.ny;
+      if (l == 0) {
+        nxa = g0_.nx; nya = g0_.ny;
+        ca.grid = g0_;
+        bd = bl[0];
+      } else {
+        // shelf packing of the (nx+4) x (ny+4) frames, tallest first
+        std::vector<int> ord(bx_[l].size());
+        for (size_t k = 0; k < ord.size(); k++) ord[k] = (int)k;
+        std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return bx_[l][u].ny > bx_[l][v].ny; });
+        double area = 0;
+        int maxw = 2;
+        for (auto& b : bx_[l]) { area += (double)(b.nx + 4) * (b.ny + 4); maxw = std::max(maxw, b.nx + 4); }
+        nxa = std::max(maxw, (int)std::ceil(std::sqrt(area * 1.1)));
+        int x = 0, y = 0, sh = 0;
+        for (int k : ord) {
+          Box& b = bx_[l][k];
+          if (x + b.nx + 4 > nxa) { x = 0; y += sh; sh = 0; }
+          b.px = x + NG; b.py = y + NG;   // the atlas has its own two-cell frame
+          x += b.nx + 4;
+          sh = std::max(sh, b.ny + 4);
+        }
+        nya = std::max(2, y + sh);
+        ca.grid = g0_;
+        ca.grid.nx = nxa; ca.grid.ny = nya;
+        ca.grid.dx = dx_[l]; ca.grid.dy = dx_[l];
+        for (int s = 0; s < 4; s++) ca.grid.bc[s] = SGN_BC_EXTRAP;
+        bd.assign((size_t)nxa * nya, 1000.0);   // empty atlas cells: dry land
+        pd.assign((size_t)nxa * nya, 0);
+        for (auto& b : bx_[l])
+          for (int J = 0; J < b.ny + 4; J++)
+            for (int I = 0; I < b.nx + 4; I++) {
+              int X = b.i0 - 2 + I, Y = b.j0 - 2 + J;
+              size_t o = (size_t)(b.py - NG + J) * nxa + (b.px - NG + I);
+              bd[o] = bval(l, X, Y);
+              pd[o] = phival(l, X, Y);
+            }
+      }
+      atlas_[l] = (long long)(nxa + 4) * (nya + 4);
+      if ((long long)((nxa + 5 + 31) / 32 * 32) * (nya + 5) >= (1LL << 31)) return SGN_EINVAL;
+      ca.b = bd.data();
+      ca.phi = l == 0 ? nullptr : pd.data();
+      lv_[l] = new Solver<MODEL, Real>();
+      int rc = lv_[l]->init(ca);
+      if (rc) return rc;
+      // kind: 1 interior, +2 covered by the next level; interior cell (i, j) of
+      // a box is dense atlas cell (px - NG + 2 + i, py - NG + 2 + j)
+      kd.assign((size_t)nxa * nya, 0);
+      for (int k = 0; k < (int)bx_[l].size(); k++) {
+        const Box& b = bx_[l][k];
+        for (int j = 0; j < b.ny; j++)
+          for (int i = 0; i < b.nx; i++) {
+            unsigned char v = 1;
+            if (l + 1 < L && own[l + 1].find((b.i0 + i) * r, (b.j0 + j) * r) >= 0) v |= 2;
+            kd[(size_t)(b.py + j) * nxa + (b.px + i)] = v;
+          }
+      }
+      rc = lv_[l]->set_kind(kd.data());
+      if (rc) return rc;
+    }
+    tb_.assign(L, Tabs{});
+    // padded atlas index of frame cell (I, J) of box b on level l
+    auto pidx = [&](int l, const Box& b, int I, int J) {
+      return (int)((size_t)(b.py + J) * lv_[l]->dev().pitch + (b.px + I));
+    };
+    for (int l = 1; l < L; l++) {
+      std::vector<GEnt> fill, bcs;
+      for (int k = 0; k < (int)bx_[l].size(); k++) {
+        const Box& b = bx_[l][k];
+        const Box& P = bx_[l - 1][b.parent];
+        for (int J = 0; J < b.ny + 4; J++)
+          for (int I = 0; I < b.nx + 4; I++) {
+            if (I >= 2 && I < b.nx + 2 && J >= 2 && J < b.ny + 2) continue;
+            int X = b.i0 - 2 + I, Y = b.j0 - 2 + J;
+            int dst = pidx(l, b, I, J);
+            if (X < 0 || Y < 0 || X >= NX_[l] || Y >= NY_[l]) {
+              bool fx, fy;
+              int Xs = bc_index(X, NX_[l], g0_.bc[0], g0_.bc[1], fx);
+              int Ys = bc_index(Y, NY_[l], g0_.bc[2], g0_.bc[3], fy);
+              int Is = Xs - b.i0 + 2, Js = Ys - b.j0 + 2;
+              if (Is < 0 || Js < 0 || Is >= b.nx + 4 || Js >= b.ny + 4) return SGN_EINVAL;
+              bcs.push_back(GEnt{dst, pidx(l, b, Is, Js), GE_BC | (fx ? 4 : 0) | (fy ? 8 : 0)});
+              continue;
+            }
+            int o = own[l].find(X, Y, k);
+            if (o >= 0) {
+              const Box& s = bx_[l][o];
+              fill.push_back(GEnt{dst, pidx(l, s, X - s.i0 + 2, Y - s.j0 + 2), GE_SIB});
+              continue;
+            }
+            int ic = X / r, jc = Y / r;
+            int nb = (ic - 1 >= 0 ? 1 : 0) | (ic + 1 < NX_[l - 1] ? 2 : 0) | (jc - 1 >= 0 ? 4 : 0) |
+                     (jc + 1 < NY_[l - 1] ? 8 : 0);
+            int Ip = ic - P.i0 + 2, Jp = jc - P.j0 + 2;
+            if (Ip - 1 < 0 || Jp - 1 < 0 || Ip + 1 >= P.nx + 4 || Jp + 1 >= P.ny + 4) return SGN_EINVAL;
+            fill.push_back(GEnt{dst, pidx(l - 1, P, Ip, Jp), GE_PAR | ((X % r) << 8) | ((Y % r) << 16) | (nb << 24)});
+          }
+      }
+      tb_[l].fill = up(fill); tb_[l].nfill = (int)fill.size();
+      tb_[l].bc = up(bcs); tb_[l].nbc = (int)bcs.size();
+      if ((tb_[l].nfill && !tb_[l].fill) || (tb_[l].nbc && !tb_[l].bc)) return SGN_ENOMEM;
+    }
+    // registers and average-down maps of level l (coarse side)
+    for (int l = 0; l + 1 < L; l++) {
+      std::vector<int> fc, ff, af, ac, cellof;
+      std::vector<signed char> dr, sg;
+      for (int ci = 0; ci < (int)bx_[l + 1].size(); ci++) {
+        const Box& c = bx_[l + 1][ci];
+        const Box& P = bx_[l][c.parent];
+        int c0 = c.i0 / r, d0 = c.j0 / r, cw = c.nx / r, ch = c.ny / r;
+        for (int jc = d0; jc < d0 + ch; jc++)
+          for (int ic = c0; ic < c0 + cw; ic++) {
+            ac.push_back(pidx(l, P, ic - P.i0 + 2, jc - P.j0 + 2));
+            af.push_back(pidx(l + 1, c, (ic - c0) * r + 2, (jc - d0) * r + 2));
+          }
+        struct Cand { int d, ux, uy, fx, fy, s, fI, fJ; };
+        std::vector<Cand> cand;
+        for (int jc = d0; jc < d0 + ch; jc++) {
+          cand.push_back(Cand{0, c0 - 1, jc, c0, jc, +1, 2, (jc - d0) * r + 2});
+          cand.push_back(Cand{0, c0 + cw, jc, c0 + cw, jc, -1, c.nx + 2, (jc - d0) * r + 2});
+        }
+        for (int ic = c0; ic < c0 + cw; ic++) {
+          cand.push_back(Cand{1, ic, d0 - 1, ic, d0, +1, (ic - c0) * r + 2, 2});
+          cand.push_back(Cand{1, ic, d0 + ch, ic, d0 + ch, -1, (ic - c0) * r + 2, c.ny + 2});
+        }
+        for (const Cand& q : cand) {
+          if (q.ux < 0 || q.uy < 0 || q.ux >= NX_[l] || q.uy >= NY_[l]) continue;
+          if (own[l + 1].find(q.ux * r, q.uy * r) >= 0) continue;   // covered: a sibling face
+          fc.push_back(pidx(l, P, q.fx - P.i0 + 2, q.fy - P.j0 + 2));
+          ff.push_back(pidx(l + 1, c, q.fI, q.fJ));
+          dr.push_back((signed char)q.d);
+          sg.push_back((signed char)q.s);
+          cellof.push_back(pidx(l, P, q.ux - P.i0 + 2, q.uy - P.j0 + 2));
+        }
+      }
+      // group the registers by corrected cell (creation order within a cell)
+      std::vector<int> order(cellof.size());
+      for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return cellof[u] < cellof[v]; });
+      std::vector<int> fc2, ff2, cells, first;
+      std::vector<signed char> dr2, sg2;
+      for (size_t i = 0; i < order.size(); i++) {
+        int g = order[i];
+        if (i == 0 || cellof[g] != cellof[order[i - 1]]) { cells.push_back(cellof[g]); first.push_back((int)i); }
+        fc2.push_back(fc[g]); ff2.push_back(ff[g]); dr2.push_back(dr[g]); sg2.push_back(sg[g]);
+      }
+      first.push_back((int)order.size());
+      Tabs& t = tb_[l];
+      t.nreg = (int)fc2.size();
+      if (t.nreg) {
+        t.rface_c = up(fc2); t.rface_f = up(ff2); t.rdir = up(dr2); t.rsgn = up(sg2);
+        t.rval = lv_[0]->template alloc_dev<double>(t.nreg);
+        t.ncell = (int)cells.size();
+        t.rcell = up(cells); t.rfirst = up(first);
+        if (!t.rface_c || !t.rface_f || !t.rdir || !t.rsgn || !t.rval || !t.rcell || !t.rfirst) return SGN_ENOMEM;
+      }
+      t.navg = (int)ac.size();
+      if (t.navg) {
+        t.acoarse = up(ac); t.afine = up(af);
+        if (!t.acoarse || !t.afine) return SGN_ENOMEM;
+      }
+    }
+    sc_ = lv_[0]->template alloc_dev<double>(8);
+    if (!sc_) return SGN_ENOMEM;
+    SGN_CK(cudaMemsetAsync(sc_, 0, 8 * sizeof(double), st_));
+    size_t mx = 0;
+    for (auto& v : bx_)
+      for (auto& b : v) mx = std::max(mx, (size_t)b.nx * b.ny);
+    staging_ = lv_[0]->template alloc_dev<double>(mx * NV);
+    if (!staging_) return SGN_ENOMEM;
+    // step bookkeeping
+    dt_.L = L; dt_.strang = prm_.strang; dt_.cfl = prm_.cfl;
+    double Rl = 1.0;
+    for (int l = 0; l < L; l++) {
+      Dev<Real>& d = lv_[l]->dev();
+      dt_.R[l] = Rl; Rl *= r;
+      dt_.dx[l] = d.dx; dt_.dy[l] = d.dy;
+      dt_.smax[l] = d.smax; dt_.cmax[l] = d.cmax; dt_.dt[l] = d.dt; dt_.lam[l] = d.lam;
+    }
+    dt_.status = lv_[0]->dev().status;
+    dt_.sc = sc_;
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaStreamSynchronize(st_));
+    fresh_ = true;
+    return SGN_OK;
+  }
+
+  int set_patch(int l, int k, const double* q) override {
+    if (l < 0 || l >= L_ || k < 0 || k >= (int)bx_[l].size() || !q) return SGN_EINVAL;
+    const Box& b = bx_[l][k];
+    size_t n = (size_t)b.nx * b.ny * NV;
+    SGN_CK(cudaMemcpyAsync(staging_, q, n * sizeof(double), cudaMemcpyHostToDevice, st_));
+    dim3 gr((b.nx + 31) / 32, (b.ny + 7) / 8);
+    k_amr_pack<MODEL, Real><<<gr, dim3(32, 8), 0, st_>>>(lv_[l]->dev(), staging_, b.px, b.py, b.nx, b.ny,
+                                                          lv_[l]->cur());
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaStreamSynchronize(st_));
+    fresh_ = true;
+    return SGN_OK;
+  }
+
+  int get_patch(int l, int k, double* q) override {
+    if (l < 0 || l >= L_ || k < 0 || k >= (int)bx_[l].size() || !q) return SGN_EINVAL;
+    const Box& b = bx_[l][k];
+    size_t n = (size_t)b.nx * b.ny * NV;
+    dim3 gr((b.nx + 31) / 32, (b.ny + 7) / 8);
+    k_amr_unpack<MODEL, Real><<<gr, dim3(32, 8), 0, st_>>>(lv_[l]->dev(), staging_, b.px, b.py, b.nx, b.ny,
+                                                            lv_[l]->cur());
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaMemcpyAsync(q, staging_, n * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    return SGN_OK;
+  }
+
+  // speeds of the current states -> dt0 and the level steps; clears time,
+  // status and clipping
+  int begin() {
+    for (int l = 0; l < L_; l++) {
+      Dev<Real>& d = lv_[l]->dev();
+      SGN_CK(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st_));
+      SGN_CK(cudaMemsetAsync(d.smax, 0, 2 * sizeof(unsigned long long), st_));
+      k_speed<MODEL, Real><<<lv_[l]->grid_interior(), dim3(32, 8), 0, st_>>>(d, lv_[l]->cur());
+    }
+    SGN_CK(cudaMemsetAsync(sc_ + 1, 0, 4 * sizeof(double), st_));
+    k_amr_finalize<<<1, 32, 0, st_>>>(dt_, 0);
+    SGN_CK(cudaGetLastError());
+    fresh_ = false;
+    return SGN_OK;
+  }
+
+  // one level-l step at substep ksub of its parent, then the finer levels
+  void run_level(cudaStream_t s, int l, int ksub, int& nl) {
+    Solver<MODEL, Real>* S = lv_[l];
+    Tabs& t = tb_[l];
+    const int c = S->cur();
+    if (l > 0) {
+      Solver<MODEL, Real>* P = lv_[l - 1];
+      const int pnew = P->cur(), pold = 1 - pnew;   // the parent has stepped already
+      if (t.nfill) {
+        k_amr_fill<MODEL, Real><<<grid1(t.nfill), 256, 0, s>>>(S->dev(), P->dev(), t.fill, t.nfill, c, pold, pnew,
+                                                                 (double)ksub / r_, r_);
+        nl++;
+      }
+      if (t.nbc) { k_amr_fill_bc<MODEL, Real><<<grid1(t.nbc), 256, 0, s>>>(S->dev(), t.bc, t.nbc, c); nl++; }
+    }
+    S->launch_phase1(s, c);
+    nl += 6;
+    if (l > 0 && t.nfill) { k_amr_theta<Real><<<grid1(t.nfill), 256, 0, s>>>(S->dev(), t.fill, t.nfill); nl++; }
+    if (l + 1 < L_ && t.nreg) {
+      k_amr_reg_coarse<Real><<<grid1(t.nreg), 256, 0, s>>>(S->dev(), t.rface_c, t.rdir, t.rsgn, t.rval, t.nreg);
+      nl++;
+    }
+    if (l > 0 && tb_[l - 1].nreg) {
+      Tabs& u = tb_[l - 1];
+      k_amr_reg_fine<Real><<<grid1(u.nreg), 256, 0, s>>>(S->dev(), u.rface_f, u.rdir, u.rsgn, u.rval, u.nreg, r_);
+      nl++;
+    }
+    S->launch_phase2(s, c);
+    nl++;
+    S->flip();
+    if (l + 1 < L_) {
+      for (int k = 0; k < r_; k++) run_level(s, l + 1, k, nl);
+      if (t.navg) {
+        k_amr_avg<MODEL, Real><<<grid1(t.navg), 256, 0, s>>>(S->dev(), lv_[l + 1]->dev(), t.acoarse, t.afine,
+                                                              t.navg, S->cur(), lv_[l + 1]->cur(), r_);
+        nl++;
+      }
+      if (t.ncell) {
+        k_amr_reflux<Real><<<grid1(t.ncell), 256, 0, s>>>(S->dev(), t.rcell, t.rfirst, t.rval, t.ncell, S->cur(),
+                                                          dx_[l] * dx_[l], sc_ + 4);
+        nl++;
+      }
+    }
+  }
+
+  unsigned curbits() const {
+    unsigned v = 0;
+    for (int l = 0; l < L_; l++) v |= (unsigned)lv_[l]->cur() << l;
+    return v;
+  }
+  void setcur(unsigned v) {
+    for (int l = 0; l < L_; l++)
+      if (((v >> l) & 1u) != (unsigned)lv_[l]->cur()) lv_[l]->flip();
+  }
+
+  int launch_one() {
+    unsigned key = curbits();
+    auto it = graphs_.find(key);
+    if (it == graphs_.end()) {
+      cudaGraph_t gr;
+      SGN_CK(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+      int nl = 0;
+      run_level(cap_, 0, 0, nl);
+      k_amr_finalize<<<1, 32, 0, cap_>>>(dt_, 1);
+      nl++;
+      unsigned after = curbits();
+      setcur(key);
+      cudaError_t e = cudaStreamEndCapture(cap_, &gr);
+      if (e != cudaSuccess) return SGN_ECUDA;
+      cudaGraphExec_t gx;
+      e = cudaGraphInstantiate(&gx, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return SGN_ECUDA;
+      it = graphs_.emplace(key, std::make_pair(gx, after)).first;
+      launches_ = nl;
+    }
+    SGN_CK(cudaGraphLaunch(it->second.first, st_));
+    setcur(it->second.second);
+    return SGN_OK;
+  }
+
+  int finish(double* t_out) {
+    unsigned st = 0;
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaMemcpyAsync(hsc_, sc_ + 1, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    for (int l = 0; l < L_; l++)
+      SGN_CK(cudaMemcpyAsync((unsigned*)(hsc_ + 2) + l, lv_[l]->dev().status, sizeof(unsigned),
+                             cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    for (int l = 0; l < L_; l++) st |= ((unsigned*)(hsc_ + 2))[l];
+    if (t_out) *t_out = hsc_[0];
+    return status_to_error(st);
+  }
+
+  int step(int n, double* t_out) override {
+    if (n < 0) return SGN_EINVAL;
+    if (fresh_) { int rc = begin(); if (rc) return rc; }
+    for (int i = 0; i < n; i++) { int rc = launch_one(); if (rc) return rc; }
+    return finish(t_out);
+  }
+
+  int step_dt(double dt0) override {
+    if (!(dt0 > 0)) return SGN_EINVAL;
+    if (fresh_) { int rc = begin(); if (rc) return rc; }
+    k_amr_setdt<<<1, 32, 0, st_>>>(dt_, dt0);
+    int rc = launch_one();
+    if (rc) return rc;
+    return finish(nullptr);
+  }
+
+  int next_dt(double* dt0) override {
+    if (fresh_) { int rc = begin(); if (rc) return rc; }
+    SGN_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    *dt0 = hsc_[0];
+    return SGN_OK;
+  }
+
+  int mass(double* m, double* clipped) override {
+    double tot = 0.0;
+    for (int l = 0; l < L_; l++) {
+      Dev<Real>& d = lv_[l]->dev();
+      k_amr_mass1<Real><<<592, 256, 0, st_>>>(d, lv_[l]->cur());
+      k_mass2<Real><<<1, 256, 0, st_>>>(d, 592);
+      SGN_CK(cudaGetLastError());
+      SGN_CK(cudaMemcpyAsync(hsc_ + 8, d.mass, sizeof(double), cudaMemcpyDeviceToHost, st_));
+      SGN_CK(cudaStreamSynchronize(st_));
+      tot += hsc_[8];
+    }
+    SGN_CK(cudaMemcpyAsync(hsc_ + 9, sc_ + 4, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    if (m) *m = tot;
+    if (clipped) *clipped = hsc_[9];
+    return SGN_OK;
+  }
+
+  int status(unsigned* f) override {
+    for (int l = 0; l < L_; l++)
+      SGN_CK(cudaMemcpyAsync((unsigned*)(hsc_ + 2) + l, lv_[l]->dev().status, sizeof(unsigned),
+                             cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    unsigned s = 0;
+    for (int l = 0; l < L_; l++) s |= ((unsigned*)(hsc_ + 2))[l];
+    if (f) *f = s;
+    return SGN_OK;
+  }
+};
+
+}  // namespace sgn

@@ -216,3 +216,97 @@ void sgn_destroy(sgn_solver* s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// refined hierarchy (include/sgn_amr.h)
+#include "sgn_amr.cuh"
+
+struct sgn_amr {
+  sgn::AmrBase* impl;
+};
+
+extern "C" {
+
+int sgn_amr_create(const sgn_grid* grid0, const double* b_finest, int nlevels, int ratio, const int* nboxes,
+                   const int* boxes, int model, const sgn_params* params, const sgn_allocator* allocator,
+                   void* cuda_stream, sgn_amr** out) {
+  if (!out) return SGN_EINVAL;
+  *out = nullptr;
+  if (!grid0 || !b_finest || !params || nlevels < 1 || nlevels > sgn::AMR_MAXL || ratio < 2 || ratio > 8)
+    return SGN_EINVAL;
+  if (nlevels > 1 && (!nboxes || !boxes)) return SGN_EINVAL;
+  for (int i = 0; i < 4; i++)
+    if (grid0->bc[i] != SGN_BC_WALL && grid0->bc[i] != SGN_BC_EXTRAP) return SGN_EINVAL;
+  if (grid0->dx != grid0->dy) return SGN_EINVAL;
+  long long R = 1;
+  for (int l = 1; l < nlevels; l++) R *= ratio;
+  if ((long long)grid0->nx * R > (1LL << 30) || (long long)grid0->ny * R > (1LL << 30)) return SGN_EINVAL;
+  int r = check_args(grid0, b_finest, model, params);
+  if (r) return r;
+  if (allocator && (!allocator->alloc || !allocator->free)) return SGN_EINVAL;
+  sgn::AmrArgs a;
+  a.grid = *grid0;
+  a.prm = *params;
+  a.model = model;
+  a.L = nlevels;
+  a.r = ratio;
+  a.b = b_finest;
+  a.alloc = allocator;
+  a.stream = (cudaStream_t)cuda_stream;
+  int off = 0;
+  for (int l = 1; l < nlevels; l++) {
+    if (nboxes[l - 1] < 0) return SGN_EINVAL;
+    a.boxes.emplace_back(boxes + 4 * off, boxes + 4 * (off + nboxes[l - 1]));
+    off += nboxes[l - 1];
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SGN_ECUDA;
+  sgn::AmrBase* impl = params->precision == SGN_MIXED ? sgn::make_amr_mixed(model) : sgn::make_amr_f64(model);
+  if (!impl) return SGN_ENOMEM;
+  r = impl->init(a);
+  if (r) {
+    delete impl;
+    return r;
+  }
+  sgn_amr* h = new (std::nothrow) sgn_amr;
+  if (!h) { delete impl; return SGN_ENOMEM; }
+  h->impl = impl;
+  *out = h;
+  return SGN_OK;
+}
+
+void sgn_amr_destroy(sgn_amr* a) {
+  if (!a) return;
+  delete a->impl;
+  delete a;
+}
+
+int sgn_amr_npatches(const sgn_amr* a, int level) { return a ? a->impl->npatches(level) : SGN_EINVAL; }
+
+int sgn_amr_set_patch(sgn_amr* a, int level, int patch, const double* q) {
+  return (a && q) ? a->impl->set_patch(level, patch, q) : SGN_EINVAL;
+}
+
+int sgn_amr_get_patch(sgn_amr* a, int level, int patch, double* q) {
+  return (a && q) ? a->impl->get_patch(level, patch, q) : SGN_EINVAL;
+}
+
+int sgn_amr_step(sgn_amr* a, int n, double* t_out) { return a ? a->impl->step(n, t_out) : SGN_EINVAL; }
+
+int sgn_amr_step_dt(sgn_amr* a, double dt0) { return a ? a->impl->step_dt(dt0) : SGN_EINVAL; }
+
+int sgn_amr_next_dt(sgn_amr* a, double* dt0) { return (a && dt0) ? a->impl->next_dt(dt0) : SGN_EINVAL; }
+
+int sgn_amr_mass(sgn_amr* a, double* mass, double* clipped) {
+  return a ? a->impl->mass(mass, clipped) : SGN_EINVAL;
+}
+
+int sgn_amr_status(sgn_amr* a, unsigned* flags) { return a ? a->impl->status(flags) : SGN_EINVAL; }
+
+int sgn_amr_info(const sgn_amr* a, long long* cells, long long* atlas_cells) {
+  return a ? a->impl->info(cells, atlas_cells) : SGN_EINVAL;
+}
+
+int sgn_amr_launches_per_step(const sgn_amr* a) { return a ? a->impl->launches_per_step() : SGN_EINVAL; }
+
+}  // extern "C"

@@ -222,14 +222,30 @@ class Solver : public SolverBase {
     return SGN_OK;
   }
 
-  // One time step from q[c] into q[1-c]: the kernel sequence of the method.
+  void pre(cudaStream_t s, int k) {
+    if (!prof_) return;
+    Ev e; e.k = k; cudaEventCreate(&e.a); cudaEventCreate(&e.b);
+    cudaEventRecord(e.a, s); evs_.push_back(e);
+  }
+  void post(cudaStream_t s) { if (prof_) cudaEventRecord(evs_.back().b, s); }
+
+  // One time step from q[c] into q[1-c]: the kernel sequence of the method,
+  // in two phases (a refined level exchanges ghost positivity factors and
+  // records reflux fluxes in between).
   void launch_step(cudaStream_t s, int c) {
-    auto pre = [&](int k) {
-      if (!prof_) return;
-      Ev e; e.k = k; cudaEventCreate(&e.a); cudaEventCreate(&e.b);
-      cudaEventRecord(e.a, s); evs_.push_back(e);
-    };
-    auto post = [&]() { if (prof_) cudaEventRecord(evs_.back().b, s); };
+    launch_phase1(s, c);
+    launch_phase2(s, c);
+    pre(s, KN_FINAL);
+    k_finalize<Real><<<1, 32, 0, s>>>(d_, 1); post(s);
+    if (d_.ngauge > 0) {
+      pre(s, KN_GAUGE);
+      k_gauge<Real><<<1, 256, 0, s>>>(d_, 1 - c); post(s);
+    }
+  }
+
+  void launch_phase1(cudaStream_t s, int c) {
+    auto pre = [&](int k) { this->pre(s, k); };
+    auto post = [&]() { this->post(s); };
     pre(KN_PREP);
     k_prep<MODEL, Real><<<gPad_, dim3(32, 8), 0, s>>>(d_, c); post();
     pre(KN_FACEX);
@@ -242,14 +258,32 @@ class Solver : public SolverBase {
     k_trans<MODEL, Real, 1><<<gTY_, dim3(32, 8), 0, s>>>(d_); post();
     pre(KN_THETA);
     k_theta<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_); post();
-    pre(KN_UPDATE);
-    k_update<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_, c); post();
-    pre(KN_FINAL);
-    k_finalize<Real><<<1, 32, 0, s>>>(d_, 1); post();
-    if (d_.ngauge > 0) {
-      pre(KN_GAUGE);
-      k_gauge<Real><<<1, 256, 0, s>>>(d_, 1 - c); post();
-    }
+  }
+
+  void launch_phase2(cudaStream_t s, int c) {
+    pre(s, KN_UPDATE);
+    k_update<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_, c); post(s);
+  }
+
+  // access for the refined hierarchy (sgn_amr.cuh)
+  Dev<Real>& dev() { return d_; }
+  int cur() const { return cur_; }
+  void flip() { cur_ ^= 1; }
+  dim3 grid_interior() const { return gInt_; }
+  template <typename T> T* alloc_dev(size_t n) { return dnew<T>(n); }
+  // kind plane from a dense ny*nx host array (ghost frame 0)
+  int set_kind(const unsigned char* kind_dense) {
+    unsigned char* kp = dnew<unsigned char>(d_.fs);
+    if (!kp) return SGN_ENOMEM;
+    std::vector<unsigned char> h(d_.fs, 0);
+    for (int j = 0; j < d_.ny; j++)
+      for (int i = 0; i < d_.nx; i++)
+        h[(size_t)(j + NG) * d_.pitch + (i + NG)] = kind_dense[(size_t)j * d_.nx + i];
+    SGN_CK(cudaMemcpyAsync(kp, h.data(), d_.fs, cudaMemcpyHostToDevice, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    d_.kind = kp;
+    drop_graphs();
+    return SGN_OK;
   }
 
   int launches_per_step() override { return d_.ngauge > 0 ? 9 : 8; }

@@ -36,10 +36,13 @@ def test_library_exports_exactly_the_headers(lib):
     from paper_2606_12162_gb300 import corrector, sgn
     out = subprocess.run(["nm", "-D", "--defined-only", sgn.LIB_PATH], capture_output=True, text=True).stdout
     exported = sorted(set(re.findall(r"\bT ([a-z]+_[a-z0-9_]+)$", out, flags=re.M)))
-    declared = header_functions("sgn_") + header_functions("lc_", os.path.join(ROOT, "include", "lc.h"))
+    from paper_2606_12162_gb300 import amr
+    declared = header_functions("sgn_") + header_functions("sgn_", os.path.join(ROOT, "include", "sgn_amr.h")) + \
+        header_functions("lc_", os.path.join(ROOT, "include", "lc.h"))
     assert exported == sorted(declared)
     # every declared entry point resolves through ctypes and has a binding signature
-    names = {n for n, _, _ in sgn.SIGNATURES} | {n for n, _, _ in corrector.LC_SIGS}
+    names = {n for n, _, _ in sgn.SIGNATURES} | {n for n, _, _ in corrector.LC_SIGS} | \
+        {n for n, _, _ in amr.AMR_SIGS}
     for fn in declared:
         getattr(lib[1], fn)
         assert fn in names
@@ -124,3 +127,36 @@ def test_create_without_gpu_reports_an_error_code(lib):
     rc = L.sgn_create(ctypes.byref(_grid(S)), b.ctypes.data_as(S.DP), 2, ctypes.byref(S.default_params()),
                       None, None, None, ctypes.byref(out))
     assert rc == -3 and not out.value
+
+
+def test_amr_create_rejects_invalid_arguments(lib):
+    """Refined hierarchy: argument checks on the host, before any device call."""
+    S, L = lib
+    from paper_2606_12162_gb300 import amr
+    amr.lib()
+    b = np.full((16, 16), -1.0)
+    nb = (ctypes.c_int * 1)(1)
+    bx = (ctypes.c_int * 4)(4, 4, 8, 8)
+    out = ctypes.c_void_p()
+    p = S.default_params()
+    dp = b.ctypes.data_as(S.DP)
+
+    def create(g, nlev=2, ratio=2, bb=dp, nbx=nb, box=bx, outp=ctypes.byref(out)):
+        return L.sgn_amr_create(ctypes.byref(g), bb, nlev, ratio, nbx, box, 2, ctypes.byref(p), None, None, outp)
+
+    assert create(_grid(S), outp=None) == -1
+    assert create(_grid(S), nlev=0) == -1
+    assert create(_grid(S), nlev=9) == -1
+    assert create(_grid(S), ratio=1) == -1
+    assert create(_grid(S), bb=None) == -1
+    assert create(_grid(S), nbx=None) == -1
+    assert create(_grid(S, bc=(2, 2, 0, 0))) == -1          # periodic
+    g = _grid(S)
+    g.dy = 2.0                                                 # dx != dy
+    assert create(g) == -1
+    assert L.sgn_amr_step(None, 1, None) == -1
+    assert L.sgn_amr_npatches(None, 0) == -1
+    L.sgn_amr_destroy(None)
+    import torch
+    if not torch.cuda.is_available():
+        assert create(_grid(S)) == -3 and not out.value

@@ -1,0 +1,152 @@
+"""Refined hierarchy on the GPU (include/sgn_amr.h, batched atlas kernels)
+against the plain refinement oracle (oracle/amr_oracle.py), patch by patch.
+
+FP64: per-field relative L2 <= 1e-12 on every patch, and the next level-0
+step, the mass and the clipped water to 1e-12.  Mixed precision: per-field
+tolerances as for the uniform grid.  Also: one level equals the uniform GPU
+solver bit for bit, lake at rest, and mass up to the reported clipping."""
+import numpy as np
+import pytest
+
+from paper_2606_12162_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+CFG = dict(h_star=0.0, dry_tol=1e-3, alpha=3.0)
+BOXES_R4 = [[(8, 8, 24, 16), (32, 8, 16, 16), (0, 32, 16, 16)], [(48, 48, 32, 32)]]
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_12162_gb300 import amr, build
+    build.build()
+    amr.lib()
+    return amr
+
+
+@pytest.fixture(scope="module")
+def A(oracle_mod):
+    from oracle import amr_oracle
+    return amr_oracle
+
+
+def rel_l2(a, b):
+    out = []
+    for k in range(a.shape[0]):
+        den = np.linalg.norm(b[k])
+        num = np.linalg.norm(a[k] - b[k])
+        out.append(num / den if den > 0 else num)
+    return np.array(out)
+
+
+def run_pair(M, A, model, nx0, ny0, r, boxes, seed, steps, precision=0, wetdry=True, bc=(0, 0, 0, 0), amp=0.2,
+             dx0=0.2):
+    L = len(boxes) + 1
+    b, qs = W.amr_small_case(model, nx0, ny0, r, L, seed=seed, wetdry=wetdry, amp=amp, dx0=dx0)
+    g = M.Hierarchy(b, nx0, ny0, dx0, r, boxes, model=model, bc=bc, precision=precision, **CFG)
+    g.set_state(qs)
+    o = A.AmrOracle(b, nx0, ny0, dx0, r, boxes, model=model, bc=bc, **CFG)
+    o.set_state(qs)
+    assert abs(g.next_dt() - o.dt_next) <= 1e-6 * o.dt_next
+    g.step(steps)
+    assert o.step(steps) == 0
+    return g, o, b
+
+
+@pytest.mark.parametrize("model,nx0,ny0,r,boxes,seed,steps,wetdry", [
+    (2, 24, 20, 2, W.amr_boxes_small(), 4, 10, True),
+    (1, 24, 20, 2, W.amr_boxes_small(), 5, 10, False),
+    (2, 16, 12, 4, BOXES_R4, 6, 6, True),
+    (0, 24, 20, 2, W.amr_boxes_small(), 7, 10, True),
+])
+def test_fp64_hierarchy_against_oracle(M, A, model, nx0, ny0, r, boxes, seed, steps, wetdry):
+    g, o, _ = run_pair(M, A, model, nx0, ny0, r, boxes, seed, steps, wetdry=wetdry)
+    for l in range(g.L):
+        for k in range(len(g.boxes[l])):
+            err = rel_l2(g.get_patch(l, k), o.patch_state(l, k))
+            assert (err <= FP64_TOL).all(), (l, k, err)
+    assert abs(g.next_dt() - o.dt_next) <= FP64_TOL * o.dt_next
+    m, c = g.mass()
+    mo = o.mass()
+    assert abs(m - mo) <= FP64_TOL * mo
+    assert abs(c - o.clipped) <= FP64_TOL * mo
+    assert g.status() == 0
+    assert g.launches_per_step() > 0
+
+
+def test_fixed_step_and_fine_level_covering_the_domain(M, A):
+    nx0, ny0, r = 12, 10, 2
+    boxes = [[(0, 0, nx0 * r, ny0 * r)]]
+    b, qs = W.amr_small_case(2, nx0, ny0, r, 2, seed=8)
+    g = M.Hierarchy(b, nx0, ny0, 0.2, r, boxes, model=2, **CFG)
+    g.set_state(qs)
+    o = A.AmrOracle(b, nx0, ny0, 0.2, r, boxes, model=2, **CFG)
+    o.set_state(qs)
+    dt = 0.5 * o.dt_next
+    for _ in range(3):
+        g.step_dt(dt)
+        assert o.step_dt(dt) == 0
+    for l in range(2):
+        assert (rel_l2(g.get_patch(l, 0), o.patch_state(l, 0)) <= FP64_TOL).all()
+
+
+def test_one_level_equals_the_uniform_solver(M):
+    from paper_2606_12162_gb300 import sgn
+    b, qs = W.amr_small_case(2, 40, 30, 2, 1, seed=9)
+    g = M.Hierarchy(b, 40, 30, 0.1, 2, [], model=2, bc=(0, 1, 1, 0), **CFG)
+    g.set_state(qs)
+    s = sgn.Solver(b, model=2, dx=0.1, bc=(0, 1, 1, 0), **CFG)
+    s.set_state(qs[0])
+    assert g.next_dt() == s.next_dt()
+    g.step(7)
+    s.step(7)
+    assert np.array_equal(g.get_patch(0, 0), s.get_state()[0])
+
+
+def test_mixed_hierarchy_against_fp64_oracle(M, A):
+    g, o, b = run_pair(M, A, 2, 24, 20, 2, W.amr_boxes_small(), 10, 10, precision=1, wetdry=False, amp=0.15)
+    for l in range(g.L):
+        for k in range(len(g.boxes[l])):
+            err = rel_l2(g.get_patch(l, k)[:3], o.patch_state(l, k)[:3])
+            assert err[0] <= 1e-5 and err[1] <= 1e-3 and err[2] <= 1e-3, (l, k, err)
+
+
+def test_lake_at_rest_and_mass(M, A):
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
+    rest = []
+    for l in range(3):
+        bl = b
+        for _ in range(2 - l):
+            bl = A.block_mean(bl, 2)
+        z = np.zeros_like(qs[l])
+        z[0] = np.maximum(bl, 0.0)
+        rest.append(z)
+    g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, bc=(0, 0, 1, 1), **CFG)
+    g.set_state(rest)
+    g.step(5)
+    for l in range(3):
+        for k in range(len(g.boxes[l])):
+            assert np.abs(g.get_patch(l, k)[1:]).max() <= 1e-14
+    # mass with walls over wet/dry bathymetry, up to the reported clipping
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=4, amp=0.3)
+    g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
+    g.set_state(qs)
+    m0, _ = g.mass()
+    g.step(12)
+    m, c = g.mass()
+    assert abs(m - m0 - c) <= 1e-12 * m0
+
+
+def test_invalid_hierarchies_are_rejected(M):
+    from paper_2606_12162_gb300 import sgn
+    b, _ = W.amr_small_case(2, 24, 20, 2, 2, seed=1)
+    for boxes in ([[(1, 8, 16, 12)]],                        # not aligned to parent cells
+                  [[(8, 8, 16, 12), (16, 12, 8, 8)]],        # overlapping
+                  [[(40, 8, 16, 8)]],                        # beyond the domain
+                  [[(2, 2, 8, 8)]]):                         # one parent cell from the edge
+        with pytest.raises(sgn.SGNError):
+            M.Hierarchy(b, 24, 20, 0.2, 2, boxes, model=2, **CFG)
