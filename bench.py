@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-line", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the refined-hierarchy (config 4) line")
+    ap.add_argument("--batched-n0", type=int, default=1024, help="level-0 size of the config-4 hierarchy")
     return ap.parse_args()
 
 
@@ -313,6 +315,51 @@ def time_path(S, c, args, precision, profile):
     return s, ms, kt, f
 
 
+def time_batched(args):
+    """Config 4 (three levels, ratio 4, ~2000 patches along a wave front), mixed
+    precision: W level-0 steps of warm-up, then K level-0 steps (each with all
+    finer substeps, one CUDA graph) between CUDA events on the stream."""
+    import torch
+    from paper_2606_12162_gb300 import amr, workloads as W
+    t0 = time.perf_counter()
+    c = W.config4(n0=args.batched_n0)
+    g = amr.Hierarchy(c["b"], c["n0"], c["n0"], c["dx0"], c["r"], c["boxes"], model=c["model"], bc=c["bc"],
+                      precision=1, alpha=c["alpha"], h_star=c["h_star"], cfl=c["cfl"], dry_tol=c["dry_tol"])
+    for l, lv in enumerate(c["states"]):
+        for k, q in enumerate(lv):
+            g.set_patch(l, k, q)
+    setup = time.perf_counter() - t0
+    del c["b"]
+    g.step(max(1, args.warmup))
+    k = max(3, min(args.steps, 20))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rc = g.step_rc(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells, atlas = g.info()
+    r = c["r"]
+    per_step = sum(n * r ** l for l, n in enumerate(cells))           # interior cell-updates per level-0 step
+    atlas_per_step = sum(n * r ** l for l, n in enumerate(atlas))
+    nf = c["n0"] * r ** (len(cells) - 1)
+    fine_equiv = float(nf) * nf * r ** (len(cells) - 1)                # uniform finest grid, same span
+    m, clipped = g.mass()
+    return {"value": per_step * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
+            "dtype": "f32+f64", "status": rc,
+            "workload": "config4: 3 levels, ratio 4, level 0 %dx%d at 2 km, fractal bathymetry + coast strip, "
+                        "%d patches (16..128 cells) along a ring front, 2 m Gaussian uplift, HSGN"
+                        % (c["n0"], c["n0"], sum(len(b) for b in c["boxes"])),
+            "patches_per_level": [1] + [len(b) for b in c["boxes"]],
+            "interior_cells_per_level": cells, "atlas_cells_per_level": atlas,
+            "cell_updates_per_step": per_step, "atlas_cell_updates_per_step": atlas_per_step,
+            "fine_equivalent_cell_updates_per_s": fine_equiv * k / (ms / 1e3),
+            "gpu_launches": g.launches_per_step() * k, "setup_s": setup,
+            "mass": m, "clipped": clipped}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -382,6 +429,16 @@ def main():
                  "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt2.items() if v[1]}}
         del s2
 
+    batched = None
+    if not args.no_batched:
+        batched = time_batched(args)
+        bms = reduce_max(batched["ms_per_step"], ws)          # replicas: slowest rank
+        batched["value"] = batched["cell_updates_per_step"] * ws / (bms / 1e3)
+        batched["fine_equivalent_cell_updates_per_s"] *= ws * batched["ms_per_step"] / bms
+        batched["ms_per_step"] = bms
+        if extra:
+            batched["vs_fp64_uniform"] = batched["value"] / extra["value"]
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args)
@@ -408,6 +465,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64": extra,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

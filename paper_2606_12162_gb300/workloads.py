@@ -258,3 +258,119 @@ def amr_boxes_small():
     lvl1 = [(8, 8, 16, 12), (24, 8, 8, 12), (0, 28, 12, 12)]
     lvl2 = [(20, 20, 16, 12), (52, 20, 8, 8)]
     return [lvl1, lvl2]
+
+
+# --------------------------------------------------------------------------
+# Config 4: three refinement levels, ratio 4, level 0 1024 x 1024 at 2 km over
+# a fractal bathymetry with a sloping coast strip; patches of seeded sizes
+# 16..128 cells (multiples of 8) along the advancing front of a ring wave.
+def config4_bathymetry(n0=1024, r=4, levels=3, seed=4001, depth=6000.0):
+    """Finest-level bathymetry (n0 r^(L-1))^2: a fractal field (|k|^-2, seed
+    4001) on a 4x coarser grid, bilinearly refined, plus a coast strip rising
+    1:100 to at most +50 m over the last 8 % of the domain in x."""
+    R = r ** (levels - 1)
+    nf = n0 * R
+    nb = nf // 4
+    base = fractal_bathymetry(nb, seed, depth=depth, land_frac=0.1)
+    t = (np.arange(nf) + 0.5) / 4.0 - 0.5
+    i0 = np.clip(np.floor(t).astype(np.int64), 0, nb - 2)
+    w = np.clip(t - i0, 0.0, 1.0)
+    rows = base[i0] * (1.0 - w)[:, None] + base[i0 + 1] * w[:, None]
+    b = rows[:, i0] * (1.0 - w)[None, :] + rows[:, i0 + 1] * w[None, :]
+    del rows
+    dxf = 2000.0 / R
+    x = (np.arange(nf) + 0.5) * dxf
+    xc = 0.92 * nf * dxf
+    b += np.where(x > xc, (x - xc) / 100.0, 0.0)[None, :]
+    np.minimum(b, 50.0, out=b)
+    return b
+
+
+def _seeded_cuts(rng, a0, a1, sizes):
+    """Cut [a0, a1) into consecutive lengths drawn from `sizes`; the last piece
+    takes the remainder (split in two if it would exceed the largest size)."""
+    cuts, x = [], a0
+    lo, hi = min(sizes), max(sizes)
+    while x < a1:
+        w = int(rng.choice(sizes))
+        if a1 - (x + w) < lo:
+            w = a1 - x
+            if w > hi:
+                h1 = (w // 2) // 8 * 8
+                cuts.append((x, h1))
+                x, w = x + h1, w - h1
+        cuts.append((x, w))
+        x += w
+    return cuts
+
+
+def config4_boxes(n0=1024, r=4, levels=3, seed=4001, centre=(0.45, 0.5), radius=300e3, width=70e3, dx0=2000.0,
+                  sizes=tuple(range(16, 129, 8))):
+    """Patches along the front of a ring wave (radius 300 km, a flagged band
+    70 km wide around it: the |d eta| flag of an expanding ring).  The region a
+    level may refine (the whole grid for level 1; each level-1 box two level-1
+    cells inside its edges for level 2) is cut into rows and columns of seeded
+    sizes 16..128 cells (multiples of 8); every tile holding a flagged cell
+    becomes a box.  Returns [level-1 boxes, level-2 boxes]."""
+    rng = np.random.default_rng(seed)
+    cx, cy = centre[0] * n0 * dx0, centre[1] * n0 * dx0
+
+    def flagged(level, X, Y):
+        d = dx0 / r ** level
+        rr = np.hypot((X + 0.5) * d - cx, (Y + 0.5) * d - cy)
+        return np.abs(rr - radius) < 0.5 * width
+
+    out = []
+    parents = [(0, 0, n0, n0)]
+    for level in range(1, levels):
+        Np = n0 * r ** (level - 1)
+        boxes = []
+        for (pi0, pj0, pnx, pny) in parents:
+            m0 = 0 if level == 1 else 2 * r
+            a0 = pi0 * r + (0 if pi0 == 0 else m0)
+            a1 = (pi0 + pnx) * r - (0 if pi0 + pnx == Np else m0)
+            b0 = pj0 * r + (0 if pj0 == 0 else m0)
+            b1 = (pj0 + pny) * r - (0 if pj0 + pny == Np else m0)
+            a0, b0 = (a0 + 7) // 8 * 8, (b0 + 7) // 8 * 8
+            a1, b1 = a1 // 8 * 8, b1 // 8 * 8
+            if a1 - a0 < min(sizes) or b1 - b0 < min(sizes):
+                continue
+            for (j0, h) in _seeded_cuts(rng, b0, b1, sizes):
+                for (i0, w) in _seeded_cuts(rng, a0, a1, sizes):
+                    ys, xs = np.mgrid[j0:j0 + h:8, i0:i0 + w:8]
+                    if flagged(level, xs + 4, ys + 4).any():
+                        boxes.append((int(i0), int(j0), int(w), int(h)))
+        out.append(boxes)
+        parents = boxes
+    return out
+
+
+def config4(model=HSGN, n0=1024, r=4, levels=3, amp=2.0, radius=30e3, centre=(0.45, 0.5), boxes=None):
+    """Config 4 input: finest bathymetry, boxes, and the initial state of every
+    patch (Gaussian uplift of 2 m, radius 30 km, at the ring centre, over the
+    ocean only), states[level][patch] of shape (nvar, ny, nx)."""
+    dx0 = 2000.0
+    b = config4_bathymetry(n0, r, levels)
+    if boxes is None:
+        boxes = config4_boxes(n0, r, levels, centre=centre, dx0=dx0)
+    cx, cy = centre[0] * n0 * dx0, centre[1] * n0 * dx0
+    allboxes = [[(0, 0, n0, n0)]] + boxes
+    R = r ** (levels - 1)
+    states = []
+    for level, bxs in enumerate(allboxes):
+        d = dx0 / r ** level
+        f = r ** (levels - 1 - level)      # finest cells per cell of this level
+        lv = []
+        for (i0, j0, nx, ny) in bxs:
+            blk = b[j0 * f:(j0 + ny) * f, i0 * f:(i0 + nx) * f]
+            bb = blk.reshape(ny, f, nx, f).mean(axis=(1, 3)) if f > 1 else blk
+            x = (np.arange(i0, i0 + nx) + 0.5) * d
+            y = (np.arange(j0, j0 + ny) + 0.5) * d
+            rr2 = (x[None, :] - cx) ** 2 + (y[:, None] - cy) ** 2
+            q = np.zeros((NVAR[model], ny, nx))
+            q[0] = apply_surface(bb, amp * np.exp(-rr2 / radius ** 2))
+            lv.append(q)
+        states.append(lv)
+    del R
+    return dict(b=b, boxes=boxes, states=states, n0=n0, r=r, dx0=dx0, bc=(1, 1, 1, 1), model=model,
+                alpha=3.0, h_star=20.0, cfl=0.9, dry_tol=1e-3)
