@@ -20,7 +20,8 @@
  *  - ghost cells: boundary condition (outside the domain), copy from another
  *    patch of the level, or limited interpolation of surface and primitives
  *    from the parent at the substep's time weight (a dry parent cell gives a
- *    ghost at the still level);
+ *    ghost at the still level; a conserved ghost value never exceeds the
+ *    parent cell's own in magnitude);
  *  - positivity factors of ghost cells copied from a patch are taken from it;
  *  - mass is refluxed at coarse faces between covered and uncovered cells (a
  *    correction that would leave a negative depth is clipped to zero depth and

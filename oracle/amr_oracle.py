@@ -32,9 +32,13 @@ below are the readings the CUDA hierarchy implements as well.
     sub-cell offset ((s + 1/2)/r - 1/2 in coarse cells), a one-sided difference
     counting only towards a wet coarse neighbour inside the domain (else that
     slope is 0); eta is raised to the ghost cell's own b where it falls below
-    it, and the conserved fields are the ghost depth times the primitives (zero
-    when that depth is at most dry_tol).  Interpolating velocities rather than
-    momenta keeps a thin interpolated layer from getting a large velocity.
+    it, and each conserved field is the ghost depth times its primitive (zero
+    when that depth is at most dry_tol), bounded in magnitude by the coarse
+    cell's own conserved value (time-interpolated) and set to zero where the two
+    differ in sign.  Interpolating velocities keeps a thin interpolated layer
+    from getting a large velocity; the bound keeps a deep sub-cell of a coarse
+    cell that is mostly dry (small mean depth, unreliable velocity) from getting
+    a large momentum.
  A5 Subcycling: a level-l step of dt_l is followed by r steps of dt_l / r of
     level l + 1 at time weights k / r, k = 0..r-1, then average-down and reflux.
  A6 Positivity factors of ghost cells copied from a patch of the same level are
@@ -362,8 +366,11 @@ class AmrOracle:
                     bf = p["b"][J, I]
                     out[0] = max(out[0], bf)
                     hf = out[0] - bf
+                    cc = (1.0 - a) * qo[:, Jp, Ip] + a * qn[:, Jp, Ip]
                     for f in range(1, self.nv):
-                        out[f] = hf * out[f] if hf > self.dry_tol else 0.0
+                        v = hf * out[f] if hf > self.dry_tol else 0.0
+                        # no larger than the coarse cell's own conserved value (A4)
+                        out[f] = (v if abs(v) <= abs(cc[f]) else cc[f]) if v * cc[f] > 0.0 else 0.0
                     q[:, J, I] = out
         for p in pats:
             q = p["q"]

@@ -186,9 +186,10 @@ def generate_pairs(nc=512, r=4, dxc=2000.0, scenarios=range(40), times=(60.0, 12
         stats.setdefault("gauges", {})
     for s in scenarios:
         cx, cy, amp, rad = scenario_source(bc, dxc, s)
+        # the same source evaluated on each grid (a restriction of the fine
+        # state would put water on coarse cells that hold fine land)
         qf0 = source_state(model, bf, dxf, cx, cy, amp, rad)
-        qc0 = np.zeros((nv, nc, nc))
-        qc0[0] = qf0[0].reshape(nc, r, nc, r).mean(axis=(1, 3))
+        qc0 = source_state(model, bc, dxc, cx, cy, amp, rad)
         sf.set_state(qf0)
         sc.set_state(qc0)
         sf.cfl_dt = sc.cfl_dt = 0.0

@@ -88,7 +88,13 @@ __global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t,
   const double hf = out[0] - bf;
   qc[g.dst] = (Real)out[0];
 #pragma unroll
-  for (int k = 1; k < NV; k++) qc[k * c.fs + g.dst] = (Real)(hf > dry ? hf * out[k] : 0.0);
+  for (int k = 1; k < NV; k++) {
+    // depth x primitive, no larger than the parent cell's own conserved value
+    // (a mostly dry parent has a small mean depth and an unreliable velocity)
+    const double v = hf > dry ? hf * out[k] : 0.0;
+    const double cv = (1.0 - a) * (double)qo[k * p.fs + ic] + a * (double)qn[k * p.fs + ic];
+    qc[k * c.fs + g.dst] = (Real)(v * cv > 0.0 ? (fabs(v) <= fabs(cv) ? v : cv) : 0.0);
+  }
 }
 
 template <int MODEL, typename Real>
