@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-fp64-line", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the refined-hierarchy (config 4) line")
     ap.add_argument("--batched-n0", type=int, default=1024, help="level-0 size of the config-4 hierarchy")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector (config 5) line")
+    ap.add_argument("--only", default=None, choices=["batched", "learned"],
+                    help="run only that line (for profiling); prints its object alone")
     return ap.parse_args()
 
 
@@ -330,13 +333,13 @@ def time_batched(args):
             g.set_patch(l, k, q)
     setup = time.perf_counter() - t0
     del c["b"]
-    g.step(max(1, args.warmup))
+    rc0 = g.step_rc(max(1, args.warmup))
     k = max(3, min(args.steps, 20))
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    rc = g.step_rc(k)
+    rc = g.step_rc(k) if rc0 == 0 else rc0
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -360,6 +363,63 @@ def time_batched(args):
             "mass": m, "clipped": clipped}
 
 
+def time_learned(args, nc=1024, r=4, dxc=2000.0, snapshot_s=60.0):
+    """Config 5 form (coarse 1024^2 at 2 km + the corrector to the 4096^2 level):
+    K coarse steps of the mixed solver between CUDA events, and the corrector's
+    inference (input assembly, 5 x 3x3 conv layers of 32 channels, corrected
+    prolongation) timed the same way; the learned form delivers fine-level
+    states at one inference per `snapshot_s` of simulated time.  The network's
+    cost does not depend on its weights (untrained here); its error comes from
+    the corrector experiment (python -m paper_2606_12162_gb300.corrector)."""
+    import torch
+    from paper_2606_12162_gb300 import corrector as C, sgn as S, workloads as W
+    bf, bc = C.scenario_bathymetry(nc, r)
+    cx, cy, amp, rad = C.scenario_source(bc, dxc, 32)
+    q = C.source_state(W.HSGN, bc, dxc, cx, cy, amp, rad)
+    sv = S.Solver(bc, dx=dxc, model=W.HSGN, bc=(1, 1, 1, 1), h_star=20.0, alpha=3.0, precision=S.MIXED)
+    sv.set_state(q)
+    sv.step(max(1, args.warmup))
+    k = max(3, min(args.steps, 50))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rc = sv.step_rc(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / k
+    dtc = sv.status()[1]
+    net = C.Net(cin=5, width=32, depth=5, r=r, max_hw=nc * nc, seed=5000)
+    qc = torch.empty((W.NVAR[W.HSGN], nc, nc), dtype=torch.float64, device="cuda")
+    sv.get_state_device(qc)
+    _, phic = sv.aux()
+    bcd = torch.from_numpy(np.ascontiguousarray(bc)).cuda()
+    phid = torch.from_numpy(np.ascontiguousarray(phic)).cuda()
+    out = torch.empty((3, nc * r, nc * r), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        C.correct(net, qc, bcd, phid, out)
+    reps = 5
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        C.correct(net, qc, bcd, phid, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_inf = e0.elapsed_time(e1) / reps
+    steps_per_snapshot = snapshot_s / dtc
+    nf = nc * r
+    fine_per_coarse = float(nf) * nf * r          # the fine grid takes r steps per coarse step
+    per_step_ms = ms_step + ms_inf / steps_per_snapshot
+    return {"value": fine_per_coarse / (per_step_ms / 1e3), "unit": UNIT, "steps": k, "status": rc,
+            "coarse_ms_per_step": ms_step, "inference_ms": ms_inf, "coarse_dt_s": dtc,
+            "inference_per_coarse_steps": steps_per_snapshot, "dtype": "f32+f64 solve, bf16/f32 network",
+            "workload": "config5 form: coarse %dx%d at %.0f m (fractal bathymetry, seed 5001, smoothed), HSGN "
+                        "mixed, corrector to %dx%d every %.0f s of simulated time" % (nc, nc, dxc, nf, nf, snapshot_s),
+            "coarse_cell_updates_per_s": float(nc) * nc / (ms_step / 1e3),
+            "fine_cell_updates_per_coarse_step": fine_per_coarse,
+            "network_gflop": 2.0 * sum(ci * co * 9 for ci, co in net.layers()) * nc * nc * 1e-9}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -370,6 +430,11 @@ def main():
     ws, rank, local = dist_setup()
     build.build()
     S.load()
+    if args.only:
+        res = time_batched(args) if args.only == "batched" else time_learned(args)
+        if rank == 0:
+            print(json.dumps({args.only: res}), flush=True)
+        return
     c = workload(args)
     prec = 1 if args.precision == "mixed" else 0
     nv = S.NVAR[c["model"]]
@@ -439,6 +504,15 @@ def main():
         if extra:
             batched["vs_fp64_uniform"] = batched["value"] / extra["value"]
 
+    learned = None
+    if not args.no_learned:
+        learned = time_learned(args)
+        lms = reduce_max(learned["coarse_ms_per_step"] + learned["inference_ms"] /
+                         learned["inference_per_coarse_steps"], ws)
+        learned["value"] = learned["fine_cell_updates_per_coarse_step"] * ws / (lms / 1e3)
+        if extra:
+            learned["vs_fp64_uniform"] = learned["value"] / extra["value"]
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args)
@@ -466,6 +540,7 @@ def main():
             "cpu_baseline": cpu,
             "fp64": extra,
             "batched": batched,
+            "learned": learned,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -266,12 +266,15 @@ def amr_boxes_small():
 # 16..128 cells (multiples of 8) along the advancing front of a ring wave.
 def config4_bathymetry(n0=1024, r=4, levels=3, seed=4001, depth=6000.0):
     """Finest-level bathymetry (n0 r^(L-1))^2: a fractal field (|k|^-2, seed
-    4001) on a 4x coarser grid, bilinearly refined, plus a coast strip rising
-    1:100 to at most +50 m over the last 8 % of the domain in x."""
+    4001) on a 4x coarser grid, low-pass filtered (Gaussian, 4 cells of that
+    grid: the level-0 spacing, so that level 0 resolves the coasts), bilinearly
+    refined, plus a coast strip rising 1:100 to at most +50 m over the last 8 %
+    of the domain in x."""
+    from scipy.ndimage import gaussian_filter
     R = r ** (levels - 1)
     nf = n0 * R
     nb = nf // 4
-    base = fractal_bathymetry(nb, seed, depth=depth, land_frac=0.1)
+    base = gaussian_filter(fractal_bathymetry(nb, seed, depth=depth, land_frac=0.1), 4.0, mode="nearest")
     t = (np.arange(nf) + 0.5) / 4.0 - 0.5
     i0 = np.clip(np.floor(t).astype(np.int64), 0, nb - 2)
     w = np.clip(t - i0, 0.0, 1.0)
@@ -373,4 +376,4 @@ def config4(model=HSGN, n0=1024, r=4, levels=3, amp=2.0, radius=30e3, centre=(0.
         states.append(lv)
     del R
     return dict(b=b, boxes=boxes, states=states, n0=n0, r=r, dx0=dx0, bc=(1, 1, 1, 1), model=model,
-                alpha=3.0, h_star=20.0, cfl=0.9, dry_tol=1e-3)
+                alpha=3.0, h_star=20.0, cfl=0.9, dry_tol=1e-2)
