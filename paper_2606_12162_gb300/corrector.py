@@ -30,7 +30,7 @@ LC_SIGS = [
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("lc_make_input", ctypes.c_int, [DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, DP, ctypes.c_void_p]),
-    ("lc_make_target", ctypes.c_int, [DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+    ("lc_make_target", ctypes.c_int, [DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                       ctypes.c_float, DP, ctypes.c_void_p]),
     ("lc_apply", ctypes.c_int, [DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_int, DP, ctypes.c_void_p]),
@@ -173,6 +173,7 @@ def generate_pairs(nc=512, r=4, dxc=2000.0, scenarios=range(40), times=(60.0, 12
     sf = sgn.Solver(bf, dx=dxf, **cfg)
     _, phic = sc.aux()
     bcd = torch.from_numpy(np.ascontiguousarray(bc)).cuda()
+    bfd = torch.from_numpy(np.ascontiguousarray(bf)).cuda()
     phid = torch.from_numpy(np.ascontiguousarray(phic)).cuda()
     nv = W.NVAR[model]
     qc = torch.empty((nv, nc, nc), dtype=torch.float64, device="cuda")
@@ -218,7 +219,7 @@ def generate_pairs(nc=512, r=4, dxc=2000.0, scenarios=range(40), times=(60.0, 12
             x = torch.empty((5, nc, nc), dtype=torch.float32, device="cuda")
             tg = torch.empty((3, nf, nf), dtype=torch.float32, device="cuda")
             _ck(L.lc_make_input(_p(qc), _p(bcd), _p(phid), nc, nc, S_ETA, S_Q, S_B, _p(x), st), "lc_make_input")
-            _ck(L.lc_make_target(_p(qf), _p(qc), nc, nc, r, S_ETA, S_Q, _p(tg), st), "lc_make_target")
+            _ck(L.lc_make_target(_p(qf), _p(qc), _p(bfd), nc, nc, r, S_ETA, S_Q, _p(tg), st), "lc_make_target")
             keep = keep_fine is None or keep_fine(s)
             mypairs.append(dict(x=x, t=tg, qc=qc[:3].clone(), qf=qf[:3].clone() if keep else None, scenario=s,
                                 time=T))
@@ -341,51 +342,60 @@ def predict_fine(net, pair, use_net=True):
     return out
 
 
-def evaluate(net, pairs, block=8, bound=0.05, indicator_thr=0.02):
-    """Relative L2 error of eta at the fine level, prolongation vs corrected, and
-    the fallback: per block of block x block coarse cells, blocks whose corrected
-    error (relative L2 against the fine solve, over the block) exceeds `bound` fall
-    back to the fine solve.  Also the a-priori indicator of the paper's refinement
-    flag, |d eta| between coarse neighbours > indicator_thr [m], and how many of
-    the over-bound blocks it flags (recall)."""
+def evaluate(net, pairs, block=8, bound=0.05, indicator_thr=0.02, ocean_f=None, ocean_c=None):
+    """Error of the fine-level surface over the ocean (ocean_f: fine cells with
+    b < 0; all cells if None; land keeps eta = b and carries no wave), plain
+    prolongation vs corrected, and the fallback: per block of block x block
+    coarse cells, blocks whose corrected error (relative L2 against the fine
+    solve over the block's ocean) exceeds `bound` fall back to the fine solve.
+    Also the a-priori indicator of the paper's refinement flag, |d eta| > 
+    indicator_thr [m] between neighbouring coarse ocean cells (ocean_c), and how
+    many of the over-bound blocks it flags (recall)."""
     import torch
     r = net.r
     rows = []
     for p in pairs:
         qf = p["qf"]
         eta_f = qf[0]
+        m = torch.ones_like(eta_f) if ocean_f is None else ocean_f.to(eta_f.dtype)
         pp = predict_fine(net, p, use_net=False)[0]
         pn = predict_fine(net, p, use_net=True)[0]
-        e_p = torch.linalg.norm(pp - eta_f).item()
-        e_n = torch.linalg.norm(pn - eta_f).item()
+        e_p = torch.linalg.norm((pp - eta_f) * m).item()
+        e_n = torch.linalg.norm((pn - eta_f) * m).item()
+        ref = torch.linalg.norm(eta_f * m).item()
         nf = eta_f.shape[0]
         nb = nf // (block * r)
         bsz = block * r
-        d2 = ((pn - eta_f) ** 2)[:nb * bsz, :nb * bsz].reshape(nb, bsz, nb, bsz).sum(dim=(1, 3))
-        ref2 = ((eta_f - eta_f.mean()) ** 2)[:nb * bsz, :nb * bsz].reshape(nb, bsz, nb, bsz).sum(dim=(1, 3))
-        sig = (eta_f.abs().max().item() ** 2) * bsz * bsz * 1e-6
+        cut = (slice(0, nb * bsz), slice(0, nb * bsz))
+        d2 = (((pn - eta_f) * m) ** 2)[cut].reshape(nb, bsz, nb, bsz).sum(dim=(1, 3))
+        ref2 = ((eta_f * m) ** 2)[cut].reshape(nb, bsz, nb, bsz).sum(dim=(1, 3))
+        sig = ((eta_f * m).abs().max().item() ** 2) * bsz * bsz * 1e-6
         rel = torch.sqrt(d2 / (ref2 + sig))
         over = rel > bound
         # hybrid: fine solve on the fallback blocks, corrected field elsewhere
         mask = over.repeat_interleave(bsz, 0).repeat_interleave(bsz, 1)
         hyb = pn.clone()
-        hyb[:nb * bsz, :nb * bsz][mask] = eta_f[:nb * bsz, :nb * bsz][mask]
-        e_h = torch.linalg.norm(hyb - eta_f).item()
+        hyb[cut][mask] = eta_f[cut][mask]
+        e_h = torch.linalg.norm((hyb - eta_f) * m).item()
         ec = p["qc"][0]
-        gx = (ec[:, 1:] - ec[:, :-1]).abs()
-        gy = (ec[1:, :] - ec[:-1, :]).abs()
+        oc = torch.ones_like(ec, dtype=torch.bool) if ocean_c is None else ocean_c
+        gx = ((ec[:, 1:] - ec[:, :-1]).abs() > indicator_thr) & oc[:, 1:] & oc[:, :-1]
+        gy = ((ec[1:, :] - ec[:-1, :]).abs() > indicator_thr) & oc[1:, :] & oc[:-1, :]
         flag = torch.zeros_like(ec, dtype=torch.bool)
-        flag[:, 1:] |= gx > indicator_thr
-        flag[:, :-1] |= gx > indicator_thr
-        flag[1:, :] |= gy > indicator_thr
-        flag[:-1, :] |= gy > indicator_thr
+        flag[:, 1:] |= gx
+        flag[:, :-1] |= gx
+        flag[1:, :] |= gy
+        flag[:-1, :] |= gy
         ncb = nb * block
         fb = flag[:ncb, :ncb].reshape(nb, block, nb, block).any(dim=3).any(dim=1)
         recall = (fb & over).sum().item() / max(over.sum().item(), 1)
         rows.append(dict(scenario=p["scenario"], time=p["time"], err_prolong=e_p, err_net=e_n, err_hybrid=e_h,
+                         rel_prolong=e_p / max(ref, 1e-300), rel_net=e_n / max(ref, 1e-300),
+                         rel_hybrid=e_h / max(ref, 1e-300),
                          gain=e_p / max(e_n, 1e-300), fallback_frac=over.float().mean().item(),
                          indicator_frac=fb.float().mean().item(), indicator_recall=recall))
     return rows
+
 
 
 def correct(net, qc, bcd, phid, out=None):
@@ -441,19 +451,16 @@ def experiment(nc=1024, r=4, dxc=2000.0, n_train=32, n_held=8, times=(60.0, 120.
     res["train_s"] = time.perf_counter() - t0
     res["loss_first50"] = float(losses[:50].mean())
     res["loss_last50"] = float(losses[-50:].mean())
-    rows = evaluate(net, held, block, bound)
+    ocean_f = torch.from_numpy(meta["bf"] < 0.0).cuda()
+    ocean_c = torch.from_numpy(meta["bc"] < 0.0).cuda()
+    rows = evaluate(net, held, block, bound, ocean_f=ocean_f, ocean_c=ocean_c)
     res["rows"] = rows
-    for k in ("err_prolong", "err_net", "err_hybrid", "gain", "fallback_frac", "indicator_frac",
+    for k in ("rel_prolong", "rel_net", "rel_hybrid", "gain", "fallback_frac", "indicator_frac",
               "indicator_recall"):
         v = np.array([row[k] for row in rows])
         res[k + "_median"] = float(np.median(v))
         res[k + "_min"] = float(v.min())
         res[k + "_max"] = float(v.max())
-    rel_p = [_rel_l2(predict_fine(net, p, False)[0], p["qf"][0]) for p in held]
-    rel_n = [_rel_l2(predict_fine(net, p, True)[0], p["qf"][0]) for p in held]
-    res["rel_l2_eta_prolong_median"] = float(np.median(rel_p))
-    res["rel_l2_eta_net_median"] = float(np.median(rel_n))
-    res["rel_l2_eta_net_max"] = float(np.max(rel_n))
     # inference time per snapshot (input assembly, network, corrected prolongation)
     bcd = torch.from_numpy(np.ascontiguousarray(meta["bc"])).cuda()
     phid = torch.from_numpy(np.ascontiguousarray(meta["phic"])).cuda()
@@ -522,9 +529,9 @@ def experiment(nc=1024, r=4, dxc=2000.0, n_train=32, n_held=8, times=(60.0, 120.
                 wall += time.perf_counter() - t0
                 nst += k
                 sv.get_state_device(q64)
-                e_mixed.append(_rel_l2(p["qf"][0], q64[0]))
-                e_net.append(_rel_l2(predict_fine(net, p, True)[0], q64[0]))
-                e_pro.append(_rel_l2(predict_fine(net, p, False)[0], q64[0]))
+                e_mixed.append(_rel_l2(p["qf"][0] * ocean_f, q64[0] * ocean_f))
+                e_net.append(_rel_l2(predict_fine(net, p, True)[0] * ocean_f, q64[0] * ocean_f))
+                e_pro.append(_rel_l2(predict_fine(net, p, False)[0] * ocean_f, q64[0] * ocean_f))
         except sgn.SGNError as e:
             res["fp64_error"] = dict(scenario=s, time=tt, error=str(e))
         sv.close()
