@@ -179,6 +179,17 @@ int sgn_mass(sgn_solver* s, double* mass);
  * bytes) of the interior cells; either pointer may be NULL. */
 int sgn_get_aux(sgn_solver* s, double* c2, unsigned char* phi);
 
+/* Well-prepared initial data for mbHSGN (Sec. 3.2): replaces hw and hp of the
+ * current state by h w and h p, w from the mbSGN constraint and p from the
+ * relation of Sec. 3.2 with d_t u eliminated (readings G26, G27 of the design
+ * notes: w = -(h/2) u_x + u b_x; p re-derived from the hw equation and that
+ * constraint), for data varying along x: every row is solved independently
+ * (one tridiagonal system per row, zero-gradient ends); rows with a dry cell
+ * are left unchanged.  mbHSGN solvers only (else EINVAL).  The first call
+ * allocates 7 nx ny doubles of scratch through the solver's allocator (ENOMEM).
+ * Recomputes the next time step.  Synchronises the stream. */
+int sgn_well_prepare(sgn_solver* s);
+
 /* Per-kernel timing: when enabled, steps launch kernels without CUDA graphs and
  * bracket each launch with CUDA events on the solver stream.  sgn_kernel_times
  * returns, for up to n kernels, the name, the accumulated time [ms] and the

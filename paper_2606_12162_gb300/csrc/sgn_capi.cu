@@ -189,6 +189,11 @@ int sgn_mass(sgn_solver* s, double* mass) {
   return s->impl->mass(mass);
 }
 
+int sgn_well_prepare(sgn_solver* s) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->well_prepare();
+}
+
 int sgn_get_aux(sgn_solver* s, double* c2, unsigned char* phi) {
   if (!s) return SGN_EINVAL;
   return s->impl->get_aux(c2, phi);

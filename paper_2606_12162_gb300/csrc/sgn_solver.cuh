@@ -35,6 +35,7 @@ struct SolverBase {
   virtual int next_dt(double* dt) = 0;
   virtual int mass(double* m) = 0;
   virtual int get_aux(double* c2, unsigned char* phi) = 0;
+  virtual int well_prepare() = 0;
   virtual int set_profiling(int on) = 0;
   virtual int kernel_times(const char** names, double* ms, long* launches, int n) = 0;
   virtual int launches_per_step() = 0;
@@ -425,6 +426,24 @@ class Solver : public SolverBase {
     SGN_CK(cudaMemcpyAsync(hscal_ + 7, d_.mass, sizeof(double), cudaMemcpyDeviceToHost, st_));
     SGN_CK(cudaStreamSynchronize(st_));
     *m = hscal_[7];
+    return SGN_OK;
+  }
+
+  double* wp_scratch_ = nullptr;
+  int well_prepare() override {
+    if (MODEL != 1) return SGN_EINVAL;
+    if (!wp_scratch_) {
+      wp_scratch_ = dnew<double>((size_t)7 * d_.nx * d_.ny);
+      if (!wp_scratch_) return SGN_ENOMEM;
+    }
+    k_well_prepared<Real><<<(d_.ny + 127) / 128, 128, 0, st_>>>(d_, cur_, wp_scratch_);
+    SGN_CK(cudaGetLastError());
+    // the time step of the next step from the new state
+    SGN_CK(cudaMemsetAsync(d_.smax, 0, sizeof(unsigned long long), st_));
+    k_speed<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, cur_);
+    k_finalize<Real><<<1, 32, 0, st_>>>(d_, 0);
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaStreamSynchronize(st_));
     return SGN_OK;
   }
 

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("sgn_next_dt", ctypes.c_int, [ctypes.c_void_p, DP]),
     ("sgn_mass", ctypes.c_int, [ctypes.c_void_p, DP]),
     ("sgn_get_aux", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.c_void_p]),
+    ("sgn_well_prepare", ctypes.c_int, [ctypes.c_void_p]),
     ("sgn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sgn_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_char_p), DP,
                                         ctypes.POINTER(ctypes.c_long), ctypes.c_int]),
@@ -293,6 +294,10 @@ class Solver:
         phi = np.empty((self.ny, self.nx), dtype=np.uint8)
         _ck(load().sgn_get_aux(self.h, _dp(c2), phi.ctypes.data), "sgn_get_aux")
         return c2, phi
+
+    def well_prepare(self):
+        """Replace hw and hp by the well-prepared values of Sec. 3.2 (mbHSGN)."""
+        _ck(load().sgn_well_prepare(self.h), "sgn_well_prepare")
 
     def set_profiling(self, on):
         _ck(load().sgn_set_profiling(self.h, int(bool(on))), "sgn_set_profiling")
