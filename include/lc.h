@@ -60,12 +60,13 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
 int lc_make_input(const double* q_dev, const double* b_dev, const unsigned char* phi_dev, int Hc, int Wc,
                   float s_eta, float s_q, float s_b, float* x_dev, void* cuda_stream);
 /* target[3][r Hc][r Wc] = (q_fine - P q_coarse) / s, P the piecewise-constant
- * prolongation; s = (s_eta, s_q, s_q).  bf_dev (fine bathymetry, r Hc x r Wc,
- * may be NULL): where bf >= 0 (land at or above the still level) the surface
- * target is 0, so the network is not trained to reproduce sub-grid land
- * elevation. */
-int lc_make_target(const double* qf_dev, const double* qc_dev, const double* bf_dev, int Hc, int Wc, int r,
-                   float s_eta, float s_q, float* t_dev, void* cuda_stream);
+ * prolongation; s = (s_eta, s_q, s_q).  bf_dev (fine bathymetry, r Hc x r Wc)
+ * and bc_dev (coarse bathymetry, Hc x Wc), either may be NULL: the surface
+ * target is 0 on fine cells with bf >= 0 or whose coarse cell has bc >= 0 (land
+ * at or above the still level, where the surface is bathymetry rather than a
+ * wave), so the network is not trained to reproduce sub-grid land elevation. */
+int lc_make_target(const double* qf_dev, const double* qc_dev, const double* bf_dev, const double* bc_dev, int Hc,
+                   int Wc, int r, float s_eta, float s_q, float* t_dev, void* cuda_stream);
 /* out[3][r Hc][r Wc] = P q_coarse + s * shuffle(y) (y = lc_forward output); with
  * use_net == 0 the plain prolongation. */
 int lc_apply(const double* qc_dev, const float* y_dev, int Hc, int Wc, int r, float s_eta, float s_q,

@@ -30,7 +30,7 @@ LC_SIGS = [
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("lc_make_input", ctypes.c_int, [DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, DP, ctypes.c_void_p]),
-    ("lc_make_target", ctypes.c_int, [DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+    ("lc_make_target", ctypes.c_int, [DP, DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                       ctypes.c_float, DP, ctypes.c_void_p]),
     ("lc_apply", ctypes.c_int, [DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_int, DP, ctypes.c_void_p]),
@@ -219,7 +219,7 @@ def generate_pairs(nc=512, r=4, dxc=2000.0, scenarios=range(40), times=(60.0, 12
             x = torch.empty((5, nc, nc), dtype=torch.float32, device="cuda")
             tg = torch.empty((3, nf, nf), dtype=torch.float32, device="cuda")
             _ck(L.lc_make_input(_p(qc), _p(bcd), _p(phid), nc, nc, S_ETA, S_Q, S_B, _p(x), st), "lc_make_input")
-            _ck(L.lc_make_target(_p(qf), _p(qc), _p(bfd), nc, nc, r, S_ETA, S_Q, _p(tg), st), "lc_make_target")
+            _ck(L.lc_make_target(_p(qf), _p(qc), _p(bfd), _p(bcd), nc, nc, r, S_ETA, S_Q, _p(tg), st), "lc_make_target")
             keep = keep_fine is None or keep_fine(s)
             mypairs.append(dict(x=x, t=tg, qc=qc[:3].clone(), qf=qf[:3].clone() if keep else None, scenario=s,
                                 time=T))
@@ -344,13 +344,14 @@ def predict_fine(net, pair, use_net=True):
 
 def evaluate(net, pairs, block=8, bound=0.05, indicator_thr=0.02, ocean_f=None, ocean_c=None):
     """Error of the fine-level surface over the ocean (ocean_f: fine cells with
-    b < 0; all cells if None; land keeps eta = b and carries no wave), plain
-    prolongation vs corrected, and the fallback: per block of block x block
-    coarse cells, blocks whose corrected error (relative L2 against the fine
-    solve over the block's ocean) exceeds `bound` fall back to the fine solve.
-    Also the a-priori indicator of the paper's refinement flag, |d eta| > 
-    indicator_thr [m] between neighbouring coarse ocean cells (ocean_c), and how
-    many of the over-bound blocks it flags (recall)."""
+    b < 0 whose coarse cell has b < 0 as well; all cells if None: on land the
+    surface is bathymetry, not a wave), plain prolongation vs corrected,
+    relative to the surface's own norm over the ocean; and the fallback: blocks
+    of block x block coarse cells whose RMS corrected error over their ocean
+    exceeds `bound` x the RMS of the fine surface over the whole ocean fall
+    back to the fine solve.  Also the a-priori indicator of the paper's
+    refinement flag, |d eta| > indicator_thr [m] between neighbouring coarse
+    ocean cells (ocean_c), and how many of the over-bound blocks it flags."""
     import torch
     r = net.r
     rows = []
@@ -368,10 +369,9 @@ def evaluate(net, pairs, block=8, bound=0.05, indicator_thr=0.02, ocean_f=None, 
         bsz = block * r
         cut = (slice(0, nb * bsz), slice(0, nb * bsz))
         d2 = (((pn - eta_f) * m) ** 2)[cut].reshape(nb, bsz, nb, bsz).sum(dim=(1, 3))
-        ref2 = ((eta_f * m) ** 2)[cut].reshape(nb, bsz, nb, bsz).sum(dim=(1, 3))
-        sig = ((eta_f * m).abs().max().item() ** 2) * bsz * bsz * 1e-6
-        rel = torch.sqrt(d2 / (ref2 + sig))
-        over = rel > bound
+        nblk = m[cut].reshape(nb, bsz, nb, bsz).sum(dim=(1, 3)).clamp(min=1.0)
+        rms_all = ref / max(m.sum().item(), 1.0) ** 0.5
+        over = torch.sqrt(d2 / nblk) > bound * rms_all
         # hybrid: fine solve on the fallback blocks, corrected field elsewhere
         mask = over.repeat_interleave(bsz, 0).repeat_interleave(bsz, 1)
         hyb = pn.clone()
@@ -396,6 +396,16 @@ def evaluate(net, pairs, block=8, bound=0.05, indicator_thr=0.02, ocean_f=None, 
                          indicator_frac=fb.float().mean().item(), indicator_recall=recall))
     return rows
 
+
+
+def ocean_masks(meta):
+    """(fine cells with b < 0 whose coarse cell has b < 0, coarse cells with
+    b < 0) as device booleans."""
+    import torch
+    r = meta["r"]
+    bc = meta["bc"]
+    pc = np.repeat(np.repeat(bc < 0.0, r, axis=0), r, axis=1)
+    return torch.from_numpy((meta["bf"] < 0.0) & pc).cuda(), torch.from_numpy(bc < 0.0).cuda()
 
 
 def correct(net, qc, bcd, phid, out=None):
@@ -451,8 +461,7 @@ def experiment(nc=1024, r=4, dxc=2000.0, n_train=32, n_held=8, times=(60.0, 120.
     res["train_s"] = time.perf_counter() - t0
     res["loss_first50"] = float(losses[:50].mean())
     res["loss_last50"] = float(losses[-50:].mean())
-    ocean_f = torch.from_numpy(meta["bf"] < 0.0).cuda()
-    ocean_c = torch.from_numpy(meta["bc"] < 0.0).cuda()
+    ocean_f, ocean_c = ocean_masks(meta)
     rows = evaluate(net, held, block, bound, ocean_f=ocean_f, ocean_c=ocean_c)
     res["rows"] = rows
     for k in ("rel_prolong", "rel_net", "rel_hybrid", "gain", "fallback_frac", "indicator_frac",

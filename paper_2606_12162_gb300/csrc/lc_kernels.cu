@@ -233,8 +233,8 @@ __global__ void k_make_input(const double* __restrict__ q, const double* __restr
 }
 
 __global__ void k_make_target(const double* __restrict__ qf, const double* __restrict__ qc,
-                              const double* __restrict__ bf, int Hc, int Wc, int r, float se, float sq,
-                              float* __restrict__ t) {
+                              const double* __restrict__ bf, const double* __restrict__ bc, int Hc, int Wc, int r,
+                              float se, float sq, float* __restrict__ t) {
   long Wf = (long)Wc * r, n = (long)Hc * r * Wf;
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * n) return;
@@ -243,9 +243,9 @@ __global__ void k_make_target(const double* __restrict__ qf, const double* __res
   long Y = p / Wf, X = p - Y * Wf;
   size_t ic = (size_t)f * Hc * Wc + (size_t)(Y / r) * Wc + (X / r);
   float s = f == 0 ? se : sq;
-  // fine land at or above the still level: no surface target (its eta is its
-  // bathymetry, not a wave)
-  if (f == 0 && bf && bf[p] >= 0.0) { t[i] = 0.f; return; }
+  // fine land, or a fine cell whose coarse cell is land, at or above the still
+  // level: no surface target (its eta is bathymetry, not a wave)
+  if (f == 0 && ((bf && bf[p] >= 0.0) || (bc && bc[ic] >= 0.0))) { t[i] = 0.f; return; }
   t[i] = (float)((qf[i] - qc[ic]) / s);
 }
 
@@ -473,12 +473,12 @@ int lc_make_input(const double* q_dev, const double* b_dev, const unsigned char*
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int lc_make_target(const double* qf_dev, const double* qc_dev, const double* bf_dev, int Hc, int Wc, int r,
-                   float s_eta, float s_q, float* t_dev, void* cuda_stream) {
+int lc_make_target(const double* qf_dev, const double* qc_dev, const double* bf_dev, const double* bc_dev, int Hc,
+                   int Wc, int r, float s_eta, float s_q, float* t_dev, void* cuda_stream) {
   if (!qf_dev || !qc_dev || !t_dev || Hc <= 0 || Wc <= 0 || r <= 0) return -1;
   long nn = 3L * Hc * r * Wc * r;
-  k_make_target<<<nblk(nn, 256), 256, 0, (cudaStream_t)cuda_stream>>>(qf_dev, qc_dev, bf_dev, Hc, Wc, r, s_eta,
-                                                                        s_q, t_dev);
+  k_make_target<<<nblk(nn, 256), 256, 0, (cudaStream_t)cuda_stream>>>(qf_dev, qc_dev, bf_dev, bc_dev, Hc, Wc, r,
+                                                                        s_eta, s_q, t_dev);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -32,15 +32,14 @@ constexpr int AMR_MAXL = 8;
 struct GEnt { int dst, src, info; };
 enum { GE_SIB = 0, GE_PAR = 1, GE_BC = 2 };
 
-__device__ __forceinline__ double amr_minmod(double a, double b) {
-  if (a * b <= 0.0) return 0.0;
-  return fabs(a) < fabs(b) ? a : b;
-}
-
 template <int MODEL, typename Real>
 __global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t, int n, int cc, int pold, int pnew,
                            double a, int r) {
   constexpr int NV = MT<MODEL>::NV;
+  // the interpolation runs in the bulk type (the depth of a parent cell, which
+  // decides dry or wet, in FP64): a ghost value is an input of the step, not
+  // one of its balanced or positivity-critical terms
+  typedef Real A;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const GEnt g = t[e];
@@ -53,21 +52,22 @@ __global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t,
   const int sx = (g.info >> 8) & 255, sy = (g.info >> 16) & 255, nb = (g.info >> 24) & 15;
   const Real* qo = p.q[pold];
   const Real* qn = p.q[pnew];
-  const double dry = c.dry_tol;
+  const A a1 = A(a), a0 = A(1.0 - a);
   // surface and primitives of a parent cell at the time weight (false: dry)
-  auto prim = [&](size_t id, double* o) -> bool {
-    double v[NV];
+  auto prim = [&](size_t id, A* o) -> bool {
+    A v[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) v[k] = (1.0 - a) * (double)qo[k * p.fs + id] + a * (double)qn[k * p.fs + id];
-    double h = v[0] - (double)p.b[id];
-    if (!(h > dry)) return false;
+    for (int k = 0; k < NV; k++) v[k] = a0 * (A)qo[k * p.fs + id] + a1 * (A)qn[k * p.fs + id];
+    double hd = (1.0 - a) * (double)qo[id] + a * (double)qn[id] - (double)p.b[id];
+    if (!(hd > c.dry_tol)) return false;
+    A ih = A(1) / A(hd);
     o[0] = v[0];
 #pragma unroll
-    for (int k = 1; k < NV; k++) o[k] = v[k] / h;
+    for (int k = 1; k < NV; k++) o[k] = v[k] * ih;
     return true;
   };
   const double bf = (double)c.b[g.dst];
-  double pc[NV], pw[NV], pe[NV], ps[NV], pn[NV], out[NV];
+  A pc[NV], pw[NV], pe[NV], ps[NV], pn[NV], out[NV];
   const size_t ic = (size_t)g.src;
   if (!prim(ic, pc)) {
     qc[g.dst] = (Real)(bf > 0.0 ? bf : 0.0);
@@ -77,23 +77,25 @@ __global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t,
   }
   const bool hx = (nb & 1) && (nb & 2) && prim(ic - 1, pw) && prim(ic + 1, pe);
   const bool hy = (nb & 4) && (nb & 8) && prim(ic - p.pitch, ps) && prim(ic + p.pitch, pn);
-  const double xi = (sx + 0.5) / r - 0.5, yi = (sy + 0.5) / r - 0.5;
+  const A xi = A((sx + 0.5) / r - 0.5), yi = A((sy + 0.5) / r - 0.5);
+  auto mm = [](A u, A v) -> A { return u * v <= A(0) ? A(0) : (fabs(u) < fabs(v) ? u : v); };
 #pragma unroll
   for (int k = 0; k < NV; k++) {
-    double slx = hx ? amr_minmod(pc[k] - pw[k], pe[k] - pc[k]) : 0.0;
-    double sly = hy ? amr_minmod(pc[k] - ps[k], pn[k] - pc[k]) : 0.0;
+    A slx = hx ? mm(pc[k] - pw[k], pe[k] - pc[k]) : A(0);
+    A sly = hy ? mm(pc[k] - ps[k], pn[k] - pc[k]) : A(0);
     out[k] = pc[k] + xi * slx + yi * sly;
   }
-  if (out[0] < bf) out[0] = bf;
-  const double hf = out[0] - bf;
-  qc[g.dst] = (Real)out[0];
+  double eta = (double)out[0];
+  if (eta < bf) eta = bf;
+  const double hf = eta - bf;
+  qc[g.dst] = (Real)eta;
 #pragma unroll
   for (int k = 1; k < NV; k++) {
     // depth x primitive, no larger than the parent cell's own conserved value
     // (a mostly dry parent has a small mean depth and an unreliable velocity)
-    const double v = hf > dry ? hf * out[k] : 0.0;
-    const double cv = (1.0 - a) * (double)qo[k * p.fs + ic] + a * (double)qn[k * p.fs + ic];
-    qc[k * c.fs + g.dst] = (Real)(v * cv > 0.0 ? (fabs(v) <= fabs(cv) ? v : cv) : 0.0);
+    const A v = hf > c.dry_tol ? A(hf) * out[k] : A(0);
+    const A cv = a0 * (A)qo[k * p.fs + ic] + a1 * (A)qn[k * p.fs + ic];
+    qc[k * c.fs + g.dst] = (Real)(v * cv > A(0) ? (fabs(v) <= fabs(cv) ? v : cv) : A(0));
   }
 }
 
@@ -158,12 +160,19 @@ __global__ void k_amr_avg(Dev<Real> cd, Dev<Real> fd, const int* __restrict__ ci
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   const size_t f0 = (size_t)fi[g];
-#pragma unroll
-  for (int k = 0; k < NV; k++) {
+  // the surface (mass) is summed in FP64; the other fields in the bulk type
+  {
     double s = 0.0;
     for (int dj = 0; dj < r; dj++)
-      for (int di = 0; di < r; di++) s += (double)fd.q[fc][k * fd.fs + f0 + (size_t)dj * fd.pitch + di];
-    cd.q[cc][k * cd.fs + ci[g]] = (Real)(s / (double)(r * r));
+      for (int di = 0; di < r; di++) s += (double)fd.q[fc][f0 + (size_t)dj * fd.pitch + di];
+    cd.q[cc][ci[g]] = (Real)(s / (double)(r * r));
+  }
+#pragma unroll
+  for (int k = 1; k < NV; k++) {
+    Real s = Real(0);
+    for (int dj = 0; dj < r; dj++)
+      for (int di = 0; di < r; di++) s += fd.q[fc][k * fd.fs + f0 + (size_t)dj * fd.pitch + di];
+    cd.q[cc][k * cd.fs + ci[g]] = s / Real(r * r);
   }
 }
 

@@ -59,10 +59,11 @@ def test_data_kernels(C):
     x = torch.empty((5, nc, nc), dtype=torch.float32, device="cuda")
     assert L.lc_make_input(C._p(d(qc)), C._p(d(b)), C._p(d(phi)), nc, nc, 2.0, 50.0, 100.0, C._p(x), None) == 0
     t = torch.empty((3, nc * r, nc * r), dtype=torch.float32, device="cuda")
-    assert L.lc_make_target(C._p(d(qf)), C._p(d(qc)), None, nc, nc, r, 2.0, 50.0, C._p(t), None) == 0
+    assert L.lc_make_target(C._p(d(qf)), C._p(d(qc)), None, None, nc, nc, r, 2.0, 50.0, C._p(t), None) == 0
     bfine = rng.uniform(-50, 20, (nc * r, nc * r))
     tm = torch.empty((3, nc * r, nc * r), dtype=torch.float32, device="cuda")
-    assert L.lc_make_target(C._p(d(qf)), C._p(d(qc)), C._p(d(bfine)), nc, nc, r, 2.0, 50.0, C._p(tm), None) == 0
+    assert L.lc_make_target(C._p(d(qf)), C._p(d(qc)), C._p(d(bfine)), C._p(d(b)), nc, nc, r, 2.0, 50.0, C._p(tm),
+                            None) == 0
     y = torch.from_numpy(rng.standard_normal((3 * r * r, nc, nc)).astype(np.float32)).cuda()
     out = torch.empty((3, nc * r, nc * r), dtype=torch.float64, device="cuda")
     assert L.lc_apply(C._p(d(qc)), C._p(y), nc, nc, r, 2.0, 50.0, 1, C._p(out), None) == 0
@@ -76,7 +77,8 @@ def test_data_kernels(C):
     s = np.array([2.0, 50.0, 50.0])[:, None, None]
     assert np.allclose(t.cpu().numpy(), (qf - P) / s, rtol=1e-6, atol=1e-6)
     tmr = (qf - P) / s
-    tmr[0] = np.where(bfine >= 0.0, 0.0, tmr[0])        # no surface target on land
+    land = (bfine >= 0.0) | np.repeat(np.repeat(b >= 0.0, r, 0), r, 1)
+    tmr[0] = np.where(land, 0.0, tmr[0])                 # no surface target on land
     assert np.allclose(tm.cpu().numpy(), tmr, rtol=1e-6, atol=1e-6)
     from oracle import conv_ref as R
     assert np.allclose(out.cpu().numpy(), P + s * R.shuffle(y.cpu().numpy().astype(np.float64), r, 3), rtol=1e-12)
@@ -97,8 +99,7 @@ def test_trained_corrector_gains_over_prolongation(C):
     net = C.Net(cin=5, width=16, depth=4, r=4, nout=3, max_hw=64 * 64, seed=11)
     losses = C.train(net, train, iters=800, crop=32, lr=2e-3)
     assert losses[-50:].mean() < 0.5 * losses[:50].mean()
-    ocean_f = torch.from_numpy(meta["bf"] < 0.0).cuda()
-    ocean_c = torch.from_numpy(meta["bc"] < 0.0).cuda()
+    ocean_f, ocean_c = C.ocean_masks(meta)
     rows = C.evaluate(net, held, block=8, bound=0.1, ocean_f=ocean_f, ocean_c=ocean_c)
     for r_ in rows:
         assert r_["err_net"] < r_["err_prolong"], r_
