@@ -38,8 +38,10 @@ LC_SIGS = [
 ]
 _ready = False
 
-# scales of the normalised inputs and outputs: surface [m], momentum [m^2/s], bathymetry [m]
-S_ETA, S_Q, S_B = 1.0, 100.0, 1000.0
+# scales of the normalised inputs and outputs: surface [m], momentum [m^2/s],
+# bathymetry [m] (surface and momentum at the size of the fine/coarse
+# differences of the waves, so that the targets are of order 0.1-1)
+S_ETA, S_Q, S_B = 0.1, 10.0, 1000.0
 
 
 def lib():

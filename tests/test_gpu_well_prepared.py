@@ -34,9 +34,10 @@ def _rows_case(nx=300, ny=6, dx=0.1, seed=3):
         h = -b[j] + 0.1 * np.exp(-((x - rng.uniform(10, 20)) / 2.0) ** 2)
         q[0, j] = b[j] + h
         q[1, j] = h * 0.3 * np.cos(k[1] * x)
-    b[-1, 40] = 0.5                       # a dry cell: the row stays as it is
-    q[0, -1, 40] = 0.5
-    q[1, -1, 40] = 0.0
+    i = nx // 3
+    b[-1, i] = 0.5                        # a dry cell: the row stays as it is
+    q[0, -1, i] = 0.5
+    q[1, -1, i] = 0.0
     return b, q, dx
 
 
