@@ -224,7 +224,7 @@ def generate_pairs(nc=512, r=4, dxc=2000.0, scenarios=range(40), times=(60.0, 12
             _ck(L.lc_make_target(_p(qf), _p(qc), _p(bfd), _p(bcd), nc, nc, r, S_ETA, S_Q, _p(tg), st), "lc_make_target")
             keep = keep_fine is None or keep_fine(s)
             mypairs.append(dict(x=x, t=tg, qc=qc[:3].clone(), qf=qf[:3].clone() if keep else None, scenario=s,
-                                time=T))
+                                time=T, centre=(int(cy / dxc), int(cx / dxc))))
         if failed:
             # a scenario whose solve reports an error is dropped whole (and counted)
             if stats is not None:
@@ -309,8 +309,11 @@ def advance_to(sv, t, T):
     return T, n
 
 
-def train(net, pairs, iters=2000, crop=64, lr=1e-3, seed=0, fw=(1.0, 1.0, 1.0), log=None):
-    """Adam on random crops of the training pairs (crop x crop coarse cells)."""
+def train(net, pairs, iters=2000, crop=64, lr=1e-3, seed=0, fw=(1.0, 1.0, 1.0), log=None, near=0.8):
+    """Adam on crops of the training pairs (crop x crop coarse cells): with
+    probability `near` a crop whose centre lies within crop/2 of the scenario's
+    source (where the waves are: far from them the target is zero), otherwise
+    anywhere."""
     import torch
     rng = np.random.default_rng(seed)
     r = net.r
@@ -320,7 +323,12 @@ def train(net, pairs, iters=2000, crop=64, lr=1e-3, seed=0, fw=(1.0, 1.0, 1.0), 
         p = pairs[int(rng.integers(len(pairs)))]
         nc = p["x"].shape[-1]
         c = min(crop, nc)
-        j, i = int(rng.integers(0, nc - c + 1)), int(rng.integers(0, nc - c + 1))
+        if "centre" in p and rng.random() < near:
+            cj, ci = p["centre"]
+            j = int(np.clip(cj - c // 2 + rng.integers(-(c // 2), c // 2 + 1), 0, nc - c))
+            i = int(np.clip(ci - c // 2 + rng.integers(-(c // 2), c // 2 + 1), 0, nc - c))
+        else:
+            j, i = int(rng.integers(0, nc - c + 1)), int(rng.integers(0, nc - c + 1))
         x = p["x"][:, j:j + c, i:i + c].contiguous()
         t = p["t"][:, j * r:(j + c) * r, i * r:(i + c) * r].contiguous()
         lr_it = lr * 0.5 * (1.0 + math.cos(math.pi * it / iters))
