@@ -181,9 +181,10 @@ int sgn_get_aux(sgn_solver* s, double* c2, unsigned char* phi);
 
 /* Well-prepared initial data for mbHSGN (Sec. 3.2): replaces hw and hp of the
  * current state by h w and h p, w from the mbSGN constraint and p from the
- * relation of Sec. 3.2 with d_t u eliminated (readings G26, G27 of the design
- * notes: w = -(h/2) u_x + u b_x; p re-derived from the hw equation and that
- * constraint), for data varying along x: every row is solved independently
+ * relation of Sec. 3.2 with d_t u eliminated (w = -(h/2) u_x + u b_x, the sign
+ * of Eq. (mbHSGN) and of the kinematic bottom condition; p re-derived from the
+ * hw equation and that constraint, as the printed relation is dimensionally
+ * inconsistent), for data varying along x: every row is solved independently
  * (one tridiagonal system per row, zero-gradient ends); rows with a dry cell
  * are left unchanged.  mbHSGN solvers only (else EINVAL).  The first call
  * allocates 7 nx ny doubles of scratch through the solver's allocator (ENOMEM).

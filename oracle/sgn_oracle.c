@@ -11,8 +11,8 @@
  * OpenMP only parallelises independent loop iterations (results do not depend
  * on the thread count).
  *
- * Readings of points where the paper is silent (they are listed in the design
- * notes with the same letters):
+ * Readings of points where the paper is silent, ambiguous or garbled (the
+ * letters are used throughout the repository):
  *  G1  c^2 = alpha^2 g H phi_T  (Sec. 3.3 formula vs the definition alpha = c/sqrt(gH))
  *  G7  Strang splitting by default, Lie-Trotter as an option (Sec. 4)
  *  G8  transverse solver: App. C eigenstructure at the Roe average of the cell
