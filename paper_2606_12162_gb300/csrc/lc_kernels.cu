@@ -26,25 +26,29 @@ constexpr int COT = 16;       // output channels per block (forward)
 // sum_ci sum_k w[co][ci][k] in[ci][y+ky-1][x+kx-1], then optional ReLU and an
 // optional multiplication by the mask (mask_src > 0) used by the backward pass.
 // WT: weight element type (BF16 network weights or FP32 flipped weights).
+// A block of TS x TS threads computes a TS x 2TS output tile: each thread two
+// pixels 16 columns apart, so every weight vector read from shared memory
+// feeds two pixels' FMAs.
+constexpr int TSX = 2 * TS;   // output tile width of the convolution
 template <typename WT>
 __global__ void __launch_bounds__(TS * TS) k_conv3x3(const float* __restrict__ in, int cin, int H, int W,
                                                      const WT* __restrict__ w, const float* __restrict__ bias,
                                                      int cout, int relu, const float* __restrict__ mask_src,
                                                      float* __restrict__ out) {
-  __shared__ float sin_[CIC][TS + 2][TS + 2];
+  __shared__ float sin_[CIC][TS + 2][TSX + 2];
   __shared__ __align__(16) float sw[CIC][9][COT];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TS + tx;
-  const int x = blockIdx.x * TS + tx, y = blockIdx.y * TS + ty;
+  const int x0 = blockIdx.x * TSX + tx, y = blockIdx.y * TS + ty;
   const int co0 = blockIdx.z * COT;
-  float acc[COT];
+  float acc0[COT], acc1[COT];
 #pragma unroll
-  for (int c = 0; c < COT; c++) acc[c] = 0.f;
+  for (int c = 0; c < COT; c++) { acc0[c] = 0.f; acc1[c] = 0.f; }
   for (int c0 = 0; c0 < cin; c0 += CIC) {
     __syncthreads();
-    for (int t = tid; t < CIC * (TS + 2) * (TS + 2); t += TS * TS) {
-      int ci = t / ((TS + 2) * (TS + 2)), r = t - ci * (TS + 2) * (TS + 2);
-      int yy = r / (TS + 2), xx = r - yy * (TS + 2);
-      int gy = blockIdx.y * TS + yy - 1, gx = blockIdx.x * TS + xx - 1;
+    for (int t = tid; t < CIC * (TS + 2) * (TSX + 2); t += TS * TS) {
+      int ci = t / ((TS + 2) * (TSX + 2)), r = t - ci * (TS + 2) * (TSX + 2);
+      int yy = r / (TSX + 2), xx = r - yy * (TSX + 2);
+      int gy = blockIdx.y * TS + yy - 1, gx = blockIdx.x * TSX + xx - 1;
       float v = 0.f;
       if (c0 + ci < cin && gy >= 0 && gy < H && gx >= 0 && gx < W) v = in[((size_t)(c0 + ci) * H + gy) * W + gx];
       sin_[ci][yy][xx] = v;
@@ -61,28 +65,34 @@ __global__ void __launch_bounds__(TS * TS) k_conv3x3(const float* __restrict__ i
     for (int ci = 0; ci < CIC; ci++) {
 #pragma unroll
       for (int k = 0; k < 9; k++) {
-        const float v = sin_[ci][ty + k / 3][tx + k % 3];
+        const float v0 = sin_[ci][ty + k / 3][tx + k % 3];
+        const float v1 = sin_[ci][ty + k / 3][tx + TS + k % 3];
 #pragma unroll
         for (int c = 0; c < COT; c += 4) {
           const float4 w4 = *reinterpret_cast<const float4*>(&sw[ci][k][c]);
-          acc[c] += w4.x * v;
-          acc[c + 1] += w4.y * v;
-          acc[c + 2] += w4.z * v;
-          acc[c + 3] += w4.w * v;
+          acc0[c] += w4.x * v0; acc1[c] += w4.x * v1;
+          acc0[c + 1] += w4.y * v0; acc1[c + 1] += w4.y * v1;
+          acc0[c + 2] += w4.z * v0; acc1[c + 2] += w4.z * v1;
+          acc0[c + 3] += w4.w * v0; acc1[c + 3] += w4.w * v1;
         }
       }
     }
   }
-  if (x >= W || y >= H) return;
+  if (y >= H) return;
 #pragma unroll
-  for (int c = 0; c < COT; c++) {
-    int co = co0 + c;
-    if (co >= cout) break;
-    float v = acc[c] + (bias ? bias[co] : 0.f);
-    if (relu) v = v > 0.f ? v : 0.f;
-    size_t o = ((size_t)co * H + y) * W + x;
-    if (mask_src && !(mask_src[o] > 0.f)) v = 0.f;
-    out[o] = v;
+  for (int h = 0; h < 2; h++) {
+    const int x = x0 + h * TS;
+    if (x >= W) break;
+#pragma unroll
+    for (int c = 0; c < COT; c++) {
+      int co = co0 + c;
+      if (co >= cout) break;
+      float v = (h ? acc1[c] : acc0[c]) + (bias ? bias[co] : 0.f);
+      if (relu) v = v > 0.f ? v : 0.f;
+      size_t o = ((size_t)co * H + y) * W + x;
+      if (mask_src && !(mask_src[o] > 0.f)) v = 0.f;
+      out[o] = v;
+    }
   }
 }
 
@@ -398,7 +408,7 @@ int lc_set_params(lc_net* n, const float* host, long count) {
 }
 
 static void conv_fwd(lc_net* n, int l, const float* in, int H, int W, float* out) {
-  dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, (n->co[l] + COT - 1) / COT);
+  dim3 grid((W + TSX - 1) / TSX, (H + TS - 1) / TS, (n->co[l] + COT - 1) / COT);
   k_conv3x3<__nv_bfloat16><<<grid, dim3(TS, TS), 0, n->st>>>(in, n->ci[l], H, W, n->pb + n->woff[l],
                                                                n->p + n->boff[l], n->co[l],
                                                                l < n->depth - 1 ? 1 : 0, nullptr, out);
@@ -444,7 +454,7 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
     if (l > 0) {
       int a = n->ci[l], b = n->co[l];
       k_flip<<<nblk((long)a * b * 9, 256), 256, 0, n->st>>>(n->pb + n->woff[l], a, b, n->wf);
-      dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, (a + COT - 1) / COT);
+      dim3 grid((W + TSX - 1) / TSX, (H + TS - 1) / TS, (a + COT - 1) / COT);
       // dL/d(out of layer l-1), times ReLU'(out of layer l-1)
       k_conv3x3<float><<<grid, dim3(TS, TS), 0, n->st>>>(n->ga, b, H, W, n->wf, nullptr, a, 0, n->act[l - 1],
                                                          n->gb);
