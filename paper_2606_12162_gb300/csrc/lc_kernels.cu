@@ -26,10 +26,11 @@ constexpr int COT = 16;       // output channels per block (forward)
 // sum_ci sum_k w[co][ci][k] in[ci][y+ky-1][x+kx-1], then optional ReLU and an
 // optional multiplication by the mask (mask_src > 0) used by the backward pass.
 // WT: weight element type (BF16 network weights or FP32 flipped weights).
-// A block of TS x TS threads computes a TS x 2TS output tile: each thread two
-// pixels 16 columns apart, so every weight vector read from shared memory
-// feeds two pixels' FMAs.
-constexpr int TSX = 2 * TS;   // output tile width of the convolution
+// A block of TS x TS threads computes a TS x (PX TS) output tile: each thread
+// PX pixels TS columns apart, so every weight vector read from shared memory
+// feeds PX pixels' FMAs.
+constexpr int PX = 4;          // output pixels per thread (along x)
+constexpr int TSX = PX * TS;   // output tile width of the convolution
 template <typename WT>
 __global__ void __launch_bounds__(TS * TS) k_conv3x3(const float* __restrict__ in, int cin, int H, int W,
                                                      const WT* __restrict__ w, const float* __restrict__ bias,
@@ -40,9 +41,11 @@ __global__ void __launch_bounds__(TS * TS) k_conv3x3(const float* __restrict__ i
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TS + tx;
   const int x0 = blockIdx.x * TSX + tx, y = blockIdx.y * TS + ty;
   const int co0 = blockIdx.z * COT;
-  float acc0[COT], acc1[COT];
+  float acc[PX][COT];
 #pragma unroll
-  for (int c = 0; c < COT; c++) { acc0[c] = 0.f; acc1[c] = 0.f; }
+  for (int h = 0; h < PX; h++)
+#pragma unroll
+    for (int c = 0; c < COT; c++) acc[h][c] = 0.f;
   for (int c0 = 0; c0 < cin; c0 += CIC) {
     __syncthreads();
     for (int t = tid; t < CIC * (TS + 2) * (TSX + 2); t += TS * TS) {
@@ -61,33 +64,36 @@ __global__ void __launch_bounds__(TS * TS) k_conv3x3(const float* __restrict__ i
       sw[ci][k][co] = v;
     }
     __syncthreads();
-#pragma unroll 2
     for (int ci = 0; ci < CIC; ci++) {
 #pragma unroll
       for (int k = 0; k < 9; k++) {
-        const float v0 = sin_[ci][ty + k / 3][tx + k % 3];
-        const float v1 = sin_[ci][ty + k / 3][tx + TS + k % 3];
+        float v[PX];
+#pragma unroll
+        for (int h = 0; h < PX; h++) v[h] = sin_[ci][ty + k / 3][tx + h * TS + k % 3];
 #pragma unroll
         for (int c = 0; c < COT; c += 4) {
           const float4 w4 = *reinterpret_cast<const float4*>(&sw[ci][k][c]);
-          acc0[c] += w4.x * v0; acc1[c] += w4.x * v1;
-          acc0[c + 1] += w4.y * v0; acc1[c + 1] += w4.y * v1;
-          acc0[c + 2] += w4.z * v0; acc1[c + 2] += w4.z * v1;
-          acc0[c + 3] += w4.w * v0; acc1[c + 3] += w4.w * v1;
+#pragma unroll
+          for (int h = 0; h < PX; h++) {
+            acc[h][c] += w4.x * v[h];
+            acc[h][c + 1] += w4.y * v[h];
+            acc[h][c + 2] += w4.z * v[h];
+            acc[h][c + 3] += w4.w * v[h];
+          }
         }
       }
     }
   }
   if (y >= H) return;
 #pragma unroll
-  for (int h = 0; h < 2; h++) {
+  for (int h = 0; h < PX; h++) {
     const int x = x0 + h * TS;
     if (x >= W) break;
 #pragma unroll
     for (int c = 0; c < COT; c++) {
       int co = co0 + c;
       if (co >= cout) break;
-      float v = (h ? acc1[c] : acc0[c]) + (bias ? bias[co] : 0.f);
+      float v = acc[h][c] + (bias ? bias[co] : 0.f);
       if (relu) v = v > 0.f ? v : 0.f;
       size_t o = ((size_t)co * H + y) * W + x;
       if (mask_src && !(mask_src[o] > 0.f)) v = 0.f;
