@@ -491,3 +491,72 @@ def test_mbhsgn_nontrivial_steady_state(oracle_mod):
     assert np.log2(err[1] / err[-1]) / 3 >= 1.5, err
     printed = [_steady_error(oracle_mod, N, 1.5) for N in (400, 800)]
     assert min(printed) > 0.2 and printed[1] > 0.5 * printed[0]
+
+
+def _radial_reference(oracle_mod, dr, T, A=0.05, R0=1.0, H=1.0, alpha=3.0, L=12.0, g=9.81):
+    """App. D: a radially symmetric solution of mbHSGN is the 1-D system in r
+    with the forcing -(1/r) (h u, h u^2, h u w, h u (p + c^2)).  The 1-D step is
+    the oracle's own (a strip, wall at r = 0); the forcing is added by Strang
+    splitting with a second-order Runge-Kutta step on each half."""
+    N = int(round(L / dr))
+    r = (np.arange(N) + 0.5) * dr
+    c2 = alpha * alpha * g * H
+    b = -H * np.ones((2, N))
+    q = np.zeros((5, 2, N))
+    q[0] = A * np.exp(-(r / R0) ** 2)
+    o = oracle_mod.Oracle(b, dx=dr, model=1, bc=(0, 1, 0, 0), alpha=alpha, h_star=0.0, dry_tol=1e-6)
+    o.set_state(q)
+
+    def force(Q):
+        h = Q[0] + H
+        hu = Q[1]
+        out = np.zeros_like(Q)
+        out[0] = -hu / r
+        out[1] = -hu * (hu / h) / r
+        out[3] = -hu * (Q[3] / h) / r
+        out[4] = -hu * (Q[4] / h + c2) / r
+        return out
+
+    def half(Q, tau):
+        return Q + tau * force(Q + 0.5 * tau * force(Q))
+
+    t = 0.0
+    while t < T - 1e-12:
+        d = min(o.dt_cfl(), T - t)
+        o.set_state(half(o.get_state()[0], 0.5 * d), t)
+        assert o.step_dt(d) == 0
+        o.set_state(half(o.get_state()[0], 0.5 * d), t + d)
+        t += d
+    return r, o.get_state()[0][0, 0]
+
+
+def test_radial_reference_app_d(oracle_mod):
+    """A Gaussian hump on a flat bottom (mbHSGN, alpha = 3), quarter domain with
+    reflecting symmetry axes: the 2-D oracle along the x axis and along the
+    diagonal (which exercises the transverse solver) agrees with the radial
+    1-D reference of App. D, and the difference falls under refinement."""
+    T, A = 1.5, 0.05
+    rr, er = _radial_reference(oracle_mod, 0.01, T, A=A)
+    errs = []
+    for dx in (0.1, 0.05):
+        N = int(round(12.0 / dx))
+        x = (np.arange(N) + 0.5) * dx
+        X, Y = np.meshgrid(x, x)
+        q = np.zeros((5, N, N))
+        q[0] = A * np.exp(-(X ** 2 + Y ** 2))
+        o = oracle_mod.Oracle(-np.ones((N, N)), dx=dx, model=1, bc=(0, 1, 0, 1), alpha=3.0, h_star=0.0,
+                              dry_tol=1e-6)
+        o.set_state(q)
+        t = 0.0
+        while t < T - 1e-12:
+            d = min(o.dt_cfl(), T - t)
+            assert o.step_dt(d) == 0
+            t += d
+        e = o.get_state()[0][0]
+        ra, rd = np.sqrt(x ** 2 + (dx / 2) ** 2), np.sqrt(2.0) * x
+        ea = np.abs(e[0] - np.interp(ra, rr, er))[ra < 10].max()
+        ed = np.abs(np.diag(e) - np.interp(rd, rr, er))[rd < 10].max()
+        errs.append((ea, ed))
+    amp = np.abs(er).max()
+    assert max(errs[0]) < 5e-3 * amp, (errs, amp)
+    assert errs[1][0] < 0.25 * errs[0][0] and errs[1][1] < 0.25 * errs[0][1], errs
