@@ -191,6 +191,14 @@ int sgn_get_aux(sgn_solver* s, double* c2, unsigned char* phi);
  * Recomputes the next time step.  Synchronises the stream. */
 int sgn_well_prepare(sgn_solver* s);
 
+/* Replace the relaxation parameter c^2 of every cell by a given field (ny*nx
+ * doubles, row-major, copied; every value finite and >= 0): the constant-c^2
+ * setting of the steady-state test of Sec. 5.3 (Table 3) instead of
+ * alpha^2 g H phi_T.  Ghost cells follow the boundary conditions; call it
+ * before sgn_set_state (the SWE switch and the first time step use c^2).
+ * Synchronises the stream.  Errors: EINVAL. */
+int sgn_set_c2(sgn_solver* s, const double* c2);
+
 /* Per-kernel timing: when enabled, steps launch kernels without CUDA graphs and
  * bracket each launch with CUDA events on the solver stream.  sgn_kernel_times
  * returns, for up to n kernels, the name, the accumulated time [ms] and the

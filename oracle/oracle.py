@@ -82,6 +82,7 @@ def lib():
             L.or_source.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.or_psi.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.or_psi.restype = ctypes.c_double
+            L.or_set_c2.argtypes = [ctypes.c_void_p, dp]
             L.or_create_frame.restype = ctypes.c_void_p
             L.or_create_frame.argtypes = [ctypes.POINTER(Config), dp, ctypes.c_void_p]
             L.or_set_frame.argtypes = [ctypes.c_void_p, dp, ctypes.c_double]
@@ -182,6 +183,12 @@ class Oracle:
         phi = np.empty((self.ny, self.nx), dtype=np.uint8)
         lib().or_get_aux(self.h, _dp(c2), phi.ctypes.data)
         return c2, phi
+
+    def set_c2(self, c2):
+        c2 = np.ascontiguousarray(c2, dtype=np.float64)
+        assert c2.shape == (self.ny, self.nx)
+        if lib().or_set_c2(self.h, _dp(c2)):
+            raise ValueError("or_set_c2 rejected the field")
 
     def add_gauges(self, xy, capacity):
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)

@@ -573,6 +573,21 @@ int or_get_state(const or_solver* s, double* q, double* t) {
   return 0;
 }
 
+/* Replace the relaxation parameter c^2 of the interior cells (ny*nx, copied;
+ * the constant-c^2 setting of the steady-state test of Sec. 5.3, Table 3);
+ * ghost cells follow the boundary conditions. */
+int or_set_c2(or_solver* s, const double* c2) {
+  if (!s || !c2) return -1;
+  for (int j = 0; j < s->c.ny; j++)
+    for (int i = 0; i < s->c.nx; i++) {
+      double v = c2[(size_t)j * s->c.nx + i];
+      if (!(v >= 0.0)) return -1;
+      s->c2[cidx(s, i + NG, j + NG)] = v;
+    }
+  fill_ghosts(s, s->c2, 1, 0);
+  return 0;
+}
+
 int or_get_aux(const or_solver* s, double* c2, unsigned char* phi) {
   int nx = s->c.nx, ny = s->c.ny;
   for (int j = 0; j < ny; j++)

@@ -66,6 +66,8 @@ double or_last_dt(const or_solver* s);
 double or_max_courant(const or_solver* s);
 /* c2 and phi_T of the interior cells (ny*nx each; either may be NULL). */
 int or_get_aux(const or_solver* s, double* c2, unsigned char* phi);
+/* replace c^2 of the interior cells (ny*nx >= 0; ghosts by the boundary conditions). */
+int or_set_c2(or_solver* s, const double* c2);
 int or_add_gauges(or_solver* s, const double* xy, int n, int capacity);
 /* records: [rec][gauge][t, eta, hu, hv]; returns the number of records. */
 int or_gauges(const or_solver* s, double* out, size_t cap);

@@ -189,6 +189,11 @@ int sgn_mass(sgn_solver* s, double* mass) {
   return s->impl->mass(mass);
 }
 
+int sgn_set_c2(sgn_solver* s, const double* c2) {
+  if (!s || !c2) return SGN_EINVAL;
+  return s->impl->set_c2(c2);
+}
+
 int sgn_well_prepare(sgn_solver* s) {
   if (!s) return SGN_EINVAL;
   return s->impl->well_prepare();

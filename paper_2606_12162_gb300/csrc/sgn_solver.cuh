@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
+#include <cmath>
 #include <vector>
 
 #include "../../include/sgn.h"
@@ -36,6 +37,7 @@ struct SolverBase {
   virtual int mass(double* m) = 0;
   virtual int get_aux(double* c2, unsigned char* phi) = 0;
   virtual int well_prepare() = 0;
+  virtual int set_c2(const double* c2) = 0;
   virtual int set_profiling(int on) = 0;
   virtual int kernel_times(const char** names, double* ms, long* launches, int n) = 0;
   virtual int launches_per_step() = 0;
@@ -426,6 +428,17 @@ class Solver : public SolverBase {
     SGN_CK(cudaMemcpyAsync(hscal_ + 7, d_.mass, sizeof(double), cudaMemcpyDeviceToHost, st_));
     SGN_CK(cudaStreamSynchronize(st_));
     *m = hscal_[7];
+    return SGN_OK;
+  }
+
+  int set_c2(const double* c2) override {
+    size_t n = (size_t)d_.nx * d_.ny;
+    for (size_t i = 0; i < n; i++)
+      if (!(c2[i] >= 0.0) || !std::isfinite(c2[i])) return SGN_EINVAL;
+    SGN_CK(cudaMemcpyAsync(staging_, c2, n * sizeof(double), cudaMemcpyHostToDevice, st_));
+    k_set_c2<Real><<<gPad_, dim3(32, 8), 0, st_>>>(d_, staging_);
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaStreamSynchronize(st_));
     return SGN_OK;
   }
 

@@ -78,6 +78,7 @@ SIGNATURES = [
     ("sgn_mass", ctypes.c_int, [ctypes.c_void_p, DP]),
     ("sgn_get_aux", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.c_void_p]),
     ("sgn_well_prepare", ctypes.c_int, [ctypes.c_void_p]),
+    ("sgn_set_c2", ctypes.c_int, [ctypes.c_void_p, DP]),
     ("sgn_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sgn_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_char_p), DP,
                                         ctypes.POINTER(ctypes.c_long), ctypes.c_int]),
@@ -294,6 +295,13 @@ class Solver:
         phi = np.empty((self.ny, self.nx), dtype=np.uint8)
         _ck(load().sgn_get_aux(self.h, _dp(c2), phi.ctypes.data), "sgn_get_aux")
         return c2, phi
+
+    def set_c2(self, c2):
+        """Replace c^2 of every cell (ny, nx); call before set_state."""
+        c2 = np.ascontiguousarray(c2, dtype=np.float64)
+        if c2.shape != (self.ny, self.nx):
+            raise ValueError("c2 must have shape %s" % ((self.ny, self.nx),))
+        _ck(load().sgn_set_c2(self.h, _dp(c2)), "sgn_set_c2")
 
     def well_prepare(self):
         """Replace hw and hp by the well-prepared values of Sec. 3.2 (mbHSGN)."""

@@ -114,6 +114,7 @@ def test_null_handles_are_rejected(lib):
     assert L.sgn_status(None, None, None, None) == -1
     assert L.sgn_next_dt(None, x.ctypes.data_as(S.DP)) == -1
     assert L.sgn_well_prepare(None) == -1
+    assert L.sgn_set_c2(None, x.ctypes.data_as(S.DP)) == -1
     L.sgn_destroy(None)
 
 

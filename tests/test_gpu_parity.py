@@ -370,3 +370,25 @@ def test_config2_full_size_mixed_against_fp64(sgn):
     err = rel_l2(qm[:3], q64[:3], wet)
     assert err[0] <= 1e-4 and err[1] <= 1e-3 and err[2] <= 1e-3, err
     assert np.abs(qm[0] - q64[0]).max() <= 1e-3 * 5.0
+
+
+def test_c2_override_matches_oracle(sgn, oracle_mod):
+    """A prescribed relaxation field (sgn_set_c2; the constant-c^2 setting of
+    the Sec. 5.3 steady-state test, here a varying positive field) gives the
+    oracle's result with the same field."""
+    b, q = W.random_small_case(2, 48, 36, seed=21, dx=0.05, wetdry=False)
+    rng = np.random.default_rng(22)
+    c2 = rng.uniform(20.0, 200.0, b.shape)
+    cfg = dict(dx=0.05, model=2, bc=(1, 0, 1, 0))
+    s = sgn.Solver(b, **cfg)
+    s.set_c2(c2)
+    s.set_state(q)
+    s.step(15)
+    o = oracle_mod.Oracle(b, **cfg)
+    o.set_c2(c2)
+    o.set_state(q)
+    assert o.step(15) == 0
+    assert (rel_l2(s.get_state()[0], o.get_state()[0]) <= FP64_TOL).all()
+    assert np.allclose(s.aux()[0], c2, rtol=0, atol=0)
+    with pytest.raises(sgn.SGNError):
+        s.set_c2(-c2)

@@ -560,3 +560,63 @@ def test_radial_reference_app_d(oracle_mod):
     amp = np.abs(er).max()
     assert max(errs[0]) < 5e-3 * amp, (errs, amp)
     assert errs[1][0] < 0.25 * errs[0][0] and errs[1][1] < 0.25 * errs[0][1], errs
+
+
+def _guermond_steady(x, a=0.2, H=1.0, g=9.81):
+    """The explicit SGN steady state of Sec. 5.3 (Eq. (Steady state Guermond)):
+    h = H (1 + a sech^2(r x)), b = -a sech^2(r x) / 2, hu = q; the auxiliary
+    variables from the SGN constraints of Eq. (first order SGN) in steady
+    flow: sigma = -h u', w = sigma/2 + u b', p_b = q w' (hw equation),
+    p = (q sigma' + 6 p_b) / 12 (h sigma equation).  For H = 1, w = p_b = 0.
+    Returned with the datum lowered by H (still level 0, b < 0)."""
+    r = np.sqrt(3.0 * a / (1.0 + a)) / H
+    s2 = 1.0 / np.cosh(r * x) ** 2
+    t = np.tanh(r * x)
+    q = np.sqrt((1.0 + a) * g * H ** 3 / 2.0)
+    h = H * (1.0 + a * s2)
+    h1 = -2.0 * a * H * r * s2 * t
+    h2 = -2.0 * a * H * r * r * s2 * (s2 - 2.0 * t * t)
+    b = -0.5 * a * s2
+    b1 = a * r * s2 * t
+    u = q / h
+    sig = q * h1 / h
+    w = 0.5 * sig + u * b1
+    dsig = q * (h2 / h - h1 * h1 / (h * h))
+    # w' = (sigma/2 + u b')' vanishes identically for H = 1 (b = -(h - H)/2)
+    assert H == 1.0
+    pb = np.zeros_like(x)
+    p = (q * dsig + 6.0 * pb) / 12.0
+    return h, b - H, q, w, sig, p, pb
+
+
+def test_sgn_steady_state_with_constant_c2(oracle_mod):
+    """Sec. 5.3, Table 3: HSGN with c^2 = 1e5 (set directly: sgn_set_c2 / the
+    oracle's c^2 field) started from the explicit SGN steady state; after 1 s
+    the depth error falls with the grid at about first order, the behaviour of
+    Table 3 (the absolute values depend on an unstated domain)."""
+    errs = []
+    for N in (150, 300, 600):
+        L = 15.0
+        dx = 2 * L / N
+        x = -L + (np.arange(N) + 0.5) * dx
+        h, b, q, w, sig, p, pb = _guermond_steady(x)
+        B = np.tile(b, (2, 1))
+        Q = np.zeros((7, 2, N))
+        Q[0] = B + np.tile(h, (2, 1))
+        Q[1] = q
+        Q[3] = np.tile(h * w, (2, 1))
+        Q[4] = np.tile(h * sig, (2, 1))
+        Q[5] = np.tile(h * p, (2, 1))
+        Q[6] = np.tile(h * pb, (2, 1))
+        o = oracle_mod.Oracle(B, dx=dx, model=2, bc=(1, 1, 0, 0), h_star=0.0, dry_tol=1e-6)
+        o.set_c2(np.full(B.shape, 1e5))
+        o.set_state(Q)
+        t = 0.0
+        while t < 1.0 - 1e-12:
+            d = min(o.dt_cfl(), 1.0 - t)
+            assert o.step_dt(d) == 0
+            t += d
+        errs.append(np.abs(o.get_state()[0][0, 0] - b - h).max())
+    errs = np.array(errs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert (rates > 0.7).all(), (errs, rates)
