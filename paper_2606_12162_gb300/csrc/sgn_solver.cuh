@@ -70,10 +70,13 @@ class Solver : public SolverBase {
   static constexpr int NV = MT<MODEL>::NV;
   static constexpr int NP = PT<MODEL>::NP;
   static constexpr int NF = FT<MODEL>::NF;
-  static constexpr int FXB = 64, FXY = 4;   // x-face block
-  // y-face block: rows of 128 bytes; the FP64 records would exceed 48 KB of
-  // static shared memory at 32 x 16
-  static constexpr int FYB = sizeof(Real) == 4 ? 32 : 16, FYY = 16;
+  // Face blocks of 256 threads in FP32 (four resident blocks per SM within the
+  // 64-register bound; fewer, larger blocks or more registers per thread
+  // measured slower): x faces 128 x 2 (one halo face per 126), y faces 32 x 8.
+  // FP64: x 64 x 4, y 16 x 16 (the FP64 records of 32 x 16 would exceed 48 KB
+  // of static shared memory).
+  static constexpr int FXB = sizeof(Real) == 4 ? 128 : 64, FXY = sizeof(Real) == 4 ? 2 : 4;
+  static constexpr int FYB = sizeof(Real) == 4 ? 32 : 16, FYY = sizeof(Real) == 4 ? 8 : 16;
 
   Dev<Real> d_{};
   sgn_allocator al_{};
