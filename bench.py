@@ -46,7 +46,7 @@ FLOPS_PER_CELL = {
 # DRAM bytes (read + write) per cell of one launch, same capture (2048^2 is above
 # L2, so traffic per cell carries over to 4096^2).
 TRAFFIC_PER_CELL = {
-    ("hsgn", "mixed", "k_prep"): 89, ("hsgn", "mixed", "k_face_x"): 138, ("hsgn", "mixed", "k_face_y"): 139,
+    ("hsgn", "mixed", "k_prep"): 89, ("hsgn", "mixed", "k_face_x"): 145, ("hsgn", "mixed", "k_face_y"): 139,
     ("hsgn", "mixed", "k_trans_x"): 106, ("hsgn", "mixed", "k_trans_y"): 106, ("hsgn", "mixed", "k_theta"): 17,
     ("hsgn", "mixed", "k_update"): 221,
     ("hsgn", "fp64", "k_prep"): 183, ("hsgn", "fp64", "k_face_x"): 279, ("hsgn", "fp64", "k_face_y"): 279,

@@ -164,8 +164,13 @@ class Solver : public SolverBase {
     d_.cmax = (unsigned long long*)(sc + 11);
     d_.rdry_tol = (Real)p.dry_tol;
     d_.two_over_g = 2.0 / p.g;
+    d_.two_over_g_r = (Real)d_.two_over_g;
+    d_.half_g = 0.5 * p.g;
     d_.inv_dx = 1.0 / g.dx;
     d_.inv_dy = 1.0 / g.dy;
+    d_.g_r = (Real)p.g;
+    d_.inv_dx_r = (Real)d_.inv_dx;
+    d_.inv_dy_r = (Real)d_.inv_dy;
     d_.status = si; d_.gn = (int*)(si + 1);
     // launch geometry
     gPad_ = dim3((d_.nxp + 31) / 32, (d_.nyp + 7) / 8);
