@@ -251,6 +251,8 @@ struct AmrDt {
   unsigned long long* cmax[AMR_MAXL];
   double* dt[AMR_MAXL];
   double* lam[AMR_MAXL];
+  float* lamf[AMR_MAXL];    // bulk-type copies of lam (one of the two is set)
+  double* lamd[AMR_MAXL];
   unsigned* status;
   double* sc;   // dt0, t, last_dt, courant, clipped
 };
@@ -263,6 +265,10 @@ __device__ __forceinline__ void amr_level_steps(const AmrDt& a, double dt0) {
     a.lam[l][1] = dtl / a.dy[l];
     a.lam[l][2] = a.strang ? 0.5 * dtl : 0.0;
     a.lam[l][3] = a.strang ? 0.5 * dtl : dtl;
+    for (int k = 0; k < 4; k++) {
+      if (a.lamf[l]) a.lamf[l][k] = (float)a.lam[l][k];
+      if (a.lamd[l]) a.lamd[l][k] = a.lam[l][k];
+    }
   }
 }
 
@@ -703,6 +709,8 @@ class Amr : public AmrBase {
       dt_.R[l] = Rl; Rl *= r;
       dt_.dx[l] = d.dx; dt_.dy[l] = d.dy;
       dt_.smax[l] = d.smax; dt_.cmax[l] = d.cmax; dt_.dt[l] = d.dt; dt_.lam[l] = d.lam;
+      dt_.lamf[l] = sizeof(Real) == 4 ? (float*)d.lamr : nullptr;
+      dt_.lamd[l] = sizeof(Real) == 8 ? (double*)d.lamr : nullptr;
     }
     dt_.status = lv_[0]->dev().status;
     dt_.sc = sc_;

@@ -160,6 +160,7 @@ class Solver : public SolverBase {
       return SGN_ENOMEM;
     d_.dt = sc; d_.t = sc + 1; d_.last_dt = sc + 2; d_.courant = sc + 3; d_.mass = sc + 4;
     d_.lam = sc + 5;                                   // 4 doubles
+    d_.lamr = (Real*)(sc + 12);                        // 4 bulk-type values
     d_.smax = (unsigned long long*)(sc + 10);
     d_.cmax = (unsigned long long*)(sc + 11);
     d_.rdry_tol = (Real)p.dry_tol;
@@ -343,6 +344,9 @@ class Solver : public SolverBase {
     hscal_[11] = d_.strang ? 0.5 * dt : dt;
     SGN_CK(cudaMemcpyAsync(d_.dt, hscal_ + 2, sizeof(double), cudaMemcpyHostToDevice, st_));
     SGN_CK(cudaMemcpyAsync(d_.lam, hscal_ + 8, 4 * sizeof(double), cudaMemcpyHostToDevice, st_));
+    Real* hr = (Real*)(hscal_ + 16);
+    for (int k = 0; k < 4; k++) hr[k] = (Real)hscal_[8 + k];
+    SGN_CK(cudaMemcpyAsync(d_.lamr, hr, 4 * sizeof(Real), cudaMemcpyHostToDevice, st_));
     launch_step(st_, cur_);
     cur_ ^= 1;
     return finish_batch(nullptr);
