@@ -178,8 +178,8 @@ class Solver : public SolverBase {
     gInt_ = dim3((g.nx + 31) / 32, (g.ny + 7) / 8);
     gFX_ = dim3((g.nx + 1 + FXB - 3) / (FXB - 2), (g.ny + 2 + FXY - 1) / FXY);
     gFY_ = dim3((g.nx + 2 + FYB - 1) / FYB, (g.ny + 1 + FYY - 3) / (FYY - 2));
-    gTX_ = dim3((g.nx + 3 + 31) / 32, (g.ny + 2 + 7) / 8);
-    gTY_ = dim3((g.nx + 2 + 31) / 32, (g.ny + 3 + 7) / 8);
+    gTX_ = dim3((g.nx + 3 + 31) / 32, (g.ny + 2 + 3) / 4);   // 32 x 4: measured ahead of 32 x 8, 64 x 4, 128 x 2
+    gTY_ = dim3((g.nx + 2 + 31) / 32, (g.ny + 3 + 3) / 4);
     nmass_ = 1024;
     d_.mass_part = dnew<double>(nmass_);
     if (!d_.mass_part) return SGN_ENOMEM;
@@ -265,9 +265,9 @@ class Solver : public SolverBase {
     pre(KN_FACEY);
     k_face<MODEL, Real, 1, FYB, FYY><<<gFY_, dim3(FYB, FYY), 0, s>>>(d_); post();
     pre(KN_TRANSX);
-    k_trans<MODEL, Real, 0><<<gTX_, dim3(32, 8), 0, s>>>(d_); post();
+    k_trans<MODEL, Real, 0><<<gTX_, dim3(32, 4), 0, s>>>(d_); post();
     pre(KN_TRANSY);
-    k_trans<MODEL, Real, 1><<<gTY_, dim3(32, 8), 0, s>>>(d_); post();
+    k_trans<MODEL, Real, 1><<<gTY_, dim3(32, 4), 0, s>>>(d_); post();
     pre(KN_THETA);
     k_theta<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_); post();
   }
