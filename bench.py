@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the refined-hierarchy (config 4) line")
     ap.add_argument("--batched-n0", type=int, default=1024, help="level-0 size of the config-4 hierarchy")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector (config 5) line")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch shapes (no sgn_autotune before timing)")
     ap.add_argument("--only", default=None, choices=["batched", "learned"],
                     help="run only that line (for profiling); prints its object alone")
     return ap.parse_args()
@@ -303,6 +305,13 @@ def time_path(S, c, args, precision, profile):
     s.set_state(c["q"])
     s.add_gauges(c["gauges"], args.steps + args.warmup + 8)
     s.step(args.warmup)
+    tuning = None
+    if not args.no_tune:
+        # autotuner (setup, outside the timed region): launch shapes per kernel
+        t0 = time.perf_counter()
+        s.autotune(reps=10)
+        tuning = {"s": time.perf_counter() - t0,
+                  "shapes": {k: ("%dx%d" % v[1]) if k != "schedule" else v[0] for k, v in s.tuning().items()}}
     if profile:
         s.set_profiling(True)
     stream = torch.cuda.current_stream()
@@ -315,6 +324,7 @@ def time_path(S, c, args, precision, profile):
     ms = e0.elapsed_time(e1)
     kt = s.kernel_times() if profile else {}
     f, dt, cr = s.status()
+    s.tuning_report = tuning
     return s, ms, kt, f
 
 
@@ -334,6 +344,11 @@ def time_batched(args):
     setup = time.perf_counter() - t0
     del c["b"]
     rc0 = g.step_rc(max(1, args.warmup))
+    tune = None
+    if rc0 == 0 and not args.no_tune:
+        t1 = time.perf_counter()
+        ch, _ = g.autotune(reps=5)
+        tune = {"s": time.perf_counter() - t1, "choice_per_level": ch.tolist()}
     k = max(3, min(args.steps, 20))
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -359,7 +374,7 @@ def time_batched(args):
             "interior_cells_per_level": cells, "atlas_cells_per_level": atlas,
             "cell_updates_per_step": per_step, "atlas_cell_updates_per_step": atlas_per_step,
             "fine_equivalent_cell_updates_per_s": fine_equiv * k / (ms / 1e3),
-            "gpu_launches": g.launches_per_step() * k, "setup_s": setup,
+            "gpu_launches": g.launches_per_step() * k, "setup_s": setup, "tuning": tune,
             "mass": m, "clipped": clipped}
 
 
@@ -488,7 +503,7 @@ def main():
         ms2 = reduce_max(ms2, ws)
         v2 = cells * a2.steps * ws / (ms2 / 1e3)
         extra = {"value": v2, "unit": UNIT, "steps": a2.steps, "ms_per_step": ms2 / a2.steps,
-                 "dtype": "f64",
+                 "dtype": "f64", "tuning": s2.tuning_report,
                  "roofline": roofline(args.model, "fp64", kt2, cells, nv * 16 + 9, nv, 8, hbm, hbm_src),
                  "hbm_fraction_step": v2 / ws * (nv * 16 + 9) / (hbm * 1e9),
                  "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt2.items() if v[1]}}
@@ -528,7 +543,8 @@ def main():
                                    % (args.nx, args.nx, c["dx"]),
                        "model": args.model.upper(), "precision": args.precision, "alpha": 3.0,
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (state %.0f MB per buffer)" % (nv * cells * esize / 1e6)},
+                       "l2": "inputs larger than L2 (state %.0f MB per buffer)" % (nv * cells * esize / 1e6),
+                       "tuning": s.tuning_report},
             "roofline": roof,
             "hbm_fraction_step": step_hbm_frac,
             "algorithmic_bytes_per_cell": b_alg,

@@ -210,6 +210,43 @@ int sgn_kernel_times(sgn_solver* s, const char** names, double* ms, long* launch
 /* Number of kernel launches one time step issues (for launch accounting). */
 int sgn_launches_per_step(sgn_solver* s);
 
+/* Autotuner of the step's launch shapes and schedule.  The paper runs the
+ * step on CPUs (Sec. 7) and has no counterpart; it serves the batched form,
+ * whose level grids differ in size and shape.
+ *
+ * A tuning is SGN_TUNE_N option indices, one per slot:
+ *   SGN_TUNE_PREP, _FACE_X, _FACE_Y, _TRANS_X, _TRANS_Y, _THETA, _UPDATE: the
+ *     thread-block shape of that kernel, 0 .. SGN_TUNE_OPTS-1 (0 = default);
+ *     sgn_get_tuning reports the block dimensions each index stands for;
+ *   SGN_TUNE_SCHEDULE: 0 = one stream; 1 = the x and y face kernels, then the
+ *     two transverse kernels, as two concurrent branches.
+ * Every option computes the same values bit for bit; only the time differs.
+ *
+ * sgn_autotune times, on the current state and in step order, reps launches
+ * of each option of each kernel (CUDA events on the solver stream, after one
+ * untimed launch), keeps the fastest, then times the first phase of the step
+ * (prep to positivity factors) as a CUDA graph in both schedules.  It leaves
+ * the state, time, next dt and status unchanged: the next step is the one that
+ * would have run without it.  choice (SGN_TUNE_N ints, may be NULL) receives
+ * the tuning kept; ms (SGN_TUNE_N * SGN_TUNE_OPTS doubles, may be NULL) the
+ * mean time per launch [ms] of option o of slot k at ms[k*SGN_TUNE_OPTS + o]
+ * (for the schedule slot: of the first phase; -1 where not measured).
+ * Synchronises the stream.  Errors: EINVAL (reps outside 1..10000), ECUDA.
+ *
+ * sgn_set_tuning installs a tuning (EINVAL for an index out of range);
+ * sgn_get_tuning reports the current one and, per slot, the block dimensions
+ * (bx, by; 0 for the schedule slot).  Any pointer of sgn_get_tuning may be
+ * NULL. */
+#define SGN_TUNE_N 8
+#define SGN_TUNE_OPTS 3
+enum {
+  SGN_TUNE_PREP = 0, SGN_TUNE_FACE_X = 1, SGN_TUNE_FACE_Y = 2, SGN_TUNE_TRANS_X = 3,
+  SGN_TUNE_TRANS_Y = 4, SGN_TUNE_THETA = 5, SGN_TUNE_UPDATE = 6, SGN_TUNE_SCHEDULE = 7
+};
+int sgn_autotune(sgn_solver* s, int reps, int* choice, double* ms);
+int sgn_set_tuning(sgn_solver* s, const int* choice);
+int sgn_get_tuning(sgn_solver* s, int* choice, int* bx, int* by);
+
 /* Release all device memory and the handle (NULL is ignored). */
 void sgn_destroy(sgn_solver* s);
 

@@ -82,6 +82,16 @@ int sgn_amr_info(const sgn_amr* a, long long* cells, long long* atlas_cells);
 /* Kernel launches in one level-0 step (all levels); 0 before the first step. */
 int sgn_amr_launches_per_step(const sgn_amr* a);
 
+/* Autotuner of every level (sgn_autotune of sgn.h on each level's atlas grid,
+ * which differ in size and shape): choice (L * SGN_TUNE_N ints, may be NULL)
+ * receives level l's tuning at choice[l * SGN_TUNE_N]; ms (may be NULL) L *
+ * SGN_TUNE_N * SGN_TUNE_OPTS times laid out per level as in sgn_autotune.  The
+ * hierarchy's state, time and next step are unchanged; its graphs are
+ * re-captured by the next step.  sgn_amr_set_tuning installs one tuning per
+ * level.  Errors: EINVAL, ECUDA. */
+int sgn_amr_autotune(sgn_amr* a, int reps, int* choice, double* ms);
+int sgn_amr_set_tuning(sgn_amr* a, const int* choice);
+
 #ifdef __cplusplus
 }
 #endif

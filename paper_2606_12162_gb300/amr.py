@@ -24,6 +24,8 @@ AMR_SIGS = [
     ("sgn_amr_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(ctypes.c_longlong)]),
     ("sgn_amr_launches_per_step", ctypes.c_int, [ctypes.c_void_p]),
+    ("sgn_amr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), DP]),
+    ("sgn_amr_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 ]
 _ready = False
 
@@ -153,3 +155,21 @@ class Hierarchy:
 
     def launches_per_step(self):
         return lib().sgn_amr_launches_per_step(self.h)
+
+    def autotune(self, reps=20):
+        """Tune every level's launch shapes and schedule (state unchanged).
+        Returns (choice per level, ms table per level)."""
+        n = self.L * sgn.TUNE_N
+        ch = (ctypes.c_int * n)()
+        ms = (ctypes.c_double * (n * sgn.TUNE_OPTS))()
+        _ck(lib().sgn_amr_autotune(self.h, int(reps), ch, ms), "sgn_amr_autotune")
+        return (np.array(ch[:]).reshape(self.L, sgn.TUNE_N),
+                np.array(ms[:]).reshape(self.L, sgn.TUNE_N, sgn.TUNE_OPTS))
+
+    def set_tuning(self, choice):
+        """choice: L x TUNE_N option indices (one tuning per level)."""
+        c = np.asarray(choice, dtype=np.int64).reshape(-1)
+        ch = (ctypes.c_int * len(c))(*[int(v) for v in c])
+        if len(c) != self.L * sgn.TUNE_N:
+            raise ValueError("need %d options" % (self.L * sgn.TUNE_N))
+        _ck(lib().sgn_amr_set_tuning(self.h, ch), "sgn_amr_set_tuning")

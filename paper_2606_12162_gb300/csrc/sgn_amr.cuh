@@ -335,6 +335,8 @@ struct AmrBase {
   virtual int status(unsigned* f) = 0;
   virtual int info(long long* cells, long long* atlas) const = 0;
   virtual int launches_per_step() const = 0;
+  virtual int autotune(int reps, int* choice, double* ms) = 0;
+  virtual int set_tuning(const int* choice) = 0;
 };
 
 AmrBase* make_amr_f64(int model);
@@ -896,6 +898,34 @@ class Amr : public AmrBase {
     SGN_CK(cudaStreamSynchronize(st_));
     if (m) *m = tot;
     if (clipped) *clipped = hsc_[9];
+    return SGN_OK;
+  }
+
+  void drop_amr_graphs() {
+    for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second.first);
+    graphs_.clear();
+  }
+
+  int autotune(int reps, int* ch, double* ms) override {
+    if (reps < 1 || reps > 10000) return SGN_EINVAL;
+    SGN_CK(cudaStreamSynchronize(st_));
+    for (int l = 0; l < L_; l++) {
+      int rc = lv_[l]->autotune(reps, ch ? ch + l * TU_N : nullptr, ms ? ms + l * TU_N * TU_OPTS : nullptr);
+      if (rc) return rc;
+    }
+    drop_amr_graphs();
+    return SGN_OK;
+  }
+
+  int set_tuning(const int* ch) override {
+    for (int l = 0; l < L_; l++)
+      for (int k = 0; k < TU_N; k++)
+        if (ch[l * TU_N + k] < 0 || ch[l * TU_N + k] >= (k == TU_SCHED ? 2 : TU_OPTS)) return SGN_EINVAL;
+    for (int l = 0; l < L_; l++) {
+      int rc = lv_[l]->set_tuning(ch + l * TU_N);
+      if (rc) return rc;
+    }
+    drop_amr_graphs();
     return SGN_OK;
   }
 

@@ -219,6 +219,21 @@ int sgn_launches_per_step(sgn_solver* s) {
   return s->impl->launches_per_step();
 }
 
+int sgn_autotune(sgn_solver* s, int reps, int* choice, double* ms) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->autotune(reps, choice, ms);
+}
+
+int sgn_set_tuning(sgn_solver* s, const int* choice) {
+  if (!s || !choice) return SGN_EINVAL;
+  return s->impl->set_tuning(choice);
+}
+
+int sgn_get_tuning(sgn_solver* s, int* choice, int* bx, int* by) {
+  if (!s) return SGN_EINVAL;
+  return s->impl->get_tuning(choice, bx, by);
+}
+
 void sgn_destroy(sgn_solver* s) {
   if (!s) return;
   delete s->impl;
@@ -318,5 +333,13 @@ int sgn_amr_info(const sgn_amr* a, long long* cells, long long* atlas_cells) {
 }
 
 int sgn_amr_launches_per_step(const sgn_amr* a) { return a ? a->impl->launches_per_step() : SGN_EINVAL; }
+
+int sgn_amr_autotune(sgn_amr* a, int reps, int* choice, double* ms) {
+  return a ? a->impl->autotune(reps, choice, ms) : SGN_EINVAL;
+}
+
+int sgn_amr_set_tuning(sgn_amr* a, const int* choice) {
+  return (a && choice) ? a->impl->set_tuning(choice) : SGN_EINVAL;
+}
 
 }  // extern "C"

@@ -41,6 +41,9 @@ struct SolverBase {
   virtual int set_profiling(int on) = 0;
   virtual int kernel_times(const char** names, double* ms, long* launches, int n) = 0;
   virtual int launches_per_step() = 0;
+  virtual int autotune(int reps, int* choice, double* ms) = 0;
+  virtual int set_tuning(const int* choice) = 0;
+  virtual int get_tuning(int* choice, int* bx, int* by) = 0;
 };
 
 SolverBase* make_solver_f64(int model);
@@ -65,6 +68,30 @@ enum { KN_PREP, KN_FACEX, KN_FACEY, KN_TRANSX, KN_TRANSY, KN_THETA, KN_UPDATE, K
 static const char* const kKernelNames[KN_COUNT] = {
     "k_prep", "k_face_x", "k_face_y", "k_trans_x", "k_trans_y", "k_theta", "k_update", "k_finalize", "k_gauge"};
 
+// Autotuner choices (include/sgn.h, SGN_TUNE_*): one launch-shape option per
+// tuned kernel, in step order, then the schedule of the first phase.  Option 0
+// is the default of each slot.
+enum { TU_PREP, TU_FACEX, TU_FACEY, TU_TRANSX, TU_TRANSY, TU_THETA, TU_UPDATE, TU_SCHED, TU_N };
+static const int TU_OPTS = 3;
+static_assert(TU_N == SGN_TUNE_N && TU_OPTS == SGN_TUNE_OPTS, "tuning table size");
+
+// Face block shapes (BX, BY) per option; they are template arguments of
+// k_face (the shared-memory wave records are sized by them).  FP32: 256 or 512
+// threads, 64 registers; FP64: records of 16 values x 8 B x BX x BY within
+// 48 KB of static shared memory.
+template <bool F32> struct FaceShapes;
+template <> struct FaceShapes<true> {
+  static constexpr int XB[3] = {128, 64, 256}, XY[3] = {2, 4, 1};
+  static constexpr int YB[3] = {32, 32, 64}, YY[3] = {8, 16, 4};
+};
+template <> struct FaceShapes<false> {
+  static constexpr int XB[3] = {64, 32, 128}, XY[3] = {4, 8, 2};
+  static constexpr int YB[3] = {16, 32, 16}, YY[3] = {16, 8, 8};
+};
+// blocks of the kernels that take their shape at run time
+static const int kTransShape[3][2] = {{32, 4}, {32, 8}, {64, 4}};
+static const int kCellShape[3][2] = {{32, 8}, {32, 4}, {64, 4}};
+
 template <int MODEL, typename Real>
 class Solver : public SolverBase {
   static constexpr int NV = MT<MODEL>::NV;
@@ -75,8 +102,20 @@ class Solver : public SolverBase {
   // measured slower): x faces 128 x 2 (one halo face per 126), y faces 32 x 8.
   // FP64: x 64 x 4, y 16 x 16 (the FP64 records of 32 x 16 would exceed 48 KB
   // of static shared memory).
-  static constexpr int FXB = sizeof(Real) == 4 ? 128 : 64, FXY = sizeof(Real) == 4 ? 2 : 4;
-  static constexpr int FYB = sizeof(Real) == 4 ? 32 : 16, FYY = sizeof(Real) == 4 ? 8 : 16;
+  // These are option 0 of FaceShapes; the autotuner may pick another.
+  typedef FaceShapes<sizeof(Real) == 4> FS;
+  typedef void (*KFace)(Dev<Real>);
+  template <int DIR, int O> static KFace face_fn() {
+    return DIR == 0 ? (KFace)k_face<MODEL, Real, 0, FS::XB[O], FS::XY[O]>
+                    : (KFace)k_face<MODEL, Real, 1, FS::YB[O], FS::YY[O]>;
+  }
+  KFace kface_[2][TU_OPTS] = {{face_fn<0, 0>(), face_fn<0, 1>(), face_fn<0, 2>()},
+                              {face_fn<1, 0>(), face_fn<1, 1>(), face_fn<1, 2>()}};
+  int tune_[TU_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+  dim3 tg_[TU_N], tb_[TU_N];    // grid and block of each tuned kernel for the current choices
+  cudaStream_t aux_ = nullptr;  // second branch of the forked schedule
+  cudaEvent_t fork_[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned long long* save_ = nullptr;   // accumulators kept across autotuning
 
   Dev<Real> d_{};
   sgn_allocator al_{};
@@ -92,7 +131,7 @@ class Solver : public SolverBase {
   std::vector<Ev> evs_;
   double kms_[KN_COUNT] = {0};
   long kcnt_[KN_COUNT] = {0};
-  dim3 gPad_, gInt_, gFX_, gFY_, gTX_, gTY_;
+  dim3 gPad_, gInt_;
   int nmass_ = 0;
 
   void* dalloc(size_t bytes) {
@@ -106,6 +145,41 @@ class Solver : public SolverBase {
     return p;
   }
   template <typename T> T* dnew(size_t n) { return (T*)dalloc(n * sizeof(T) + 256); }
+
+  // grid and block of every tuned kernel from tune_.  Face kernels solve one
+  // extra face on each side of a block along their direction: x faces
+  // I in [1, nx+3] (BX - 2 per block), y faces J in [1, ny+3] (BY - 2 per block).
+  void set_geometry() {
+    const int nx = d_.nx, ny = d_.ny;
+    auto cell = [&](int k, int w, int h) {
+      const int* sh = kCellShape[tune_[k]];
+      tb_[k] = dim3(sh[0], sh[1]);
+      tg_[k] = dim3((w + sh[0] - 1) / sh[0], (h + sh[1] - 1) / sh[1]);
+    };
+    cell(TU_PREP, d_.nxp, d_.nyp);
+    cell(TU_THETA, nx, ny);
+    cell(TU_UPDATE, nx, ny);
+    {
+      const int bx = FS::XB[tune_[TU_FACEX]], by = FS::XY[tune_[TU_FACEX]];
+      tb_[TU_FACEX] = dim3(bx, by);
+      tg_[TU_FACEX] = dim3((nx + 1 + bx - 3) / (bx - 2), (ny + 2 + by - 1) / by);
+    }
+    {
+      const int bx = FS::YB[tune_[TU_FACEY]], by = FS::YY[tune_[TU_FACEY]];
+      tb_[TU_FACEY] = dim3(bx, by);
+      tg_[TU_FACEY] = dim3((nx + 2 + bx - 1) / bx, (ny + 1 + by - 3) / (by - 2));
+    }
+    {
+      const int* sh = kTransShape[tune_[TU_TRANSX]];
+      tb_[TU_TRANSX] = dim3(sh[0], sh[1]);
+      tg_[TU_TRANSX] = dim3((nx + 3 + sh[0] - 1) / sh[0], (ny + 2 + sh[1] - 1) / sh[1]);
+    }
+    {
+      const int* sh = kTransShape[tune_[TU_TRANSY]];
+      tb_[TU_TRANSY] = dim3(sh[0], sh[1]);
+      tg_[TU_TRANSY] = dim3((nx + 2 + sh[0] - 1) / sh[0], (ny + 3 + sh[1] - 1) / sh[1]);
+    }
+  }
 
   void drop_graphs() {
     for (int i = 0; i < 2; i++)
@@ -123,6 +197,9 @@ class Solver : public SolverBase {
     }
     if (hscal_) cudaFreeHost(hscal_);
     if (cap_) cudaStreamDestroy(cap_);
+    if (aux_) cudaStreamDestroy(aux_);
+    for (auto& e : fork_)
+      if (e) cudaEventDestroy(e);
   }
 
   int init(const CreateArgs& a) override {
@@ -176,10 +253,11 @@ class Solver : public SolverBase {
     // launch geometry
     gPad_ = dim3((d_.nxp + 31) / 32, (d_.nyp + 7) / 8);
     gInt_ = dim3((g.nx + 31) / 32, (g.ny + 7) / 8);
-    gFX_ = dim3((g.nx + 1 + FXB - 3) / (FXB - 2), (g.ny + 2 + FXY - 1) / FXY);
-    gFY_ = dim3((g.nx + 2 + FYB - 1) / FYB, (g.ny + 1 + FYY - 3) / (FYY - 2));
-    gTX_ = dim3((g.nx + 3 + 31) / 32, (g.ny + 2 + 3) / 4);   // 32 x 4: measured ahead of 32 x 8, 64 x 4, 128 x 2
-    gTY_ = dim3((g.nx + 2 + 31) / 32, (g.ny + 3 + 3) / 4);
+    set_geometry();
+    SGN_CK(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
+    for (int k = 0; k < 4; k++) SGN_CK(cudaEventCreateWithFlags(&fork_[k], cudaEventDisableTiming));
+    save_ = dnew<unsigned long long>(4);
+    if (!save_) return SGN_ENOMEM;
     nmass_ = 1024;
     d_.mass_part = dnew<double>(nmass_);
     if (!d_.mass_part) return SGN_ENOMEM;
@@ -255,27 +333,53 @@ class Solver : public SolverBase {
     }
   }
 
-  void launch_phase1(cudaStream_t s, int c) {
-    auto pre = [&](int k) { this->pre(s, k); };
-    auto post = [&]() { this->post(s); };
-    pre(KN_PREP);
-    k_prep<MODEL, Real><<<gPad_, dim3(32, 8), 0, s>>>(d_, c); post();
-    pre(KN_FACEX);
-    k_face<MODEL, Real, 0, FXB, FXY><<<gFX_, dim3(FXB, FXY), 0, s>>>(d_); post();
-    pre(KN_FACEY);
-    k_face<MODEL, Real, 1, FYB, FYY><<<gFY_, dim3(FYB, FYY), 0, s>>>(d_); post();
-    pre(KN_TRANSX);
-    k_trans<MODEL, Real, 0><<<gTX_, dim3(32, 4), 0, s>>>(d_); post();
-    pre(KN_TRANSY);
-    k_trans<MODEL, Real, 1><<<gTY_, dim3(32, 4), 0, s>>>(d_); post();
-    pre(KN_THETA);
-    k_theta<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_); post();
+  // one launch of tuned kernel k (TU_PREP .. TU_UPDATE) with its current shape
+  void launch_kernel(cudaStream_t s, int k, int c) {
+    switch (k) {
+      case TU_PREP: k_prep<MODEL, Real><<<tg_[k], tb_[k], 0, s>>>(d_, c); break;
+      case TU_FACEX: kface_[0][tune_[k]]<<<tg_[k], tb_[k], 0, s>>>(d_); break;
+      case TU_FACEY: kface_[1][tune_[k]]<<<tg_[k], tb_[k], 0, s>>>(d_); break;
+      case TU_TRANSX: k_trans<MODEL, Real, 0><<<tg_[k], tb_[k], 0, s>>>(d_); break;
+      case TU_TRANSY: k_trans<MODEL, Real, 1><<<tg_[k], tb_[k], 0, s>>>(d_); break;
+      case TU_THETA: k_theta<MODEL, Real><<<tg_[k], tb_[k], 0, s>>>(d_); break;
+      case TU_UPDATE: k_update<MODEL, Real><<<tg_[k], tb_[k], 0, s>>>(d_, c); break;
+    }
+  }
+  void timed(cudaStream_t s, int k, int c) {   // KN_* and TU_* agree for k <= TU_UPDATE
+    pre(s, k);
+    launch_kernel(s, k, c);
+    post(s);
   }
 
-  void launch_phase2(cudaStream_t s, int c) {
-    pre(s, KN_UPDATE);
-    k_update<MODEL, Real><<<gInt_, dim3(32, 8), 0, s>>>(d_, c); post(s);
+  // Prep, faces, transverse kernels and positivity factors.  Schedule 1 runs
+  // the x and y face kernels, then the two transverse kernels, as two
+  // concurrent branches (they read the same inputs and write disjoint planes);
+  // profiling keeps the serial order so that each launch is timed alone.
+  void launch_phase1(cudaStream_t s, int c) {
+    timed(s, TU_PREP, c);
+    if (tune_[TU_SCHED] == 1 && !prof_) {
+      cudaEventRecord(fork_[0], s);
+      cudaStreamWaitEvent(aux_, fork_[0], 0);
+      launch_kernel(aux_, TU_FACEY, c);
+      launch_kernel(s, TU_FACEX, c);
+      cudaEventRecord(fork_[1], aux_);
+      cudaEventRecord(fork_[2], s);
+      cudaStreamWaitEvent(aux_, fork_[2], 0);   // transverse x reads the y faces and vice versa
+      cudaStreamWaitEvent(s, fork_[1], 0);
+      launch_kernel(aux_, TU_TRANSY, c);
+      launch_kernel(s, TU_TRANSX, c);
+      cudaEventRecord(fork_[3], aux_);
+      cudaStreamWaitEvent(s, fork_[3], 0);
+    } else {
+      timed(s, TU_FACEX, c);
+      timed(s, TU_FACEY, c);
+      timed(s, TU_TRANSX, c);
+      timed(s, TU_TRANSY, c);
+    }
+    timed(s, TU_THETA, c);
   }
+
+  void launch_phase2(cudaStream_t s, int c) { timed(s, TU_UPDATE, c); }
 
   // access for the refined hierarchy (sgn_amr.cuh)
   Dev<Real>& dev() { return d_; }
@@ -509,6 +613,103 @@ class Solver : public SolverBase {
       if (launches) launches[k] = kcnt_[k];
     }
     return KN_COUNT;
+  }
+
+  int set_tuning(const int* ch) override {
+    if (!ch) return SGN_EINVAL;
+    for (int k = 0; k < TU_N; k++)
+      if (ch[k] < 0 || ch[k] >= (k == TU_SCHED ? 2 : TU_OPTS)) return SGN_EINVAL;
+    SGN_CK(cudaStreamSynchronize(st_));
+    for (int k = 0; k < TU_N; k++) tune_[k] = ch[k];
+    set_geometry();
+    drop_graphs();
+    return SGN_OK;
+  }
+
+  int get_tuning(int* ch, int* bx, int* by) override {
+    for (int k = 0; k < TU_N; k++) {
+      if (ch) ch[k] = tune_[k];
+      if (bx) bx[k] = k == TU_SCHED ? 0 : (int)tb_[k].x;
+      if (by) by[k] = k == TU_SCHED ? 0 : (int)tb_[k].y;
+    }
+    return SGN_OK;
+  }
+
+  // Times every option of each tuned kernel on the current state, in step
+  // order, keeping the fastest (ties keep the lower option), then the two
+  // schedules of the first phase replayed as graphs.  Every option of a kernel
+  // writes the same values (a block shape changes only which thread computes
+  // what), so each kernel leaves the next one's inputs as a step would.  The
+  // speed and Courant maxima and the status word are saved first and put back
+  // at the end, and the planes the trials rewrite are recomputed by every
+  // step, so the next step is the one that would have run without tuning.
+  int autotune(int reps, int* ch, double* ms) override {
+    if (reps < 1 || reps > 10000) return SGN_EINVAL;
+    if (ms)
+      for (int i = 0; i < TU_N * TU_OPTS; i++) ms[i] = -1.0;
+    const int c = cur_;
+    const bool prof = prof_;
+    prof_ = false;
+    SGN_CK(cudaStreamSynchronize(st_));
+    SGN_CK(cudaMemcpyAsync(save_, d_.smax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st_));
+    SGN_CK(cudaMemcpyAsync(save_ + 2, d_.status, sizeof(unsigned), cudaMemcpyDeviceToDevice, st_));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = SGN_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SGN_ECUDA;
+    // mean time of one launch over reps, after one untimed launch
+    auto time_it = [&](auto&& launch, float* out) -> int {
+      launch();
+      cudaEventRecord(e0, st_);
+      for (int r = 0; r < reps; r++) launch();
+      cudaEventRecord(e1, st_);
+      if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return SGN_ECUDA;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return SGN_ECUDA;
+      *out = t / reps;
+      return SGN_OK;
+    };
+    for (int k = 0; k < TU_SCHED && rc == SGN_OK; k++) {
+      float best = 0.f;
+      int bo = 0;
+      for (int o = 0; o < TU_OPTS && rc == SGN_OK; o++) {
+        tune_[k] = o;
+        set_geometry();
+        float t = 0.f;
+        rc = time_it([&]() { launch_kernel(st_, k, c); }, &t);
+        if (ms) ms[k * TU_OPTS + o] = t;
+        if (o == 0 || t < best) { best = t; bo = o; }
+      }
+      tune_[k] = bo;
+      set_geometry();
+    }
+    float serial = 0.f;
+    for (int o = 0; o < 2 && rc == SGN_OK; o++) {
+      tune_[TU_SCHED] = o;
+      cudaGraph_t gr = nullptr;
+      cudaGraphExec_t gx = nullptr;
+      if (cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SGN_ECUDA; break; }
+      launch_phase1(cap_, c);
+      if (cudaStreamEndCapture(cap_, &gr) != cudaSuccess) { rc = SGN_ECUDA; break; }
+      cudaError_t e = cudaGraphInstantiate(&gx, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) { rc = SGN_ECUDA; break; }
+      float t = 0.f;
+      rc = time_it([&]() { cudaGraphLaunch(gx, st_); }, &t);
+      cudaGraphExecDestroy(gx);
+      if (ms) ms[TU_SCHED * TU_OPTS + o] = t;
+      if (o == 0) serial = t;
+      else tune_[TU_SCHED] = (rc == SGN_OK && t < serial) ? 1 : 0;
+    }
+    if (rc) tune_[TU_SCHED] = 0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    prof_ = prof;
+    drop_graphs();
+    SGN_CK(cudaMemcpyAsync(d_.smax, save_, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st_));
+    SGN_CK(cudaMemcpyAsync(d_.status, save_ + 2, sizeof(unsigned), cudaMemcpyDeviceToDevice, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    if (rc) return rc;
+    return get_tuning(ch, nullptr, nullptr);
   }
 
   double x0_ = 0, y0_ = 0;

@@ -83,12 +83,18 @@ SIGNATURES = [
     ("sgn_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_char_p), DP,
                                         ctypes.POINTER(ctypes.c_long), ctypes.c_int]),
     ("sgn_launches_per_step", ctypes.c_int, [ctypes.c_void_p]),
+    ("sgn_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), DP]),
+    ("sgn_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("sgn_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("sgn_destroy", None, [ctypes.c_void_p]),
     ("sgn_math_check", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("sgn_mass_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
 ]
 MASS_SCRATCH_MAX = 65536
+TUNE_N, TUNE_OPTS = 8, 3
+TUNE_SLOTS = ("prep", "face_x", "face_y", "trans_x", "trans_y", "theta", "update", "schedule")
 
 
 def mass_static(eta, b, dx, dy, out, stream=None):
@@ -320,3 +326,22 @@ class Solver:
 
     def launches_per_step(self):
         return load().sgn_launches_per_step(self.h)
+
+    def autotune(self, reps=20):
+        """Time the launch-shape options of each step kernel and the two
+        schedules on the current state, keep the fastest (state unchanged).
+        Returns (choice list, ms table TUNE_N x TUNE_OPTS)."""
+        ch = (ctypes.c_int * TUNE_N)()
+        ms = (ctypes.c_double * (TUNE_N * TUNE_OPTS))()
+        _ck(load().sgn_autotune(self.h, int(reps), ch, ms), "sgn_autotune")
+        return list(ch), np.array(ms[:]).reshape(TUNE_N, TUNE_OPTS)
+
+    def set_tuning(self, choice):
+        ch = (ctypes.c_int * TUNE_N)(*[int(c) for c in choice])
+        _ck(load().sgn_set_tuning(self.h, ch), "sgn_set_tuning")
+
+    def tuning(self):
+        """Current tuning: {slot: (option, (bx, by))}; the schedule slot has (0, 0)."""
+        ch, bx, by = (ctypes.c_int * TUNE_N)(), (ctypes.c_int * TUNE_N)(), (ctypes.c_int * TUNE_N)()
+        _ck(load().sgn_get_tuning(self.h, ch, bx, by), "sgn_get_tuning")
+        return {TUNE_SLOTS[k]: (ch[k], (bx[k], by[k])) for k in range(TUNE_N)}
