@@ -82,6 +82,25 @@ int sgn_amr_info(const sgn_amr* a, long long* cells, long long* atlas_cells);
 /* Kernel launches in one level-0 step (all levels); 0 before the first step. */
 int sgn_amr_launches_per_step(const sgn_amr* a);
 
+/* Regridding: replace the patches of levels 1..L-1 by a new box list (same
+ * rules and layout as sgn_amr_create) and carry the state over, so that the
+ * refined region can follow the flow (the paper's patches track the advancing
+ * front, Sec. 6.3; GeoClaw regrids every few steps).  b_finest must be the
+ * bathymetry given to sgn_amr_create (it is not kept by the library).  The
+ * new state: level 0 unchanged; coarse to fine, each interior cell of a new
+ * patch takes the old patch's value of the same cell where an old patch of
+ * its level covered it, else the limited interpolation of the ghost cells
+ * (surface and primitives, A4 of the header's definitions) from its new parent
+ * at the current time; then every covered coarse cell becomes the mean of its
+ * children (average-down, finest level first).  The time and the clipped water
+ * carry over; the next step is recomputed from the new states; the status
+ * starts clear; launch shapes return to their defaults (tune again with
+ * sgn_amr_autotune).  The new hierarchy is built before the old one is
+ * released (both are held on the device for the duration of the call).  On an
+ * error the old hierarchy is left as it was.  Synchronises the stream.
+ * Errors: EINVAL (arguments, box rules), ENOMEM, ECUDA. */
+int sgn_amr_regrid(sgn_amr* a, const double* b_finest, const int* nboxes, const int* boxes);
+
 /* Autotuner of every level (sgn_autotune of sgn.h on each level's atlas grid,
  * which differ in size and shape): choice (L * SGN_TUNE_N ints, may be NULL)
  * receives level l's tuning at choice[l * SGN_TUNE_N]; ms (may be NULL) L *

@@ -63,6 +63,12 @@ below are the readings the CUDA hierarchy implements as well.
  A9 Time step: dt_0 = min over levels of CFL r^l / smax_l, smax_l the largest
     cell speed over the interior cells of level l after each of its steps since
     the previous level-0 step (dt_l = dt_0 / r^l).
+ A11 Regridding: new boxes for levels 1..L-1 (same rules as A1).  Level 0 is
+    kept; coarse to fine, each interior cell of a new patch takes the value of
+    the old patch of its level that covered it, else the A4 interpolation from
+    its new parent at the current time (weight 0, old = new state); then every
+    level is averaged down (A8), finest first.  Time and clipped water carry
+    over; the next step is recomputed from the new states.
 """
 import numpy as np
 
@@ -328,6 +334,44 @@ class AmrOracle:
         return m
 
     # ---- ghost cells (A3, A4) ----------------------------------------------
+    def _interp(self, bf, qo, qn, bp, Jp, Ip, sx, sy, nb, a):
+        """A4: value of the fine cell (bathymetry bf, sub-cell offsets sx, sy)
+        in coarse cell (Jp, Ip) of a parent frame with old / new states qo /
+        qn and bathymetry bp, at time weight a; nb: in-domain flags W E S N."""
+        r = self.r
+
+        def prim(dj, di):
+            vv = (1.0 - a) * qo[:, Jp + dj, Ip + di] + a * qn[:, Jp + dj, Ip + di]
+            h = vv[0] - bp[Jp + dj, Ip + di]
+            if not h > self.dry_tol:
+                return None
+            out = vv / h
+            out[0] = vv[0]
+            return out
+        c = prim(0, 0)
+        out = np.zeros(self.nv)
+        if c is None:
+            out[0] = max(bf, 0.0)
+            return out
+        side = {}
+        for key, ok, (dj, di) in zip("WESN", nb, ((0, -1), (0, 1), (-1, 0), (1, 0))):
+            side[key] = prim(dj, di) if ok else None
+        xi, yi = (sx + 0.5) / r - 0.5, (sy + 0.5) / r - 0.5
+        for f in range(self.nv):
+            sxl = minmod(c[f] - side["W"][f], side["E"][f] - c[f]) \
+                if side["W"] is not None and side["E"] is not None else 0.0
+            syl = minmod(c[f] - side["S"][f], side["N"][f] - c[f]) \
+                if side["S"] is not None and side["N"] is not None else 0.0
+            out[f] = c[f] + xi * sxl + yi * syl
+        out[0] = max(out[0], bf)
+        hf = out[0] - bf
+        cc = (1.0 - a) * qo[:, Jp, Ip] + a * qn[:, Jp, Ip]
+        for f in range(1, self.nv):
+            v = hf * out[f] if hf > self.dry_tol else 0.0
+            # no larger than the coarse cell's own conserved value (A4)
+            out[f] = (v if abs(v) <= abs(cc[f]) else cc[f]) if v * cc[f] > 0.0 else 0.0
+        return out
+
     def _fill(self, l, a):
         pats = self.levels[l]
         r = self.r
@@ -337,41 +381,8 @@ class AmrOracle:
                 q[:, J, I] = pats[k]["q"][:, Js, Is]
             if p["par"]:
                 P = self.levels[l - 1][p["parent"]]
-                qo, qn, bp = P["q_old"], P["q"], P["b"]
                 for (J, I, Jp, Ip, sx, sy, nb) in p["par"]:
-                    def prim(dj, di):
-                        vv = (1.0 - a) * qo[:, Jp + dj, Ip + di] + a * qn[:, Jp + dj, Ip + di]
-                        h = vv[0] - bp[Jp + dj, Ip + di]
-                        if not h > self.dry_tol:
-                            return None
-                        out = vv / h
-                        out[0] = vv[0]
-                        return out
-                    c = prim(0, 0)
-                    out = np.zeros(self.nv)
-                    if c is None:
-                        out[0] = max(p["b"][J, I], 0.0)
-                        q[:, J, I] = out
-                        continue
-                    side = {}
-                    for key, ok, (dj, di) in zip("WESN", nb, ((0, -1), (0, 1), (-1, 0), (1, 0))):
-                        side[key] = prim(dj, di) if ok else None
-                    xi, yi = (sx + 0.5) / r - 0.5, (sy + 0.5) / r - 0.5
-                    for f in range(self.nv):
-                        sxl = minmod(c[f] - side["W"][f], side["E"][f] - c[f]) \
-                            if side["W"] is not None and side["E"] is not None else 0.0
-                        syl = minmod(c[f] - side["S"][f], side["N"][f] - c[f]) \
-                            if side["S"] is not None and side["N"] is not None else 0.0
-                        out[f] = c[f] + xi * sxl + yi * syl
-                    bf = p["b"][J, I]
-                    out[0] = max(out[0], bf)
-                    hf = out[0] - bf
-                    cc = (1.0 - a) * qo[:, Jp, Ip] + a * qn[:, Jp, Ip]
-                    for f in range(1, self.nv):
-                        v = hf * out[f] if hf > self.dry_tol else 0.0
-                        # no larger than the coarse cell's own conserved value (A4)
-                        out[f] = (v if abs(v) <= abs(cc[f]) else cc[f]) if v * cc[f] > 0.0 else 0.0
-                    q[:, J, I] = out
+                    q[:, J, I] = self._interp(p["b"][J, I], P["q_old"], P["q"], P["b"], Jp, Ip, sx, sy, nb, a)
         for p in pats:
             q = p["q"]
             for (J, I, Js, Is, fx, fy) in p["bc"]:
@@ -441,6 +452,42 @@ class AmrOracle:
             for f in range(self.nv):
                 P["q"][f, m0 // r - P1 + NG:(m0 + ky) // r - P1 + NG,
                        k0 // r - P0 + NG:(k0 + kx) // r - P0 + NG] = block_mean(fine[f], r)
+
+    # ---- regridding (A11) --------------------------------------------------
+    def regrid(self, boxes):
+        """Replace the patches of levels 1..L-1 by `boxes` (as in the
+        constructor) and carry the state over (A11)."""
+        r = self.r
+        new = AmrOracle(self.b[-1], self.dims[0][0], self.dims[0][1], self.dx[0], r, boxes, model=self.model,
+                        bc=self.bc, **self.cfg)
+        new.levels[0][0]["q"] = self.levels[0][0]["q"].copy()
+        for l in range(1, self.L):
+            for p in new.levels[l]:
+                i0, j0, nx, ny = p["box"]
+                P = new.levels[l - 1][p["parent"]]
+                P0, P1 = P["box"][:2]
+                for j in range(ny):
+                    for i in range(nx):
+                        X, Y = i0 + i, j0 + j
+                        k = self._owner(l, X, Y, None)
+                        if k is not None:
+                            o = self.levels[l][k]
+                            p["q"][:, NG + j, NG + i] = o["q"][:, Y - o["box"][1] + NG, X - o["box"][0] + NG]
+                            continue
+                        ic, jc = X // r, Y // r
+                        nb = (ic - 1 >= 0, ic + 1 < new.dims[l - 1][0], jc - 1 >= 0, jc + 1 < new.dims[l - 1][1])
+                        p["q"][:, NG + j, NG + i] = new._interp(p["b"][NG + j, NG + i], P["q"], P["q"], P["b"],
+                                                                jc - P1 + NG, ic - P0 + NG, X % r, Y % r, nb, 0.0)
+        for l in range(self.L - 2, -1, -1):
+            new._average_down(l)
+        new.t, new.clipped, new.status = self.t, self.clipped, 0
+        new.smax = [0.0] * self.L
+        for l, pats in enumerate(new.levels):
+            for p in pats:
+                p["P"].set_frame(p["q"], new.t)
+                new.smax[l] = max(new.smax[l], p["P"].max_speed())
+        new.dt_next = new._dt_from_smax()
+        self.__dict__.update(new.__dict__)
 
     def step_dt(self, dt0):
         """One level-0 step of dt0 with all finer substeps; returns 0 or the status bits."""

@@ -24,6 +24,8 @@ AMR_SIGS = [
     ("sgn_amr_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(ctypes.c_longlong)]),
     ("sgn_amr_launches_per_step", ctypes.c_int, [ctypes.c_void_p]),
+    ("sgn_amr_regrid", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
     ("sgn_amr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), DP]),
     ("sgn_amr_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 ]
@@ -84,6 +86,22 @@ class Hierarchy:
                              ctypes.byref(self.params), aptr, ctypes.c_void_p(stream) if stream else None,
                              ctypes.byref(h)), "sgn_amr_create")
         self.h = h
+        self.nx0, self.ny0 = nx0, ny0
+
+    def regrid(self, b_finest, boxes):
+        """New patches of levels 1..L-1 (same layout as at creation) with the
+        state carried over; b_finest is the bathymetry given at creation."""
+        if len(boxes) != self.L - 1:
+            raise ValueError("need box lists for %d levels" % (self.L - 1))
+        b = np.ascontiguousarray(b_finest, dtype=np.float64)
+        R = self.r ** (self.L - 1)
+        if b.shape != (self.ny0 * R, self.nx0 * R):
+            raise ValueError("b_finest must have shape %s" % ((self.ny0 * R, self.nx0 * R),))
+        nb = (ctypes.c_int * max(1, self.L - 1))(*[len(bl) for bl in boxes])
+        flat = [int(v) for bl in boxes for bx in bl for v in bx]
+        bx = (ctypes.c_int * max(1, len(flat)))(*flat)
+        _ck(lib().sgn_amr_regrid(self.h, b.ctypes.data_as(DP), nb, bx), "sgn_amr_regrid")
+        self.boxes = [self.boxes[0]] + [[tuple(int(v) for v in x) for x in bl] for bl in boxes]
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

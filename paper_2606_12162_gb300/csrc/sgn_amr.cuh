@@ -122,6 +122,19 @@ __global__ void k_amr_theta(Dev<Real> c, const GEnt* __restrict__ t, int n) {
   if ((g.info & 3) == GE_SIB) c.theta[g.dst] = c.theta[g.src];
 }
 
+// regridding: interior cell dst of the new level atlas takes every field of
+// cell src of the old atlas of the same level
+template <int MODEL, typename Real>
+__global__ void k_amr_copy(Dev<Real> c, Dev<Real> o, const int* __restrict__ dst, const int* __restrict__ src,
+                           int n, int cc, int oc) {
+  constexpr int NV = MT<MODEL>::NV;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int d = dst[e], s = src[e];
+#pragma unroll
+  for (int k = 0; k < NV; k++) c.q[cc][k * c.fs + d] = o.q[oc][k * o.fs + s];
+}
+
 // theta-weighted mass flux at a face as k_update applies it (bulk precision)
 template <typename Real>
 __device__ __forceinline__ double face_phi(const Dev<Real>& d, size_t id, int dir) {
@@ -337,6 +350,7 @@ struct AmrBase {
   virtual int launches_per_step() const = 0;
   virtual int autotune(int reps, int* choice, double* ms) = 0;
   virtual int set_tuning(const int* choice) = 0;
+  virtual int take_state(AmrBase* old) = 0;
 };
 
 AmrBase* make_amr_f64(int model);
@@ -926,6 +940,85 @@ class Amr : public AmrBase {
       if (rc) return rc;
     }
     drop_amr_graphs();
+    return SGN_OK;
+  }
+
+  // padded atlas index of frame cell (I, J) of box b on level l
+  int pidx_of(int l, const Box& b, int I, int J) const {
+    return (int)((size_t)(b.py + J) * lv_[l]->dev().pitch + (b.px + I));
+  }
+
+  // Regridding (reading A11 of the refinement oracle): this hierarchy, just
+  // created with new boxes over the same grid, takes the state of `ob`.
+  // Level 0 is copied; then, coarse to fine, every interior cell of a new
+  // patch takes the old patch's cell of the same level where one covered it,
+  // else the limited interpolation of the ghost cells (A4) from the new parent
+  // at its current state; then every level is averaged down (A8), finest
+  // first.  The time and the clipped water carry over; the time step is
+  // recomputed from the new states; the status starts clear.
+  int take_state(AmrBase* ob) override {
+    auto* o = dynamic_cast<Amr<MODEL, Real>*>(ob);
+    if (!o || o->L_ != L_ || o->r_ != r_ || o->NX_ != NX_ || o->NY_ != NY_) return SGN_EINVAL;
+    const int r = r_;
+    SGN_CK(cudaStreamSynchronize(o->st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    Dev<Real>& n0 = lv_[0]->dev();
+    Dev<Real>& o0 = o->lv_[0]->dev();
+    if (n0.fs != o0.fs || n0.pitch != o0.pitch) return SGN_EINVAL;
+    SGN_CK(cudaMemcpyAsync(n0.q[lv_[0]->cur()], o0.q[o->lv_[0]->cur()], (size_t)NV * n0.fs * sizeof(Real),
+                           cudaMemcpyDeviceToDevice, st_));
+    for (int l = 1; l < L_; l++) {
+      Owner oo;
+      oo.build(o->bx_[l], NX_[l], NY_[l]);
+      std::vector<int> cd, cs;
+      std::vector<GEnt> par;
+      for (const Box& b : bx_[l]) {
+        const Box& P = bx_[l - 1][b.parent];
+        for (int j = 0; j < b.ny; j++)
+          for (int i = 0; i < b.nx; i++) {
+            const int X = b.i0 + i, Y = b.j0 + j, dst = pidx_of(l, b, i + 2, j + 2);
+            const int k = oo.find(X, Y);
+            if (k >= 0) {
+              const Box& s = o->bx_[l][k];
+              cd.push_back(dst);
+              cs.push_back(o->pidx_of(l, s, X - s.i0 + 2, Y - s.j0 + 2));
+              continue;
+            }
+            const int ic = X / r, jc = Y / r;
+            const int nb = (ic - 1 >= 0 ? 1 : 0) | (ic + 1 < NX_[l - 1] ? 2 : 0) | (jc - 1 >= 0 ? 4 : 0) |
+                           (jc + 1 < NY_[l - 1] ? 8 : 0);
+            par.push_back(GEnt{dst, pidx_of(l - 1, P, ic - P.i0 + 2, jc - P.j0 + 2),
+                               GE_PAR | ((X % r) << 8) | ((Y % r) << 16) | (nb << 24)});
+          }
+      }
+      if (!cd.empty()) {
+        int* dd = up(cd);
+        int* ds = up(cs);
+        if (!dd || !ds) return SGN_ENOMEM;
+        k_amr_copy<MODEL, Real><<<grid1((int)cd.size()), 256, 0, st_>>>(
+            lv_[l]->dev(), o->lv_[l]->dev(), dd, ds, (int)cd.size(), lv_[l]->cur(), o->lv_[l]->cur());
+      }
+      if (!par.empty()) {
+        GEnt* dp = up(par);
+        if (!dp) return SGN_ENOMEM;
+        const int pc = lv_[l - 1]->cur();
+        k_amr_fill<MODEL, Real><<<grid1((int)par.size()), 256, 0, st_>>>(lv_[l]->dev(), lv_[l - 1]->dev(), dp,
+                                                                          (int)par.size(), lv_[l]->cur(), pc, pc,
+                                                                          0.0, r);
+      }
+      SGN_CK(cudaGetLastError());
+    }
+    for (int l = L_ - 2; l >= 0; l--)
+      if (tb_[l].navg)
+        k_amr_avg<MODEL, Real><<<grid1(tb_[l].navg), 256, 0, st_>>>(lv_[l]->dev(), lv_[l + 1]->dev(), tb_[l].acoarse,
+                                                                     tb_[l].afine, tb_[l].navg, lv_[l]->cur(),
+                                                                     lv_[l + 1]->cur(), r);
+    SGN_CK(cudaGetLastError());
+    int rc = begin();
+    if (rc) return rc;
+    SGN_CK(cudaMemcpyAsync(sc_ + 1, o->sc_ + 1, sizeof(double), cudaMemcpyDeviceToDevice, st_));
+    SGN_CK(cudaMemcpyAsync(sc_ + 4, o->sc_ + 4, sizeof(double), cudaMemcpyDeviceToDevice, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
     return SGN_OK;
   }
 

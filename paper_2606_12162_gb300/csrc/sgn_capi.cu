@@ -248,7 +248,31 @@ void sgn_destroy(sgn_solver* s) {
 
 struct sgn_amr {
   sgn::AmrBase* impl;
+  sgn::AmrArgs args;        // creation arguments (boxes and bathymetry pointer not kept)
+  sgn_allocator alloc;
+  bool has_alloc;
 };
+
+// a hierarchy from creation arguments and a box list (validated by init)
+static int amr_build(sgn::AmrArgs& a, const int* nboxes, const int* boxes, sgn::AmrBase** out) {
+  *out = nullptr;
+  a.boxes.clear();
+  int off = 0;
+  for (int l = 1; l < a.L; l++) {
+    if (nboxes[l - 1] < 0) return SGN_EINVAL;
+    a.boxes.emplace_back(boxes + 4 * off, boxes + 4 * (off + nboxes[l - 1]));
+    off += nboxes[l - 1];
+  }
+  sgn::AmrBase* impl = a.prm.precision == SGN_MIXED ? sgn::make_amr_mixed(a.model) : sgn::make_amr_f64(a.model);
+  if (!impl) return SGN_ENOMEM;
+  int r = impl->init(a);
+  if (r) {
+    delete impl;
+    return r;
+  }
+  *out = impl;
+  return SGN_OK;
+}
 
 extern "C" {
 
@@ -269,34 +293,48 @@ int sgn_amr_create(const sgn_grid* grid0, const double* b_finest, int nlevels, i
   int r = check_args(grid0, b_finest, model, params);
   if (r) return r;
   if (allocator && (!allocator->alloc || !allocator->free)) return SGN_EINVAL;
-  sgn::AmrArgs a;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SGN_ECUDA;
+  sgn_amr* h = new (std::nothrow) sgn_amr;
+  if (!h) return SGN_ENOMEM;
+  h->has_alloc = allocator != nullptr;
+  if (allocator) h->alloc = *allocator;
+  sgn::AmrArgs& a = h->args;
   a.grid = *grid0;
   a.prm = *params;
   a.model = model;
   a.L = nlevels;
   a.r = ratio;
   a.b = b_finest;
-  a.alloc = allocator;
+  a.alloc = h->has_alloc ? &h->alloc : nullptr;
   a.stream = (cudaStream_t)cuda_stream;
-  int off = 0;
-  for (int l = 1; l < nlevels; l++) {
-    if (nboxes[l - 1] < 0) return SGN_EINVAL;
-    a.boxes.emplace_back(boxes + 4 * off, boxes + 4 * (off + nboxes[l - 1]));
-    off += nboxes[l - 1];
+  r = amr_build(a, nboxes, boxes, &h->impl);
+  a.b = nullptr;
+  a.boxes.clear();
+  if (r) {
+    delete h;
+    return r;
   }
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SGN_ECUDA;
-  sgn::AmrBase* impl = params->precision == SGN_MIXED ? sgn::make_amr_mixed(model) : sgn::make_amr_f64(model);
-  if (!impl) return SGN_ENOMEM;
-  r = impl->init(a);
+  *out = h;
+  return SGN_OK;
+}
+
+int sgn_amr_regrid(sgn_amr* h, const double* b_finest, const int* nboxes, const int* boxes) {
+  if (!h || !b_finest) return SGN_EINVAL;
+  if (h->args.L > 1 && (!nboxes || !boxes)) return SGN_EINVAL;
+  sgn::AmrBase* impl = nullptr;
+  h->args.b = b_finest;
+  int r = amr_build(h->args, nboxes, boxes, &impl);
+  h->args.b = nullptr;
+  h->args.boxes.clear();
+  if (r) return r;
+  r = impl->take_state(h->impl);
   if (r) {
     delete impl;
     return r;
   }
-  sgn_amr* h = new (std::nothrow) sgn_amr;
-  if (!h) { delete impl; return SGN_ENOMEM; }
+  delete h->impl;
   h->impl = impl;
-  *out = h;
   return SGN_OK;
 }
 

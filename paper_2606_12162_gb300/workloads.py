@@ -260,6 +260,15 @@ def amr_boxes_small():
     return [lvl1, lvl2]
 
 
+def amr_boxes_small_moved():
+    """A second layout over the grid of amr_boxes_small (for regridding): one
+    level-1 patch kept, one reshaped, one moved away from the boundary; a
+    level-2 patch shifted half over its old place and one in the moved patch."""
+    lvl1 = [(8, 8, 16, 12), (24, 12, 8, 8), (28, 24, 12, 12)]
+    lvl2 = [(24, 20, 16, 12), (60, 52, 12, 16)]
+    return [lvl1, lvl2]
+
+
 # --------------------------------------------------------------------------
 # Config 4: three refinement levels, ratio 4, level 0 1024 x 1024 at 2 km over
 # a fractal bathymetry with a sloping coast strip; patches of seeded sizes

@@ -177,3 +177,90 @@ def test_refined_patch_approaches_the_fine_grid(A, oracle_mod):
     cprol = np.repeat(np.repeat(coarse.get_state()[0][0], r, 0), r, 1)[j0:j0 + ny, i0:i0 + nx]
     e_coarse = np.linalg.norm(cprol - ref)
     assert e_amr < 0.5 * e_coarse
+
+
+def _pair_states(a, b):
+    return all(np.array_equal(a.patch_state(l, k), b.patch_state(l, k))
+               for l in range(a.L) for k in range(len(a.levels[l])))
+
+
+def test_regrid_to_the_same_boxes_changes_nothing(A):
+    """A11: every new cell lies in an old patch of its level (copies only) and
+    average-down reproduces the covered coarse cells, so the run continues
+    bit for bit."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=12, amp=0.25)
+    ref = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
+    ref.set_state(qs)
+    assert ref.step(7) == 0
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
+    am.set_state(qs)
+    assert am.step(3) == 0
+    am.regrid(W.amr_boxes_small())
+    assert am.step(4) == 0
+    assert _pair_states(am, ref) and am.t == ref.t and am.dt_next == ref.dt_next
+
+
+def test_regrid_keeps_rest_and_mass(A):
+    """Moving the patches keeps the lake at rest exactly, and mass up to
+    rounding over wet bathymetry (the interpolated surface has the parent's
+    mean: the limited slopes cancel over the r x r children)."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
+    rest = []
+    for l, q in enumerate(qs):
+        z = np.zeros_like(q)
+        bl = b
+        for _ in range(2 - l):
+            bl = A.block_mean(bl, 2)
+        z[0] = np.maximum(bl, 0.0)
+        rest.append(z)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, bc=(0, 0, 1, 1), **CFG)
+    am.set_state(rest)
+    assert am.step(2) == 0
+    am.regrid(W.amr_boxes_small_moved())
+    assert am.step(3) == 0
+    for l, pats in enumerate(am.levels):
+        for k in range(len(pats)):
+            i0, j0, nx, ny = pats[k]["box"]
+            q = am.patch_state(l, k)
+            assert np.abs(q[0] - np.maximum(am.b[l][j0:j0 + ny, i0:i0 + nx], 0.0)).max() <= 1e-14
+            assert np.abs(q[1:]).max() <= 1e-14
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=5, amp=0.3, wetdry=False)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, bc=(0, 0, 0, 0), **CFG)
+    am.set_state(qs)
+    assert am.step(4) == 0
+    m0, t0 = am.mass(), am.t
+    am.regrid(W.amr_boxes_small_moved())
+    assert abs(am.mass() - m0) <= 1e-13 * m0 and am.t == t0
+    assert am.step(4) == 0
+    assert abs(am.mass() - m0 - am.clipped) <= 1e-13 * m0
+
+
+def test_regrid_copies_and_interpolates(A):
+    """New cells inside an old patch of their level keep its values; new cells
+    outside take the parent's interpolation, whose r x r mean is the parent
+    value where the parent is wet (smooth wet data, no clipping)."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=6, amp=0.2, wetdry=False)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
+    am.set_state(qs)
+    assert am.step(3) == 0
+    before = [[p["q"].copy() for p in am.levels[l]] for l in range(3)]
+    boxes_before = [list(am.boxes[l]) for l in range(3)]
+    am.regrid(W.amr_boxes_small_moved())
+    # level-1 patch (8, 8, 16, 12) is in both layouts: every interior cell kept
+    # except the covered ones (average-down of the new level 2)
+    k_old = boxes_before[1].index((8, 8, 16, 12))
+    k_new = am.boxes[1].index((8, 8, 16, 12))
+    q_old = before[1][k_old][:, 2:-2, 2:-2]
+    q_new = am.patch_state(1, k_new)
+    cov = am.cover[1][k_new]
+    assert np.array_equal(q_new[:, ~cov][0], q_old[:, ~cov][0])
+    # new level-2 cells of (24, 20, 16, 12) outside the old (20, 20, 16, 12)
+    # (level-2 x 36..39, parent cells ic = 18, 19, uncovered before): the 2 x 2
+    # mean of eta over each parent cell is that cell's value before regridding
+    k2 = am.boxes[2].index((24, 20, 16, 12))
+    q2 = am.patch_state(2, k2)[0]
+    for jc in range(10, 16):
+        for ic in range(18, 20):
+            m = q2[2 * jc - 20:2 * jc - 18, 2 * ic - 24:2 * ic - 22].mean()
+            assert abs(m - q_old[0, jc - 8, ic - 8]) <= 1e-14 * max(1.0, abs(m))
+            assert np.ptp(q2[2 * jc - 20:2 * jc - 18, 2 * ic - 24:2 * ic - 22]) > 0.0   # not a plain copy

@@ -150,3 +150,81 @@ def test_invalid_hierarchies_are_rejected(M):
                   [[(2, 2, 8, 8)]]):                         # one parent cell from the edge
         with pytest.raises(sgn.SGNError):
             M.Hierarchy(b, 24, 20, 0.2, 2, boxes, model=2, **CFG)
+
+
+@pytest.mark.parametrize("model,seed,wetdry", [(2, 21, True), (0, 22, True), (1, 23, False)])
+def test_regrid_against_oracle(M, A, model, seed, wetdry):
+    """sgn_amr_regrid (reading A11) against the oracle's regrid: step, move
+    the patches, step on; every patch, next dt, time, mass and clipped water."""
+    nx0, ny0, r = 24, 20, 2
+    b, qs = W.amr_small_case(model, nx0, ny0, r, 3, seed=seed, wetdry=wetdry, amp=0.25)
+    g = M.Hierarchy(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=model, **CFG)
+    g.set_state(qs)
+    o = A.AmrOracle(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=model, **CFG)
+    o.set_state(qs)
+    g.step(4)
+    assert o.step(4) == 0
+    g.regrid(b, W.amr_boxes_small_moved())
+    o.regrid(W.amr_boxes_small_moved())
+    assert abs(g.next_dt() - o.dt_next) <= FP64_TOL * o.dt_next
+    for l in range(g.L):
+        for k in range(len(g.boxes[l])):
+            err = rel_l2(g.get_patch(l, k), o.patch_state(l, k))
+            assert (err <= FP64_TOL).all(), ("after regrid", l, k, err)
+    t = g.step(5)
+    assert o.step(5) == 0
+    assert abs(t - o.t) <= FP64_TOL * o.t
+    for l in range(g.L):
+        for k in range(len(g.boxes[l])):
+            err = rel_l2(g.get_patch(l, k), o.patch_state(l, k))
+            assert (err <= FP64_TOL).all(), (l, k, err)
+    assert abs(g.next_dt() - o.dt_next) <= FP64_TOL * o.dt_next
+    m, c = g.mass()
+    assert abs(m - o.mass()) <= FP64_TOL * o.mass()
+    assert abs(c - o.clipped) <= FP64_TOL * o.mass()
+    assert g.status() == 0
+
+
+def test_regrid_same_boxes_bitwise_and_invalid_rejected(M):
+    from paper_2606_12162_gb300 import sgn
+    nx0, ny0, r = 24, 20, 2
+    b, qs = W.amr_small_case(2, nx0, ny0, r, 3, seed=24, amp=0.25)
+
+    def make():
+        g = M.Hierarchy(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=2, precision=1, **CFG)
+        g.set_state(qs)
+        return g
+    ref = make()
+    ref.step(8)
+    g = make()
+    g.step(3)
+    with pytest.raises(sgn.SGNError) as e:
+        g.regrid(b, [[(1, 8, 16, 12)], []])                  # not aligned: rejected, old hierarchy kept
+    assert e.value.code == -1
+    g.step(2)
+    g.regrid(b, W.amr_boxes_small())
+    g.step(3)
+    for l in range(3):
+        for k in range(len(g.boxes[l])):
+            assert np.array_equal(g.get_patch(l, k), ref.get_patch(l, k))
+    assert g.next_dt() == ref.next_dt()
+    assert g.mass() == ref.mass()
+
+
+def test_mixed_regrid_against_fp64_oracle(M, A):
+    nx0, ny0, r = 24, 20, 2
+    b, qs = W.amr_small_case(2, nx0, ny0, r, 3, seed=25, wetdry=False, amp=0.15)
+    g = M.Hierarchy(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=2, precision=1, **CFG)
+    g.set_state(qs)
+    o = A.AmrOracle(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=2, **CFG)
+    o.set_state(qs)
+    g.step(5)
+    assert o.step(5) == 0
+    g.regrid(b, W.amr_boxes_small_moved())
+    o.regrid(W.amr_boxes_small_moved())
+    g.step(5)
+    assert o.step(5) == 0
+    for l in range(g.L):
+        for k in range(len(g.boxes[l])):
+            err = rel_l2(g.get_patch(l, k)[:3], o.patch_state(l, k)[:3])
+            assert err[0] <= 1e-5 and err[1] <= 1e-3 and err[2] <= 1e-3, (l, k, err)
