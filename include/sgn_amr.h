@@ -101,6 +101,25 @@ int sgn_amr_launches_per_step(const sgn_amr* a);
  * Errors: EINVAL (arguments, box rules), ENOMEM, ECUDA. */
 int sgn_amr_regrid(sgn_amr* a, const double* b_finest, const int* nboxes, const int* boxes);
 
+/* Flag-driven regridding, so that the patches follow the flow between calls
+ * (Sec. 6.3: cells are flagged where the surface jump to a neighbouring cell
+ * exceeds a threshold).  Level by level from the coarsest: a cell of level l
+ * is flagged where |eta - eta_n| > tol for a neighbour n in the same patch
+ * (where level l has no patch, the cell takes its parent cell's flag); the
+ * flags are widened by `buffer` cells of that level; the part of each new
+ * level-l box that may hold finer patches (two cells inside its edges, except
+ * along the domain boundary) is cut into tile x tile squares of level-l cells
+ * (the last ones clipped), and every square holding a widened flag becomes a
+ * level-(l+1) box.  Then as sgn_amr_regrid with those boxes.  nboxes (L - 1
+ * ints, may be NULL) receives the number of boxes per level >= 1.  Errors as
+ * sgn_amr_regrid; EINVAL also for L = 1, tol <= 0, tile < 1 or buffer < 0. */
+int sgn_amr_regrid_flagged(sgn_amr* a, const double* b_finest, double tol, int tile, int buffer, int* nboxes);
+
+/* Boxes of a level (4 ints i0, j0, nx, ny each, in that level's cells) into
+ * boxes (capacity cap boxes; NULL to query); returns the number of boxes, or
+ * EINVAL / ERANGE. */
+int sgn_amr_get_boxes(const sgn_amr* a, int level, int* boxes, int cap);
+
 /* Autotuner of every level (sgn_autotune of sgn.h on each level's atlas grid,
  * which differ in size and shape): choice (L * SGN_TUNE_N ints, may be NULL)
  * receives level l's tuning at choice[l * SGN_TUNE_N]; ms (may be NULL) L *

@@ -69,6 +69,15 @@ below are the readings the CUDA hierarchy implements as well.
     its new parent at the current time (weight 0, old = new state); then every
     level is averaged down (A8), finest first.  Time and clipped water carry
     over; the next step is recomputed from the new states.
+ A12 Boxes from flags (Sec. 6.3: refine where the surface jump between
+    neighbouring cells exceeds a threshold): level by level from the coarsest,
+    a cell is flagged where |eta - eta_n| > tol for a neighbour n in the same
+    patch interior; where the level has no patch the cell takes its parent
+    cell's flag; flags are widened by `buffer` cells (a square); the part of
+    each new box of the level that may hold finer patches (two cells inside
+    its edges except along the domain boundary) is cut into tile x tile
+    squares from its low corner, the last ones clipped, and every square
+    holding a widened flag becomes a box of the next level.
 """
 import numpy as np
 
@@ -488,6 +497,44 @@ class AmrOracle:
                 new.smax[l] = max(new.smax[l], p["P"].max_speed())
         new.dt_next = new._dt_from_smax()
         self.__dict__.update(new.__dict__)
+
+    def flag_boxes(self, tol, tile, buffer):
+        """A12: box lists of levels 1..L-1 from refinement flags of the
+        current state."""
+        r, out, prev = self.r, [], None
+        parents = [self.boxes[0][0]]
+        for l in range(self.L - 1):
+            NX, NY = self.dims[l]
+            f = np.zeros((NY, NX), dtype=bool)
+            have = np.zeros((NY, NX), dtype=bool)
+            for p in self.levels[l]:
+                i0, j0, nx, ny = p["box"]
+                e = p["q"][0, NG:NG + ny, NG:NG + nx]
+                g = np.zeros((ny, nx), dtype=bool)
+                g[:, 1:] |= np.abs(e[:, 1:] - e[:, :-1]) > tol
+                g[:, :-1] |= np.abs(e[:, :-1] - e[:, 1:]) > tol
+                g[1:, :] |= np.abs(e[1:, :] - e[:-1, :]) > tol
+                g[:-1, :] |= np.abs(e[:-1, :] - e[1:, :]) > tol
+                f[j0:j0 + ny, i0:i0 + nx] = g
+                have[j0:j0 + ny, i0:i0 + nx] = True
+            if l > 0:
+                pro = np.repeat(np.repeat(prev, r, axis=0), r, axis=1)
+                f = np.where(have, f, pro)
+            w = np.zeros_like(f)
+            for Y, X in zip(*np.nonzero(f)):
+                w[max(0, Y - buffer):Y + buffer + 1, max(0, X - buffer):X + buffer + 1] = True
+            bl = []
+            for (i0, j0, nx, ny) in parents:
+                x0, x1 = i0 + (0 if i0 == 0 else 2), i0 + nx - (0 if i0 + nx == NX else 2)
+                y0, y1 = j0 + (0 if j0 == 0 else 2), j0 + ny - (0 if j0 + ny == NY else 2)
+                for ty in range(y0, y1, tile):
+                    for tx in range(x0, x1, tile):
+                        tw, th = min(tile, x1 - tx), min(tile, y1 - ty)
+                        if w[ty:ty + th, tx:tx + tw].any():
+                            bl.append((tx * r, ty * r, tw * r, th * r))
+            out.append(bl)
+            parents, prev = bl, f
+        return out
 
     def step_dt(self, dt0):
         """One level-0 step of dt0 with all finer substeps; returns 0 or the status bits."""

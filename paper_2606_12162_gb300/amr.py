@@ -26,6 +26,10 @@ AMR_SIGS = [
     ("sgn_amr_launches_per_step", ctypes.c_int, [ctypes.c_void_p]),
     ("sgn_amr_regrid", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
+    ("sgn_amr_regrid_flagged", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
+    ("sgn_amr_get_boxes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.c_int]),
     ("sgn_amr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), DP]),
     ("sgn_amr_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 ]
@@ -102,6 +106,24 @@ class Hierarchy:
         bx = (ctypes.c_int * max(1, len(flat)))(*flat)
         _ck(lib().sgn_amr_regrid(self.h, b.ctypes.data_as(DP), nb, bx), "sgn_amr_regrid")
         self.boxes = [self.boxes[0]] + [[tuple(int(v) for v in x) for x in bl] for bl in boxes]
+
+    def regrid_flagged(self, b_finest, tol, tile=8, buffer=2):
+        """Flag-driven regridding (surface jump above tol); returns the number
+        of boxes per level >= 1."""
+        b = np.ascontiguousarray(b_finest, dtype=np.float64)
+        nb = (ctypes.c_int * max(1, self.L - 1))()
+        _ck(lib().sgn_amr_regrid_flagged(self.h, b.ctypes.data_as(DP), float(tol), int(tile), int(buffer), nb),
+            "sgn_amr_regrid_flagged")
+        self.boxes = [self.boxes[0]] + [self.get_boxes(l) for l in range(1, self.L)]
+        return list(nb)[:self.L - 1]
+
+    def get_boxes(self, level):
+        n = lib().sgn_amr_get_boxes(self.h, int(level), None, 0)
+        if n < 0:
+            raise sgn.SGNError(n, "sgn_amr_get_boxes")
+        out = (ctypes.c_int * max(1, 4 * n))()
+        _ck(0 if lib().sgn_amr_get_boxes(self.h, int(level), out, n) == n else -1, "sgn_amr_get_boxes")
+        return [tuple(out[4 * k:4 * k + 4]) for k in range(n)]
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

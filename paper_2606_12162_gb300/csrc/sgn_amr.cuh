@@ -135,6 +135,26 @@ __global__ void k_amr_copy(Dev<Real> c, Dev<Real> o, const int* __restrict__ dst
   for (int k = 0; k < NV; k++) c.q[cc][k * c.fs + d] = o.q[oc][k * o.fs + s];
 }
 
+// refinement flag (Sec. 6.3: the surface jump between neighbouring cells
+// exceeds tol), over the patch interiors of a level's atlas; neighbours that
+// are not interior cells of the same patch are not compared
+template <typename Real>
+__global__ void k_amr_flag(Dev<Real> d, int cur, double tol, unsigned char* __restrict__ out) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= d.nxp || J >= d.nyp) return;
+  const size_t id = at(d.pitch, I, J);
+  unsigned char f = 0;
+  if (d.kind[id] & 1) {
+    const Real* e = d.q[cur];
+    const double c = (double)e[id];
+    const size_t nb[4] = {id - 1, id + 1, id - d.pitch, id + d.pitch};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if ((d.kind[nb[k]] & 1) && fabs((double)e[nb[k]] - c) > tol) f = 1;
+  }
+  out[id] = f;
+}
+
 // theta-weighted mass flux at a face as k_update applies it (bulk precision)
 template <typename Real>
 __device__ __forceinline__ double face_phi(const Dev<Real>& d, size_t id, int dir) {
@@ -351,6 +371,11 @@ struct AmrBase {
   virtual int autotune(int reps, int* choice, double* ms) = 0;
   virtual int set_tuning(const int* choice) = 0;
   virtual int take_state(AmrBase* old) = 0;
+  // level sizes, boxes (4 ints each), and the flags of a level on its full
+  // grid (dense NX x NY; have = 1 where a patch of the level holds the cell)
+  virtual void dims(int l, int* NX, int* NY) const = 0;
+  virtual void boxes(int l, std::vector<int>& out) const = 0;
+  virtual int flags(int l, double tol, std::vector<unsigned char>& flag, std::vector<unsigned char>& have) = 0;
 };
 
 AmrBase* make_amr_f64(int model);
@@ -416,6 +441,9 @@ class Amr : public AmrBase {
   std::vector<long long> cells_, atlas_;
   double* sc_ = nullptr;       // dt0, t, last_dt, courant, clipped
   double* staging_ = nullptr;
+  size_t stage_bytes_ = 0;
+  unsigned char* flag_buf_ = nullptr;   // atlas-sized flag plane (when staging_ is smaller)
+  size_t flag_cap_ = 0;
   double* hsc_ = nullptr;      // pinned host scalars
   cudaStream_t st_ = nullptr, cap_ = nullptr;
   std::map<unsigned, std::pair<cudaGraphExec_t, unsigned>> graphs_;   // cur bits -> (graph, cur bits after)
@@ -717,6 +745,7 @@ class Amr : public AmrBase {
       for (auto& b : v) mx = std::max(mx, (size_t)b.nx * b.ny);
     staging_ = lv_[0]->template alloc_dev<double>(mx * NV);
     if (!staging_) return SGN_ENOMEM;
+    stage_bytes_ = mx * NV * sizeof(double);
     // step bookkeeping
     dt_.L = L; dt_.strang = prm_.strang; dt_.cfl = prm_.cfl;
     double Rl = 1.0;
@@ -940,6 +969,42 @@ class Amr : public AmrBase {
       if (rc) return rc;
     }
     drop_amr_graphs();
+    return SGN_OK;
+  }
+
+  void dims(int l, int* NX, int* NY) const override { *NX = NX_[l]; *NY = NY_[l]; }
+
+  void boxes(int l, std::vector<int>& out) const override {
+    out.clear();
+    for (const Box& b : bx_[l]) out.insert(out.end(), {b.i0, b.j0, b.nx, b.ny});
+  }
+
+  int flags(int l, double tol, std::vector<unsigned char>& flag, std::vector<unsigned char>& have) override {
+    Dev<Real>& d = lv_[l]->dev();
+    unsigned char* fd = (unsigned char*)staging_;   // >= nvar doubles per cell of the largest patch
+    std::vector<unsigned char> atl(d.fs);
+    if ((size_t)d.fs > stage_bytes_) {
+      if (!flag_buf_ || flag_cap_ < d.fs) {
+        flag_buf_ = lv_[0]->template alloc_dev<unsigned char>(d.fs);
+        if (!flag_buf_) return SGN_ENOMEM;
+        flag_cap_ = d.fs;
+      }
+      fd = flag_buf_;
+    }
+    dim3 gr((d.nxp + 31) / 32, (d.nyp + 7) / 8);
+    k_amr_flag<Real><<<gr, dim3(32, 8), 0, st_>>>(d, lv_[l]->cur(), tol, fd);
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaMemcpyAsync(atl.data(), fd, d.fs, cudaMemcpyDeviceToHost, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    flag.assign((size_t)NX_[l] * NY_[l], 0);
+    have.assign((size_t)NX_[l] * NY_[l], 0);
+    for (const Box& b : bx_[l])
+      for (int j = 0; j < b.ny; j++)
+        for (int i = 0; i < b.nx; i++) {
+          const size_t o = (size_t)(b.j0 + j) * NX_[l] + (b.i0 + i);
+          flag[o] = atl[(size_t)pidx_of(l, b, i + 2, j + 2)];
+          have[o] = 1;
+        }
     return SGN_OK;
   }
 

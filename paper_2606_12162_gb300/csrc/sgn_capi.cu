@@ -319,6 +319,64 @@ int sgn_amr_create(const sgn_grid* grid0, const double* b_finest, int nlevels, i
   return SGN_OK;
 }
 
+// Box lists from refinement flags (reading A12 of the refinement oracle):
+// level by level from the coarsest, flag the level's cells (surface jump to a
+// neighbour above tol; where the level has no patch, the flag of the parent
+// cell), widen the flags by `buffer` cells, and cut the refinable part of each
+// new box of the level (two cells inside its edges except along the domain
+// boundary) into tile x tile squares, the last ones clipped; every square
+// holding a widened flag becomes a box of the next level.
+static int flagged_boxes(sgn::AmrBase* impl, int L, int r, double tol, int tile, int buffer,
+                         std::vector<std::vector<int>>& out) {
+  out.assign(L > 1 ? L - 1 : 0, {});
+  std::vector<int> parents;
+  impl->boxes(0, parents);
+  std::vector<unsigned char> prev;    // final flags of the previous level
+  int pNX = 0;
+  for (int l = 0; l + 1 < L; l++) {
+    int NX, NY;
+    impl->dims(l, &NX, &NY);
+    std::vector<unsigned char> f, have;
+    int rc = impl->flags(l, tol, f, have);
+    if (rc) return rc;
+    if (l > 0)
+      for (int Y = 0; Y < NY; Y++)
+        for (int X = 0; X < NX; X++) {
+          const size_t o = (size_t)Y * NX + X;
+          if (!have[o]) f[o] = prev[(size_t)(Y / r) * pNX + X / r];
+        }
+    // widen by buffer cells: rows, then columns
+    std::vector<unsigned char> t(f.size(), 0), w(f.size(), 0);
+    for (int Y = 0; Y < NY; Y++)
+      for (int X = 0; X < NX; X++)
+        if (f[(size_t)Y * NX + X])
+          for (int x = std::max(0, X - buffer); x <= std::min(NX - 1, X + buffer); x++) t[(size_t)Y * NX + x] = 1;
+    for (int Y = 0; Y < NY; Y++)
+      for (int X = 0; X < NX; X++)
+        if (t[(size_t)Y * NX + X])
+          for (int y = std::max(0, Y - buffer); y <= std::min(NY - 1, Y + buffer); y++) w[(size_t)y * NX + X] = 1;
+    std::vector<int>& nb = out[l];
+    for (size_t k = 0; k + 3 < parents.size(); k += 4) {
+      const int i0 = parents[k], j0 = parents[k + 1], nx = parents[k + 2], ny = parents[k + 3];
+      const int x0 = i0 + (i0 == 0 ? 0 : 2), x1 = i0 + nx - (i0 + nx == NX ? 0 : 2);
+      const int y0 = j0 + (j0 == 0 ? 0 : 2), y1 = j0 + ny - (j0 + ny == NY ? 0 : 2);
+      for (int ty = y0; ty < y1; ty += tile)
+        for (int tx = x0; tx < x1; tx += tile) {
+          const int tw = std::min(tile, x1 - tx), th = std::min(tile, y1 - ty);
+          bool any = false;
+          for (int y = ty; y < ty + th && !any; y++)
+            for (int x = tx; x < tx + tw; x++)
+              if (w[(size_t)y * NX + x]) { any = true; break; }
+          if (any) nb.insert(nb.end(), {tx * r, ty * r, tw * r, th * r});
+        }
+    }
+    parents = nb;
+    prev.swap(f);
+    pNX = NX;
+  }
+  return SGN_OK;
+}
+
 int sgn_amr_regrid(sgn_amr* h, const double* b_finest, const int* nboxes, const int* boxes) {
   if (!h || !b_finest) return SGN_EINVAL;
   if (h->args.L > 1 && (!nboxes || !boxes)) return SGN_EINVAL;
@@ -342,6 +400,38 @@ void sgn_amr_destroy(sgn_amr* a) {
   if (!a) return;
   delete a->impl;
   delete a;
+}
+
+int sgn_amr_regrid_flagged(sgn_amr* h, const double* b_finest, double tol, int tile, int buffer, int* nboxes) {
+  if (!h || !b_finest || !(tol > 0) || !isfinite(tol) || tile < 1 || buffer < 0) return SGN_EINVAL;
+  const int L = h->args.L;
+  if (L < 2) return SGN_EINVAL;
+  std::vector<std::vector<int>> bl;
+  int rc = flagged_boxes(h->impl, L, h->args.r, tol, tile, buffer, bl);
+  if (rc) return rc;
+  std::vector<int> nb(L - 1), flat;
+  for (int l = 0; l + 1 < L; l++) {
+    nb[l] = (int)bl[l].size() / 4;
+    flat.insert(flat.end(), bl[l].begin(), bl[l].end());
+  }
+  if (flat.empty()) flat.push_back(0);
+  rc = sgn_amr_regrid(h, b_finest, nb.data(), flat.data());
+  if (rc) return rc;
+  if (nboxes)
+    for (int l = 0; l + 1 < L; l++) nboxes[l] = nb[l];
+  return SGN_OK;
+}
+
+int sgn_amr_get_boxes(const sgn_amr* h, int level, int* boxes, int cap) {
+  if (!h || level < 0 || level >= h->args.L || cap < 0) return SGN_EINVAL;
+  std::vector<int> v;
+  h->impl->boxes(level, v);
+  const int n = (int)v.size() / 4;
+  if (boxes) {
+    if (cap < n) return SGN_ERANGE;
+    for (size_t i = 0; i < v.size(); i++) boxes[i] = v[i];
+  }
+  return n;
 }
 
 int sgn_amr_npatches(const sgn_amr* a, int level) { return a ? a->impl->npatches(level) : SGN_EINVAL; }

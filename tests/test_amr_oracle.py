@@ -264,3 +264,61 @@ def test_regrid_copies_and_interpolates(A):
             m = q2[2 * jc - 20:2 * jc - 18, 2 * ic - 24:2 * ic - 22].mean()
             assert abs(m - q_old[0, jc - 8, ic - 8]) <= 1e-14 * max(1.0, abs(m))
             assert np.ptp(q2[2 * jc - 20:2 * jc - 18, 2 * ic - 24:2 * ic - 22]) > 0.0   # not a plain copy
+
+
+def _channel_soliton(A, a=0.3, nx0=96, ny0=8, r=2, dx0=0.4, H=1.0, x0=10.0):
+    xf, yf = W.cell_centres(nx0 * r, ny0 * r, dx0 / r, dx0 / r)
+    bf = np.full(xf.shape, -H)
+    qf = W.soliton_state(2, xf, yf, bf, a, H, x0)
+    qc = qf.reshape(qf.shape[0], ny0, r, nx0, r).mean(axis=(2, 4))
+    return bf, [qc, qf], nx0, ny0, r, dx0
+
+
+def test_flagged_boxes_follow_the_wave(A, oracle_mod):
+    """A12 (Sec. 6.3 flag): regridding from the surface-jump flags every four
+    level-0 steps keeps the fine level on a travelling solitary wave, so the
+    composite solution stays closer to the uniform fine grid than with the
+    patch left where the wave started; the flagged boxes obey the nesting
+    rules (the constructor validates them) and cover every flagged cell."""
+    bf, qs, nx0, ny0, r, dx0 = _channel_soliton(A)
+    T, tol = 3.0, 0.01
+
+    def run(regrid_every):
+        am = A.AmrOracle(bf, nx0, ny0, dx0, r, [[(36, 0, 28, 16)]], model=2, **CFG)
+        am.set_state(qs)
+        n = 0
+        while am.t < T - 1e-12:
+            assert am.step_dt(min(am.dt_next, T - am.t)) == 0
+            n += 1
+            if regrid_every and n % regrid_every == 0:
+                boxes = am.flag_boxes(tol, 4, 2)
+                e = am.patch_state(0, 0)[0]
+                jump = np.zeros(e.shape, dtype=bool)
+                jump[:, 1:] |= np.abs(np.diff(e, axis=1)) > tol
+                jump[:, :-1] |= np.abs(np.diff(e, axis=1)) > tol
+                cov = np.zeros(e.shape, dtype=bool)
+                for (i0, j0, nx, ny) in boxes[0]:
+                    cov[j0 // r:(j0 + ny) // r, i0 // r:(i0 + nx) // r] = True
+                assert cov[jump].all()
+                am.regrid(boxes)
+        return am
+    u = oracle_mod.Oracle(bf, dx=dx0 / r, model=2, **CFG)
+    u.set_state(qs[1])
+    t = 0.0
+    while t < T - 1e-12:
+        dt = min(u.dt_cfl(), T - t)
+        assert u.step_dt(dt) == 0
+        t += dt
+    eu = u.get_state()[0][0]
+
+    def composite(am):
+        eta = np.repeat(np.repeat(am.patch_state(0, 0)[0], r, 0), r, 1)
+        for k, (i0, j0, nx, ny) in enumerate(am.boxes[1]):
+            eta[j0:j0 + ny, i0:i0 + nx] = am.patch_state(1, k)[0]
+        return eta
+    static, moved = run(0), run(4)
+    e_static = np.abs(composite(static) - eu).max()
+    e_moved = np.abs(composite(moved) - eu).max()
+    assert e_moved < 0.5 * e_static, (e_moved, e_static)
+    crest = int(np.argmax(eu[0]))
+    assert any(i0 <= crest < i0 + nx for (i0, j0, nx, ny) in moved.boxes[1])

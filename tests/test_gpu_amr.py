@@ -228,3 +228,43 @@ def test_mixed_regrid_against_fp64_oracle(M, A):
         for k in range(len(g.boxes[l])):
             err = rel_l2(g.get_patch(l, k)[:3], o.patch_state(l, k)[:3])
             assert err[0] <= 1e-5 and err[1] <= 1e-3 and err[2] <= 1e-3, (l, k, err)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_flagged_regrid_tracks_like_the_oracle(M, A, precision):
+    """sgn_amr_regrid_flagged (reading A12) every four level-0 steps on a
+    travelling solitary wave: the same boxes as the oracle's flag rule at every
+    regrid (FP64: bit for bit; mixed: where no jump is within 1e-4 of the
+    threshold), and the same states (FP64 1e-12; mixed within the hierarchy
+    tolerances)."""
+    nx0, ny0, r, dx0, H = 96, 8, 2, 0.4, 1.0
+    xf, yf = W.cell_centres(nx0 * r, ny0 * r, dx0 / r, dx0 / r)
+    bf = np.full(xf.shape, -H)
+    qf = W.soliton_state(2, xf, yf, bf, 0.3, H, 10.0)
+    qs = [qf.reshape(qf.shape[0], ny0, r, nx0, r).mean(axis=(2, 4)), qf]
+    boxes0 = [[(36, 0, 28, 16)]]
+    g = M.Hierarchy(bf, nx0, ny0, dx0, r, boxes0, model=2, precision=precision, **CFG)
+    g.set_state(qs)
+    o = A.AmrOracle(bf, nx0, ny0, dx0, r, boxes0, model=2, **CFG)
+    o.set_state(qs)
+    tol, moved = 0.01, 0
+    for it in range(6):
+        g.step(4)
+        assert o.step(4) == 0
+        ob = o.flag_boxes(tol, 4, 2)
+        e = o.patch_state(0, 0)[0]
+        near = np.abs(np.abs(np.diff(e, axis=1)) - tol).min()
+        nb = g.regrid_flagged(bf, tol, 4, 2)
+        if precision == 0 or near > 1e-4:
+            assert g.boxes[1] == ob[0], it
+        o.regrid(g.boxes[1:])
+        assert nb == [len(g.boxes[1])]
+        moved += g.boxes[1] != boxes0[0]
+        for k in range(len(g.boxes[1])):
+            err = rel_l2(g.get_patch(1, k), o.patch_state(1, k))
+            if precision == 0:
+                assert (err <= FP64_TOL).all(), (it, k, err)
+            else:
+                assert err[0] <= 1e-5 and err[1] <= 1e-3, (it, k, err)
+    assert moved > 0
+    assert g.status() == 0
