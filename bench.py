@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the refined-hierarchy (config 4) line")
     ap.add_argument("--batched-n0", type=int, default=1024, help="level-0 size of the config-4 hierarchy")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector (config 5) line")
+    ap.add_argument("--no-regrid", action="store_true", help="skip the flag-driven regrid after the config-4 timing")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (no sgn_autotune before timing)")
     ap.add_argument("--only", default=None, choices=["batched", "learned"],
@@ -342,7 +343,7 @@ def time_batched(args):
         for k, q in enumerate(lv):
             g.set_patch(l, k, q)
     setup = time.perf_counter() - t0
-    del c["b"]
+    b_finest = c.pop("b")
     rc0 = g.step_rc(max(1, args.warmup))
     tune = None
     if rc0 == 0 and not args.no_tune:
@@ -365,6 +366,22 @@ def time_batched(args):
     nf = c["n0"] * r ** (len(cells) - 1)
     fine_equiv = float(nf) * nf * r ** (len(cells) - 1)                # uniform finest grid, same span
     m, clipped = g.mass()
+    launches = g.launches_per_step() * k
+    # one flag-driven regrid after the timed region (outside it): the patches
+    # move from the ring onto the cells whose surface jump exceeds 5 cm, then
+    # three more level-0 steps check the new hierarchy
+    regrid = None
+    if rc == 0 and not args.no_regrid:
+        try:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            nb = g.regrid_flagged(b_finest, 0.05, 16, 2)
+            torch.cuda.synchronize()
+            regrid = {"s": time.perf_counter() - t1, "tol_m": 0.05, "tile": 16, "buffer": 2,
+                      "patches_per_level": [1] + nb, "status_after_3_steps": g.step_rc(3)}
+        except Exception as ex:          # reported, not fatal to the line
+            regrid = {"error": str(ex)[:200]}
+    del b_finest
     return {"value": per_step * k / (ms / 1e3), "unit": UNIT, "steps": k, "ms_per_step": ms / k,
             "dtype": "f32+f64", "status": rc,
             "workload": "config4: 3 levels, ratio 4, level 0 %dx%d at 2 km, fractal bathymetry + coast strip, "
@@ -374,7 +391,7 @@ def time_batched(args):
             "interior_cells_per_level": cells, "atlas_cells_per_level": atlas,
             "cell_updates_per_step": per_step, "atlas_cell_updates_per_step": atlas_per_step,
             "fine_equivalent_cell_updates_per_s": fine_equiv * k / (ms / 1e3),
-            "gpu_launches": g.launches_per_step() * k, "setup_s": setup, "tuning": tune,
+            "gpu_launches": launches, "setup_s": setup, "tuning": tune, "regrid": regrid,
             "mass": m, "clipped": clipped}
 
 
