@@ -95,7 +95,6 @@ static const int kCellShape[3][2] = {{32, 8}, {32, 4}, {64, 4}};
 template <int MODEL, typename Real>
 class Solver : public SolverBase {
   static constexpr int NV = MT<MODEL>::NV;
-  static constexpr int NP = PT<MODEL>::NP;
   static constexpr int NF = FT<MODEL>::NF;
   // Face blocks of 256 threads in FP32 (four resident blocks per SM within the
   // 64-register bound; fewer, larger blocks or more registers per thread
@@ -224,7 +223,8 @@ class Solver : public SolverBase {
     d_.q[0] = dnew<Real>(NV * fs); d_.q[1] = dnew<Real>(NV * fs);
     d_.b = dnew<Real>(fs); d_.c2 = dnew<Real>(fs); d_.psx = dnew<Real>(fs); d_.psy = dnew<Real>(fs);
     d_.phi = dnew<unsigned char>(fs);
-    d_.W = dnew<Real>(NV * fs); d_.P = dnew<Real>(NP * fs);
+    d_.W = dnew<Real>(NV * fs);
+    if (sizeof(Real) == 8) d_.P = dnew<Real>((size_t)PT<MODEL>::NP * fs);   // primitives: FP64 path only
     d_.FX = dnew<Real>(NF * fs); d_.FY = dnew<Real>(NF * fs);
     d_.TX = dnew<Real>(NV * fs); d_.TY = dnew<Real>(NV * fs);
     d_.theta = dnew<Real>(fs);
@@ -232,7 +232,7 @@ class Solver : public SolverBase {
     double* sc = dnew<double>(16);
     unsigned* si = dnew<unsigned>(16);
     staging_ = dnew<double>((size_t)NV * g.nx * g.ny);
-    if (!d_.q[0] || !d_.q[1] || !d_.b || !d_.c2 || !d_.psx || !d_.psy || !d_.phi || !d_.W || !d_.P ||
+    if (!d_.q[0] || !d_.q[1] || !d_.b || !d_.c2 || !d_.psx || !d_.psy || !d_.phi || !d_.W || (sizeof(Real) == 8 && !d_.P) ||
         !d_.FX || !d_.FY || !d_.TX || !d_.TY || !d_.theta || !d_.G2 || !sc || !si || !staging_)
       return SGN_ENOMEM;
     d_.dt = sc; d_.t = sc + 1; d_.last_dt = sc + 2; d_.courant = sc + 3; d_.mass = sc + 4;
@@ -264,7 +264,7 @@ class Solver : public SolverBase {
     // zero every buffer (faces outside the computed ranges stay 0), theta = 1
     for (size_t k = 0; k < 2; k++) SGN_CK(cudaMemsetAsync(d_.q[k], 0, NV * fs * sizeof(Real), st_));
     SGN_CK(cudaMemsetAsync(d_.W, 0, NV * fs * sizeof(Real), st_));
-    SGN_CK(cudaMemsetAsync(d_.P, 0, NP * fs * sizeof(Real), st_));
+    if (d_.P) SGN_CK(cudaMemsetAsync(d_.P, 0, PT<MODEL>::NP * fs * sizeof(Real), st_));
     SGN_CK(cudaMemsetAsync(d_.FX, 0, NF * fs * sizeof(Real), st_));
     SGN_CK(cudaMemsetAsync(d_.FY, 0, NF * fs * sizeof(Real), st_));
     SGN_CK(cudaMemsetAsync(d_.TX, 0, NV * fs * sizeof(Real), st_));
