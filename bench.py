@@ -34,24 +34,30 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP32 CUDA-core peak: 152 SMs x 128 FFMA/clk/SM x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# FP64 flops per cell-update of each kernel of the FP64 path (ncu thread-instruction
-# counts dadd + dmul + 2 dfma on the 2048^2 case divided by its cells;
-# profiles/step_kernels_2048_counters.md).
+# Counters per cell-update of each kernel, keyed by (model, precision, kernel,
+# block shape) -- the shape the launch used, since the halo work of a face
+# block depends on it; profiles/step_kernels_2048_counters.md (2048^2 is above
+# L2, so per-cell figures carry over to 4096^2).  A kernel launched with a shape
+# or code that these captures did not see reports null.
+# FP64 flops (dadd + dmul + 2 dfma thread instructions / cells), FP64 path:
 FLOPS_PER_CELL = {
-    ("hsgn", "fp64", "k_prep"): 133.2, ("hsgn", "fp64", "k_face_x"): 306.8,
-    ("hsgn", "fp64", "k_face_y"): 320.1, ("hsgn", "fp64", "k_trans_x"): 127.6,
-    ("hsgn", "fp64", "k_trans_y"): 127.6, ("hsgn", "fp64", "k_theta"): 29.4,
-    ("hsgn", "fp64", "k_update"): 217.4,
+    ("hsgn", "fp64", "k_prep", "32x8"): 133.2, ("hsgn", "fp64", "k_face_x", "64x4"): 306.8,
+    ("hsgn", "fp64", "k_face_y", "16x16"): 320.1, ("hsgn", "fp64", "k_theta", "32x8"): 29.4,
+    ("hsgn", "fp64", "k_update", "32x8"): 217.4,
 }
-# DRAM bytes (read + write) per cell of one launch, same capture (2048^2 is above
-# L2, so traffic per cell carries over to 4096^2).
+# DRAM bytes (read + write):
 TRAFFIC_PER_CELL = {
-    ("hsgn", "mixed", "k_prep"): 89, ("hsgn", "mixed", "k_face_x"): 145, ("hsgn", "mixed", "k_face_y"): 139,
-    ("hsgn", "mixed", "k_trans_x"): 106, ("hsgn", "mixed", "k_trans_y"): 106, ("hsgn", "mixed", "k_theta"): 17,
-    ("hsgn", "mixed", "k_update"): 221,
-    ("hsgn", "fp64", "k_prep"): 183, ("hsgn", "fp64", "k_face_x"): 293, ("hsgn", "fp64", "k_face_y"): 279,
-    ("hsgn", "fp64", "k_trans_x"): 215, ("hsgn", "fp64", "k_trans_y"): 215, ("hsgn", "fp64", "k_theta"): 37,
-    ("hsgn", "fp64", "k_update"): 441,
+    **{("hsgn", "mixed", "k_prep", sh): 58 for sh in ("32x8", "32x4", "64x4")},
+    ("hsgn", "mixed", "k_face_x", "128x2"): 128, ("hsgn", "mixed", "k_face_x", "256x1"): 128,
+    ("hsgn", "mixed", "k_face_x", "64x4"): 129,
+    **{("hsgn", "mixed", "k_face_y", sh): 129 for sh in ("32x8", "32x16", "64x4")},
+    **{("hsgn", "mixed", "k_trans_x", sh): 106 for sh in ("32x4", "32x8", "64x4")},
+    **{("hsgn", "mixed", "k_trans_y", sh): 107 for sh in ("32x4", "32x8", "64x4")},
+    **{("hsgn", "mixed", "k_theta", sh): 17 for sh in ("32x8", "32x4", "64x4")},
+    **{("hsgn", "mixed", "k_update", sh): 221 for sh in ("32x8", "32x4", "64x4")},
+    ("hsgn", "fp64", "k_prep", "32x8"): 183, ("hsgn", "fp64", "k_face_x", "64x4"): 293,
+    ("hsgn", "fp64", "k_face_y", "16x16"): 279, ("hsgn", "fp64", "k_theta", "32x8"): 37,
+    ("hsgn", "fp64", "k_update", "32x8"): 441,
 }
 
 
@@ -70,6 +76,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the refined-hierarchy (config 4) line")
     ap.add_argument("--batched-n0", type=int, default=1024, help="level-0 size of the config-4 hierarchy")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector (config 5) line")
+    ap.add_argument("--tuning", default=None,
+                    help="force a launch tuning (8 comma-separated option indices of sgn_set_tuning) instead of "
+                         "autotuning")
     ap.add_argument("--no-regrid", action="store_true", help="skip the flag-driven regrid after the config-4 timing")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (no sgn_autotune before timing)")
@@ -196,10 +205,11 @@ def barrier(ws):
 # reads or writes, once, for element size s, nvar fields nv (the depth plane and
 # the positivity factors are FP64 in both precisions).
 def kernel_bytes(name, nv, s):
-    if name == "k_prep":        # q, b, c2 -> W, P (nv + 1 planes), depth
-        return (nv + 2) * s + (2 * nv + 1) * s + 8
+    p = nv + 1 if s == 8 else 0            # primitive planes: FP64 path only
+    if name == "k_prep":        # q, b, c2 -> W, P, depth
+        return (nv + 2) * s + (nv + p) * s + 8
     if name in ("k_face_x", "k_face_y"):   # W, P, b, c2, psi, depth -> face planes
-        return (2 * nv + 4) * s + 8 + (2 * nv + 9) * s
+        return (nv + p + 3) * s + 8 + (2 * nv + 9) * s
     if name in ("k_trans_x", "k_trans_y"):  # other direction's Lv, Rv; Roe data, M -> T
         return (2 * nv + 9) * s + nv * s
     if name == "k_theta":       # two mass fluxes, eta, b -> theta
@@ -209,7 +219,11 @@ def kernel_bytes(name, nv, s):
     return 0
 
 
-def roofline(model, prec, kt, cells, b_alg, nv, esize, hbm, hbm_src):
+SLOT = {"k_prep": "prep", "k_face_x": "face_x", "k_face_y": "face_y", "k_trans_x": "trans_x",
+        "k_trans_y": "trans_y", "k_theta": "theta", "k_update": "update"}
+
+
+def roofline(model, prec, kt, cells, b_alg, nv, esize, hbm, hbm_src, shapes=None):
     """Roofline of the kernel with the largest time in kt (name -> (ms, launches)).
     FP64 path: bound by the FP64 pipe (flops counted by ncu per cell).  Mixed path:
     HBM; achieved = the step's algorithmic bytes per cell-update x cells of one
@@ -219,10 +233,11 @@ def roofline(model, prec, kt, cells, b_alg, nv, esize, hbm, hbm_src):
         return None
     name, (kms, kn) = max(kt.items(), key=lambda kv: kv[1][0])
     per = kms / 1e3 / max(kn, 1)
-    tr = TRAFFIC_PER_CELL.get((model, prec, name))
-    out = {"kernel": name, "launch_ms": per * 1e3, "share": kms / sum(v[0] for v in kt.values()),
+    shape = (shapes or {}).get(SLOT.get(name, ""), "")
+    tr = TRAFFIC_PER_CELL.get((model, prec, name, shape))
+    out = {"kernel": name, "block": shape, "launch_ms": per * 1e3, "share": kms / sum(v[0] for v in kt.values()),
            "traffic": tr * cells if tr else None}
-    fl = FLOPS_PER_CELL.get((model, prec, name))
+    fl = FLOPS_PER_CELL.get((model, prec, name, shape))
     if prec == "fp64" and fl:
         ach = fl * cells / per / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -307,7 +322,11 @@ def time_path(S, c, args, precision, profile):
     s.add_gauges(c["gauges"], args.steps + args.warmup + 8)
     s.step(args.warmup)
     tuning = None
-    if not args.no_tune:
+    if args.tuning:
+        s.set_tuning([int(v) for v in args.tuning.split(",")])
+        tuning = {"s": 0.0, "forced": args.tuning,
+                  "shapes": {k: ("%dx%d" % v[1]) if k != "schedule" else v[0] for k, v in s.tuning().items()}}
+    elif not args.no_tune:
         # autotuner (setup, outside the timed region): launch shapes per kernel
         t0 = time.perf_counter()
         s.autotune(reps=10)
@@ -326,6 +345,7 @@ def time_path(S, c, args, precision, profile):
     kt = s.kernel_times() if profile else {}
     f, dt, cr = s.status()
     s.tuning_report = tuning
+    s.shapes = {k: "%dx%d" % v[1] for k, v in s.tuning().items() if k != "schedule"}
     return s, ms, kt, f
 
 
@@ -485,7 +505,7 @@ def main():
 
     # dominant kernel and its roofline
     b_alg = (nv * 2 * esize + esize + 1)   # algorithmic bytes per cell-update of the step
-    roof = roofline(args.model, args.precision, kt, cells, b_alg, nv, esize, hbm, hbm_src)
+    roof = roofline(args.model, args.precision, kt, cells, b_alg, nv, esize, hbm, hbm_src, s.shapes)
     step_hbm_frac = value / ws * b_alg / (hbm * 1e9)
 
     # end to end through the C ABI with pinned host buffers
@@ -516,12 +536,16 @@ def main():
         import copy
         a2 = copy.copy(args)
         a2.steps = max(3, min(args.steps, 20))
+        # default launch shapes (the FP64 counters' shapes); tuning gains nothing
+        # measurable on this FP64-pipe-bound path (33.0 vs 33.1 ms per step)
+        a2.no_tune, a2.tuning = True, None
         s2, ms2, kt2, f2 = time_path(S, c, a2, 0, profile=True)
         ms2 = reduce_max(ms2, ws)
         v2 = cells * a2.steps * ws / (ms2 / 1e3)
         extra = {"value": v2, "unit": UNIT, "steps": a2.steps, "ms_per_step": ms2 / a2.steps,
                  "dtype": "f64", "tuning": s2.tuning_report,
-                 "roofline": roofline(args.model, "fp64", kt2, cells, nv * 16 + 9, nv, 8, hbm, hbm_src),
+                 "roofline": roofline(args.model, "fp64", kt2, cells, nv * 16 + 9, nv, 8, hbm, hbm_src,
+                                      s2.shapes),
                  "hbm_fraction_step": v2 / ws * (nv * 16 + 9) / (hbm * 1e9),
                  "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt2.items() if v[1]}}
         del s2
