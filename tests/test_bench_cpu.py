@@ -68,3 +68,21 @@ def test_reference_arm_other_ranks_exit_silently():
     r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1", "--nx", "512"],
                    env={"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_roofline_uses_the_counters_of_the_launch_shape():
+    """The bench's roofline object takes ncu traffic only for the block shape the
+    dominant kernel ran with, and null for a shape no capture saw."""
+    sys.path.insert(0, ROOT)
+    import bench
+    kt = {"k_face_y": (10.0, 10), "k_update": (5.0, 10)}
+    cells = 4096 * 4096
+    r = bench.roofline("hsgn", "mixed", kt, cells, 61, 7, 4, 6787.2, "measured", {"face_y": "32x8"})
+    assert r["kernel"] == "k_face_y" and r["block"] == "32x8"
+    assert r["traffic"] == bench.TRAFFIC_PER_CELL[("hsgn", "mixed", "k_face_y", "32x8")] * cells
+    assert abs(r["achieved"] - 61 * cells / 1e-3 / 1e9) < 1e-6 * r["achieved"]
+    r = bench.roofline("hsgn", "mixed", kt, cells, 61, 7, 4, 6787.2, "measured", {"face_y": "16x16"})
+    assert r["traffic"] is None
+    # compulsory bytes per cell: no primitive planes in the mixed path
+    assert bench.kernel_bytes("k_face_y", 7, 4) == (7 + 3) * 4 + 8 + (2 * 7 + 9) * 4
+    assert bench.kernel_bytes("k_face_y", 7, 8) == (2 * 7 + 4) * 8 + 8 + (2 * 7 + 9) * 8
