@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="force a launch tuning (8 comma-separated option indices of sgn_set_tuning) instead of "
                          "autotuning")
+    ap.add_argument("--fp64-check-steps", type=int, default=25,
+                    help="fixed steps of the mixed-vs-FP64 error check beside the FP64 line")
     ap.add_argument("--no-regrid", action="store_true", help="skip the flag-driven regrid after the config-4 timing")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (no sgn_autotune before timing)")
@@ -349,6 +351,33 @@ def time_path(S, c, args, precision, profile):
     return s, ms, kt, f
 
 
+def mixed_error(S, c, steps):
+    """Error of the mixed path against the FP64 path (itself equal to the FP64
+    oracle to 1e-12 on the parity cases) on the full workload: both take the
+    same `steps` fixed steps of 0.9 x the FP64 path's first CFL step from the
+    same state; relative L2 of eta, hu, hv over wet cells and the largest
+    surface error relative to the largest initial surface displacement."""
+    out = {}
+    for prec in (0, 1):
+        s = S.Solver(c["b"], precision=prec, **cfg_kwargs(c))
+        s.set_state(c["q"])
+        if prec == 0:
+            dt = 0.9 * s.next_dt()
+        for _ in range(steps):
+            s.step_dt(dt)
+        out[prec] = s.get_state(0b111)[0]
+        del s
+    ref, got = out[0], out[1]
+    b = c["b"]
+    wet = ref[0] - b > 1e-3
+    rel = [float(np.linalg.norm((got[k] - ref[k])[wet]) / max(np.linalg.norm(ref[k][wet]), 1e-300))
+           for k in range(3)]
+    eta0 = np.where(np.asarray(c["q"][0]) - b > 0, np.asarray(c["q"][0]), 0.0)
+    return {"steps": steps, "dt_s": dt, "rel_l2": {"eta": rel[0], "hu": rel[1], "hv": rel[2]},
+            "max_eta_err_rel": float(np.abs(got[0] - ref[0]).max() / max(np.abs(eta0).max(), 1e-300)),
+            "tolerance": {"rel_l2": 1e-4, "max_eta_err_rel": 1e-3}}
+
+
 def time_batched(args):
     """Config 4 (three levels, ratio 4, ~2000 patches along a wave front), mixed
     precision: W level-0 steps of warm-up, then K level-0 steps (each with all
@@ -549,6 +578,7 @@ def main():
                  "hbm_fraction_step": v2 / ws * (nv * 16 + 9) / (hbm * 1e9),
                  "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt2.items() if v[1]}}
         del s2
+        extra["mixed_vs_fp64"] = mixed_error(S, c, args.fp64_check_steps)
 
     batched = None
     if not args.no_batched:
