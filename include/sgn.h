@@ -118,8 +118,11 @@ int sgn_create(const sgn_grid* grid, const double* bathymetry, int model,
                const sgn_params* params, const unsigned char* phi_override,
                const sgn_allocator* allocator, void* cuda_stream, sgn_solver** out);
 
-/* Replace the state: q is nvar*ny*nx doubles in host memory (pinned memory makes
- * the copy asynchronous-capable); t is the new time.  The SWE/dry switch is
+/* Replace the state: q is nvar*ny*nx doubles in host memory; t is the new time.
+ * Pinned, mapped host memory (cudaHostAlloc, cudaMallocHost, a range registered
+ * with cudaHostRegister, a pinned torch tensor) is read by the conversion kernel
+ * in place over the host link; other host memory is first copied to a device
+ * staging buffer.  The SWE/dry switch is
  * applied (auxiliaries zeroed where phi_T = 0 or h <= dry_tol, momenta zeroed
  * where h <= dry_tol), the status word and the gauge records are cleared and the
  * CFL time step of the new state is computed.  Errors: EINVAL, ECUDA. */
@@ -141,7 +144,9 @@ int sgn_step_dt(sgn_solver* s, double dt);
 
 /* Copy fields of the state to host memory.  field_mask: bit k selects field k
  * (0: all fields); the selected fields are written consecutively (ny*nx doubles
- * each) into out, which holds out_len doubles.  t_out may be NULL.
+ * each) into out, which holds out_len doubles.  Pinned, mapped host memory is
+ * written by the conversion kernel in place; other host memory through a device
+ * staging buffer.  t_out may be NULL.
  * Synchronises the stream.  Errors: EINVAL, ERANGE, ECUDA. */
 int sgn_get_state(sgn_solver* s, int field_mask, double* out, size_t out_len, double* t_out);
 

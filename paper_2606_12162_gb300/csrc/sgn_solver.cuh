@@ -294,11 +294,28 @@ class Solver : public SolverBase {
     return set_state(q0.data(), 0.0, false);
   }
 
+  // Device address of a host buffer the GPU can reach (pinned and mapped:
+  // cudaHostAlloc, cudaMallocHost or a registered range), else null.
+  static const void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+  }
+
   int set_state(const double* q, double t, bool device) override {
     size_t n = (size_t)d_.nx * d_.ny * NV;
-    SGN_CK(cudaMemcpyAsync(staging_, q, n * sizeof(double), device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));
+    // device memory and mapped pinned host memory are read by the pack kernel
+    // in place; other host memory goes through the staging buffer
+    const double* src = device ? q : (const double*)mapped_host(q);
+    if (!src) {
+      SGN_CK(cudaMemcpyAsync(staging_, q, n * sizeof(double), cudaMemcpyHostToDevice, st_));
+      src = staging_;
+    }
     cur_ = 0;
-    k_pack_state<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, staging_, 0);
+    k_pack_state<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, src, 0);
     hscal_[0] = t;
     SGN_CK(cudaMemcpyAsync(d_.t, hscal_, sizeof(double), cudaMemcpyHostToDevice, st_));
     SGN_CK(cudaMemsetAsync(d_.status, 0, sizeof(unsigned), st_));
@@ -463,15 +480,12 @@ class Solver : public SolverBase {
     int nsel = 0;
     for (int k = 0; k < NV; k++) nsel += (mask >> k) & 1;
     if (len < nsel * n) return SGN_ERANGE;
-    k_unpack_state<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, staging_, cur_);
+    // device memory and mapped pinned host memory are written by the unpack
+    // kernel in place; other host memory through the staging buffer
+    double* dst = device ? out : (double*)mapped_host(out);
+    k_unpack_state<MODEL, Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, dst ? dst : staging_, cur_, mask);
     SGN_CK(cudaGetLastError());
-    int o = 0;
-    for (int k = 0; k < NV; k++) {
-      if (!((mask >> k) & 1)) continue;
-      SGN_CK(cudaMemcpyAsync(out + o * n, staging_ + k * n, n * sizeof(double),
-                             device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st_));
-      o++;
-    }
+    if (!dst) SGN_CK(cudaMemcpyAsync(out, staging_, nsel * n * sizeof(double), cudaMemcpyDeviceToHost, st_));
     if (t_out || !device) {
       SGN_CK(cudaMemcpyAsync(hscal_, d_.t, sizeof(double), cudaMemcpyDeviceToHost, st_));
       SGN_CK(cudaStreamSynchronize(st_));
