@@ -84,7 +84,10 @@ def parse():
     ap.add_argument("--no-regrid", action="store_true", help="skip the flag-driven regrid after the config-4 timing")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (no sgn_autotune before timing)")
-    ap.add_argument("--only", default=None, choices=["batched", "learned"],
+    ap.add_argument("--table-configs", default="1,2,3", help="configurations of --only table")
+    ap.add_argument("--table-c2-steps", type=int, default=1000)
+    ap.add_argument("--table-c3-steps", type=int, default=2000)
+    ap.add_argument("--only", default=None, choices=["batched", "learned", "table"],
                     help="run only that line (for profiling); prints its object alone")
     return ap.parse_args()
 
@@ -378,6 +381,135 @@ def mixed_error(S, c, steps):
             "tolerance": {"rel_l2": 1e-4, "max_eta_err_rel": 1e-3}}
 
 
+def _oracle_rate(c, threads, budget_s, crop=384):
+    """Oracle cell-updates/s on a crop (whole grid if smaller) around the
+    source, in a fresh process with OMP_NUM_THREADS = threads."""
+    code = r"""
+import json, os, sys, time
+import numpy as np
+sys.path.insert(0, %r)
+from oracle import oracle as O
+d = np.load(sys.argv[1])
+kw = json.loads(sys.argv[2])
+o = O.Oracle(d["b"], **kw)
+o.set_state(d["q"])
+t0 = time.perf_counter(); o.step(1); per = max(time.perf_counter() - t0, 1e-6)
+k = max(1, int(%f / per))
+t0 = time.perf_counter(); o.step(k); el = time.perf_counter() - t0
+print(json.dumps({"rate": d["b"].size * k / el, "steps": k, "seconds": el}))
+""" % (ROOT, budget_s)
+    import tempfile
+    ny, nx = c["b"].shape
+    n = min(crop, nx, ny)
+    cx, cy = c.get("source", (0.5 * nx * c["dx"], 0.5 * ny * c["dx"]))
+    i0 = int(min(max((cx - c.get("x0", 0.0)) / c["dx"] - n // 2, 0), nx - n))
+    j0 = int(min(max((cy - c.get("y0", 0.0)) / c["dx"] - n // 2, 0), ny - n))
+    sl = (slice(j0, j0 + n), slice(i0, i0 + n))
+    with tempfile.TemporaryDirectory() as td:
+        f = os.path.join(td, "crop.npz")
+        np.savez(f, b=c["b"][sl], q=c["q"][(slice(None),) + sl])
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, "-c", code, f, json.dumps(cfg_kwargs(c))], env=env,
+                           capture_output=True, text=True)
+    if r.returncode:
+        return {"error": r.stderr[-300:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out.update(threads=threads, crop=n)
+    return out
+
+
+def _arrivals(rec, frac):
+    """First record time per gauge where |eta - eta(first record)| exceeds frac
+    (NaN where it never does)."""
+    eta = rec[:, :, 1]
+    hit = np.abs(eta - eta[0][None, :]) > frac
+    out = np.full(eta.shape[1], np.nan)
+    for g in range(eta.shape[1]):
+        k = np.nonzero(hit[:, g])[0]
+        if len(k):
+            out[g] = rec[k[0], g, 0]
+    return out
+
+
+def config_row(S, name, c, steps, rate_steps, warmup=3):
+    """One row of the results table: FP64 and mixed cell-updates/s (CFL steps,
+    graph replay, CUDA events), and the mixed path's error against the FP64
+    path after `steps` steps, both driven by the same dt (the smaller of their
+    two CFL steps; the FP64 path equals the oracle to 1e-12 on the parity
+    cases): relative L2 over wet cells, largest surface error relative to the
+    largest initial displacement, gauge arrival times (1 % of that
+    displacement) in units of the mean step."""
+    import torch
+    kw = dict(cfg_kwargs(c), x0=c.get("x0", 0.0), y0=c.get("y0", 0.0))
+    cells = c["b"].size
+    row = {"config": name, "cells": cells}
+    for prec, key in ((0, "fp64"), (1, "mixed")):
+        s = S.Solver(c["b"], precision=prec, **kw)
+        s.set_state(c["q"])
+        s.step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0.record(st)
+        s.step(rate_steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        row[key] = cells * rate_steps / (e0.elapsed_time(e1) / 1e3)
+        del s
+    eta0 = np.where(c["q"][0] - c["b"] > 0, c["q"][0], 0.0)
+    amp = float(np.abs(eta0).max())
+    sv = {}
+    for prec in (0, 1):
+        sv[prec] = S.Solver(c["b"], precision=prec, **kw)
+        sv[prec].set_state(c["q"])
+        if c.get("gauges") is not None:
+            sv[prec].add_gauges(c["gauges"], steps + 2)
+    t = 0.0
+    for _ in range(steps):
+        # the smaller of the two CFL steps, so that neither path exceeds its own
+        dt = min(sv[0].next_dt(), sv[1].next_dt())
+        sv[0].step_dt(dt)
+        sv[1].step_dt(dt)
+        t += dt
+    ref, got = sv[0].get_state(0b111)[0], sv[1].get_state(0b111)[0]
+    wet = ref[0] - c["b"] > 1e-3
+    rel = [float(np.linalg.norm((got[k] - ref[k])[wet]) / max(np.linalg.norm(ref[k][wet]), 1e-300))
+           for k in range(3)]
+    err = {"steps": steps, "t_s": t, "rel_l2": {"eta": rel[0], "hu": rel[1], "hv": rel[2]},
+           "max_eta_err_rel": float(np.abs(got[0] - ref[0]).max() / amp)}
+    if c.get("gauges") is not None:
+        ga, gb = _arrivals(sv[0].gauges(), 0.01 * amp), _arrivals(sv[1].gauges(), 0.01 * amp)
+        seen = ~np.isnan(ga) & ~np.isnan(gb)
+        err["gauges_with_arrival"] = int(seen.sum())
+        err["arrival_diff_max_in_dt"] = float(np.abs(ga - gb)[seen].max() / (t / steps)) if seen.any() else None
+        err["arrival_mismatch"] = int((np.isnan(ga) != np.isnan(gb)).sum())
+    row["mixed_vs_fp64"] = err
+    del sv
+    return row
+
+
+def results_table(args):
+    """Rows of the results table for configurations 1-3 (HSGN): GPU FP64 and
+    mixed throughput, the mixed error against FP64 over the configuration's
+    step count, and the oracle on the host cores, one thread and all."""
+    from paper_2606_12162_gb300 import sgn as S, workloads as W
+    rows = []
+    for k, (name, make, steps, rate_steps) in enumerate((
+            ("config1 256^2 dx=0.05 m soliton", lambda: W.config1(model=W.HSGN), 200, 200),
+            ("config2 4096^2 dx=10 m beach + landslide", lambda: W.config2(model=W.HSGN), args.table_c2_steps, 100),
+            ("config3 8192^2 dx=500 m fractal + uplift", lambda: W.config3(model=W.HSGN), args.table_c3_steps, 50))):
+        if str(k + 1) not in args.table_configs.split(","):
+            continue
+        c = make()
+        row = config_row(S, name, c, steps, rate_steps)
+        row["oracle_1_thread"] = _oracle_rate(c, 1, 8.0)
+        row["oracle_all_cores"] = _oracle_rate(c, os.cpu_count() or 1, 8.0)
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+        del c
+    return rows
+
+
 def time_batched(args):
     """Config 4 (three levels, ratio 4, ~2000 patches along a wave front), mixed
     precision: W level-0 steps of warm-up, then K level-0 steps (each with all
@@ -511,6 +643,10 @@ def main():
     ws, rank, local = dist_setup()
     build.build()
     S.load()
+    if args.only == "table":
+        if rank == 0:
+            print(json.dumps({"table": results_table(args)}), flush=True)
+        return
     if args.only:
         res = time_batched(args) if args.only == "batched" else time_learned(args)
         if rank == 0:
