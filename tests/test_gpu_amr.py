@@ -268,3 +268,34 @@ def test_flagged_regrid_tracks_like_the_oracle(M, A, precision):
                 assert err[0] <= 1e-5 and err[1] <= 1e-3, (it, k, err)
     assert moved > 0
     assert g.status() == 0
+
+
+def test_regrid_arguments_and_boxes_query(M):
+    """sgn_amr_get_boxes reports the boxes of every level (EINVAL for a bad
+    level, ERANGE for a short buffer); sgn_amr_regrid_flagged rejects a
+    non-positive threshold, a zero tile and a negative buffer, and a one-level
+    hierarchy, leaving the hierarchy as it was."""
+    import ctypes
+    from paper_2606_12162_gb300 import amr, sgn
+    nx0, ny0, r = 24, 20, 2
+    b, qs = W.amr_small_case(2, nx0, ny0, r, 3, seed=31, amp=0.2)
+    g = M.Hierarchy(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=2, **CFG)
+    g.set_state(qs)
+    assert g.get_boxes(0) == [(0, 0, nx0, ny0)]
+    assert g.get_boxes(1) == list(W.amr_boxes_small()[0])
+    assert g.get_boxes(2) == list(W.amr_boxes_small()[1])
+    L = amr.lib()
+    assert L.sgn_amr_get_boxes(g.h, 3, None, 0) == -1
+    buf = (ctypes.c_int * 8)()
+    assert L.sgn_amr_get_boxes(g.h, 1, buf, 2) == -9
+    before = [g.get_patch(l, k) for l in range(3) for k in range(g.npatches(l))]
+    for tol, tile, buffer in ((0.0, 4, 2), (0.01, 0, 2), (0.01, 4, -1)):
+        with pytest.raises(sgn.SGNError) as e:
+            g.regrid_flagged(b, tol, tile, buffer)
+        assert e.value.code == -1
+    after = [g.get_patch(l, k) for l in range(3) for k in range(g.npatches(l))]
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))
+    g.step(2)
+    assert g.status() == 0
+    with pytest.raises(sgn.SGNError):
+        M.Hierarchy(b[::4, ::4], nx0, ny0, 0.2, r, [], model=2, **CFG).regrid_flagged(b[::4, ::4], 0.01, 4, 2)
