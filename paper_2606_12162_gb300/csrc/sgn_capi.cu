@@ -274,51 +274,6 @@ static int amr_build(sgn::AmrArgs& a, const int* nboxes, const int* boxes, sgn::
   return SGN_OK;
 }
 
-extern "C" {
-
-int sgn_amr_create(const sgn_grid* grid0, const double* b_finest, int nlevels, int ratio, const int* nboxes,
-                   const int* boxes, int model, const sgn_params* params, const sgn_allocator* allocator,
-                   void* cuda_stream, sgn_amr** out) {
-  if (!out) return SGN_EINVAL;
-  *out = nullptr;
-  if (!grid0 || !b_finest || !params || nlevels < 1 || nlevels > sgn::AMR_MAXL || ratio < 2 || ratio > 8)
-    return SGN_EINVAL;
-  if (nlevels > 1 && (!nboxes || !boxes)) return SGN_EINVAL;
-  for (int i = 0; i < 4; i++)
-    if (grid0->bc[i] != SGN_BC_WALL && grid0->bc[i] != SGN_BC_EXTRAP) return SGN_EINVAL;
-  if (grid0->dx != grid0->dy) return SGN_EINVAL;
-  long long R = 1;
-  for (int l = 1; l < nlevels; l++) R *= ratio;
-  if ((long long)grid0->nx * R > (1LL << 30) || (long long)grid0->ny * R > (1LL << 30)) return SGN_EINVAL;
-  int r = check_args(grid0, b_finest, model, params);
-  if (r) return r;
-  if (allocator && (!allocator->alloc || !allocator->free)) return SGN_EINVAL;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SGN_ECUDA;
-  sgn_amr* h = new (std::nothrow) sgn_amr;
-  if (!h) return SGN_ENOMEM;
-  h->has_alloc = allocator != nullptr;
-  if (allocator) h->alloc = *allocator;
-  sgn::AmrArgs& a = h->args;
-  a.grid = *grid0;
-  a.prm = *params;
-  a.model = model;
-  a.L = nlevels;
-  a.r = ratio;
-  a.b = b_finest;
-  a.alloc = h->has_alloc ? &h->alloc : nullptr;
-  a.stream = (cudaStream_t)cuda_stream;
-  r = amr_build(a, nboxes, boxes, &h->impl);
-  a.b = nullptr;
-  a.boxes.clear();
-  if (r) {
-    delete h;
-    return r;
-  }
-  *out = h;
-  return SGN_OK;
-}
-
 // Box lists from refinement flags (reading A12 of the refinement oracle):
 // level by level from the coarsest, flag the level's cells (surface jump to a
 // neighbour above tol; where the level has no patch, the flag of the parent
@@ -374,6 +329,51 @@ static int flagged_boxes(sgn::AmrBase* impl, int L, int r, double tol, int tile,
     prev.swap(f);
     pNX = NX;
   }
+  return SGN_OK;
+}
+
+extern "C" {
+
+int sgn_amr_create(const sgn_grid* grid0, const double* b_finest, int nlevels, int ratio, const int* nboxes,
+                   const int* boxes, int model, const sgn_params* params, const sgn_allocator* allocator,
+                   void* cuda_stream, sgn_amr** out) {
+  if (!out) return SGN_EINVAL;
+  *out = nullptr;
+  if (!grid0 || !b_finest || !params || nlevels < 1 || nlevels > sgn::AMR_MAXL || ratio < 2 || ratio > 8)
+    return SGN_EINVAL;
+  if (nlevels > 1 && (!nboxes || !boxes)) return SGN_EINVAL;
+  for (int i = 0; i < 4; i++)
+    if (grid0->bc[i] != SGN_BC_WALL && grid0->bc[i] != SGN_BC_EXTRAP) return SGN_EINVAL;
+  if (grid0->dx != grid0->dy) return SGN_EINVAL;
+  long long R = 1;
+  for (int l = 1; l < nlevels; l++) R *= ratio;
+  if ((long long)grid0->nx * R > (1LL << 30) || (long long)grid0->ny * R > (1LL << 30)) return SGN_EINVAL;
+  int r = check_args(grid0, b_finest, model, params);
+  if (r) return r;
+  if (allocator && (!allocator->alloc || !allocator->free)) return SGN_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SGN_ECUDA;
+  sgn_amr* h = new (std::nothrow) sgn_amr;
+  if (!h) return SGN_ENOMEM;
+  h->has_alloc = allocator != nullptr;
+  if (allocator) h->alloc = *allocator;
+  sgn::AmrArgs& a = h->args;
+  a.grid = *grid0;
+  a.prm = *params;
+  a.model = model;
+  a.L = nlevels;
+  a.r = ratio;
+  a.b = b_finest;
+  a.alloc = h->has_alloc ? &h->alloc : nullptr;
+  a.stream = (cudaStream_t)cuda_stream;
+  r = amr_build(a, nboxes, boxes, &h->impl);
+  a.b = nullptr;
+  a.boxes.clear();
+  if (r) {
+    delete h;
+    return r;
+  }
+  *out = h;
   return SGN_OK;
 }
 
