@@ -100,3 +100,60 @@ def test_oracle_second_order_on_exact_wave(oracle_mod, T, model):
     # magnitude of Table 1 (unknown domain length and c^2 there): within 3x
     for e, t in zip(errs, TABLE1[model][1:4]):
         assert t / 3.0 < e < 3.0 * t, (errs, TABLE1[model])
+
+
+def _d(f, dx):
+    return np.gradient(f, dx, edge_order=2)
+
+
+@pytest.mark.parametrize("model", [1, 2])
+def test_waves_satisfy_the_pde(T, model):
+    """The profiles, put into the 1-D equations of Sec. 3 as printed (flat
+    bottom, d/dt = -s d/dxi), leave residuals at the level of the finite
+    differences used to evaluate them: an independent check of the
+    travelling-wave reduction written in the module."""
+    lam = LAM
+    dxi = 2e-3
+    xi = np.arange(-12.0, 12.0 + dxi / 2, dxi)
+    if model == 1:
+        s, f = T.mbhsgn_wave(A, H, lam, 12.5)
+        h, hu, hw, hp = f(xi)
+    else:
+        s, f, _ = T.hsgn_wave(A, H, lam)
+        h, hu, hw, hs, hp, hpb = f(xi)
+    u, w, p = hu / h, hw / h, hp / h
+    dt = lambda q: -s * _d(q, dxi)
+    dx = lambda q: _d(q, dxi)
+    res = [dt(h) + dx(hu),
+           dt(hu) + dx(hu * u + 0.5 * G * h * h + h * p)]
+    scale = [np.abs(dx(hu)).max(), np.abs(dx(hu * u + 0.5 * G * h * h)).max()]
+    if model == 1:
+        res += [dt(hw) + dx(hu * w) - 1.5 * p,
+                dt(hp) + dx(hu * p) + h * lam * (dx(u) + w / (h / 2.0))]
+        scale += [np.abs(1.5 * p).max(), np.abs(h * lam * dx(u)).max()]
+    else:
+        sg, pb = hs / h, hpb / h
+        res += [dt(hw) + dx(hu * w) - pb,
+                dt(hs) + dx(hu * sg) + 6.0 * pb - 12.0 * p,
+                dt(hp) + dx(hu * (p + lam)) - lam * u * dx(h) + lam * sg,
+                dt(hpb) + dx(hu * pb) + 6.0 * lam * (w - 0.5 * sg)]
+        scale += [np.abs(pb).max(), np.abs(12.0 * p).max(), np.abs(lam * sg).max(),
+                  np.abs(6.0 * lam * w).max()]
+    for k, (r, sc) in enumerate(zip(res, scale)):
+        inner = r[5:-5]
+        assert np.abs(inner).max() < 1e-5 * sc, (model, k, np.abs(inner).max(), sc)
+
+
+def test_pde_pin_detects_a_wrong_pressure_relation(T, monkeypatch):
+    """Plant a mistake in the travelling-wave module (the momentum relation's
+    s^2 term dropped from p(h)): the PDE residual of the momentum equation must
+    then be far above the finite-difference level."""
+    monkeypatch.setattr(T, "_p", lambda h, s2, H, g: g * (H * H - h * h) / (2.0 * h))
+    dxi = 2e-3
+    xi = np.arange(-12.0, 12.0 + dxi / 2, dxi)
+    s, f = T.mbhsgn_wave(A, H, LAM, 12.5)
+    h, hu, hw, hp = f(xi)
+    p = hp / h
+    r = -s * _d(hu, dxi) + _d(hu * hu / h + 0.5 * G * h * h + h * p, dxi)
+    sc = np.abs(_d(hu * hu / h + 0.5 * G * h * h, dxi)).max()
+    assert np.abs(r[5:-5]).max() > 1e-2 * sc
