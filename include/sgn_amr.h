@@ -109,10 +109,11 @@ int sgn_amr_regrid(sgn_amr* a, const double* b_finest, const int* nboxes, const 
  * flags are widened by `buffer` cells of that level; the part of each new
  * level-l box that may hold finer patches (two cells inside its edges, except
  * along the domain boundary) is cut into tile x tile squares of level-l cells
- * (the last ones clipped), and every square holding a widened flag becomes a
- * level-(l+1) box.  Then as sgn_amr_regrid with those boxes.  nboxes (L - 1
+ * (tile >= 2; the last ones clipped, a one-cell remainder joined to the square
+ * before it), and every square holding a widened flag becomes a level-(l+1)
+ * box.  Then as sgn_amr_regrid with those boxes.  nboxes (L - 1
  * ints, may be NULL) receives the number of boxes per level >= 1.  Errors as
- * sgn_amr_regrid; EINVAL also for L = 1, tol <= 0, tile < 1 or buffer < 0. */
+ * sgn_amr_regrid; EINVAL also for L = 1, tol <= 0, tile < 2 or buffer < 0. */
 int sgn_amr_regrid_flagged(sgn_amr* a, const double* b_finest, double tol, int tile, int buffer, int* nboxes);
 
 /* Boxes of a level (4 ints i0, j0, nx, ny each, in that level's cells) into

@@ -76,7 +76,8 @@ below are the readings the CUDA hierarchy implements as well.
     cell's flag; flags are widened by `buffer` cells (a square); the part of
     each new box of the level that may hold finer patches (two cells inside
     its edges except along the domain boundary) is cut into tile x tile
-    squares from its low corner, the last ones clipped, and every square
+    squares from its low corner (tile >= 2), the last ones clipped and a
+    one-cell remainder merged into the square before it, and every square
     holding a widened flag becomes a box of the next level.
 """
 import numpy as np
@@ -103,6 +104,21 @@ def bc_map(X, N, lo, hi):
     if X >= N:
         return (2 * N - 1 - X, True) if hi == O.WALL else (N - 1, False)
     return X, False
+
+
+def _cuts(a0, a1, tile):
+    """A12: [a0, a1) cut into pieces of `tile` cells from a0; a last piece of one
+    cell is merged into the one before it, so that no piece ends one cell short
+    of a1 (a box one parent cell from its parent's edge breaks A1 when that edge
+    is the domain boundary)."""
+    out, x = [], a0
+    while x < a1:
+        w = min(tile, a1 - x)
+        if a1 - (x + w) == 1:
+            w += 1
+        out.append((x, w))
+        x += w
+    return out
 
 
 def minmod(a, b):
@@ -501,6 +517,8 @@ class AmrOracle:
     def flag_boxes(self, tol, tile, buffer):
         """A12: box lists of levels 1..L-1 from refinement flags of the
         current state."""
+        if tile < 2:
+            raise ValueError("tile must be at least 2 cells")
         r, out, prev = self.r, [], None
         parents = [self.boxes[0][0]]
         for l in range(self.L - 1):
@@ -527,9 +545,8 @@ class AmrOracle:
             for (i0, j0, nx, ny) in parents:
                 x0, x1 = i0 + (0 if i0 == 0 else 2), i0 + nx - (0 if i0 + nx == NX else 2)
                 y0, y1 = j0 + (0 if j0 == 0 else 2), j0 + ny - (0 if j0 + ny == NY else 2)
-                for ty in range(y0, y1, tile):
-                    for tx in range(x0, x1, tile):
-                        tw, th = min(tile, x1 - tx), min(tile, y1 - ty)
+                for ty, th in _cuts(y0, y1, tile):
+                    for tx, tw in _cuts(x0, x1, tile):
                         if w[ty:ty + th, tx:tx + tw].any():
                             bl.append((tx * r, ty * r, tw * r, th * r))
             out.append(bl)

@@ -279,8 +279,9 @@ static int amr_build(sgn::AmrArgs& a, const int* nboxes, const int* boxes, sgn::
 // neighbour above tol; where the level has no patch, the flag of the parent
 // cell), widen the flags by `buffer` cells, and cut the refinable part of each
 // new box of the level (two cells inside its edges except along the domain
-// boundary) into tile x tile squares, the last ones clipped; every square
-// holding a widened flag becomes a box of the next level.
+// boundary) into tile x tile squares, the last ones clipped (a one-cell
+// remainder joins the square before it); every square holding a widened flag
+// becomes a box of the next level.
 static int flagged_boxes(sgn::AmrBase* impl, int L, int r, double tol, int tile, int buffer,
                          std::vector<std::vector<int>>& out) {
   out.assign(L > 1 ? L - 1 : 0, {});
@@ -315,15 +316,24 @@ static int flagged_boxes(sgn::AmrBase* impl, int L, int r, double tol, int tile,
       const int i0 = parents[k], j0 = parents[k + 1], nx = parents[k + 2], ny = parents[k + 3];
       const int x0 = i0 + (i0 == 0 ? 0 : 2), x1 = i0 + nx - (i0 + nx == NX ? 0 : 2);
       const int y0 = j0 + (j0 == 0 ? 0 : 2), y1 = j0 + ny - (j0 + ny == NY ? 0 : 2);
-      for (int ty = y0; ty < y1; ty += tile)
-        for (int tx = x0; tx < x1; tx += tile) {
-          const int tw = std::min(tile, x1 - tx), th = std::min(tile, y1 - ty);
+      // tile x tile squares from the low corner, the last ones clipped; a
+      // one-cell remainder joins the square before it (no box may end one
+      // parent cell short of its parent's edge when that edge is the domain's)
+      auto piece = [&](int a, int a1) {
+        int w = std::min(tile, a1 - a);
+        return a1 - (a + w) == 1 ? w + 1 : w;
+      };
+      for (int ty = y0, th = 0; ty < y1; ty += th) {
+        th = piece(ty, y1);
+        for (int tx = x0, tw = 0; tx < x1; tx += tw) {
+          tw = piece(tx, x1);
           bool any = false;
           for (int y = ty; y < ty + th && !any; y++)
             for (int x = tx; x < tx + tw; x++)
               if (w[(size_t)y * NX + x]) { any = true; break; }
           if (any) nb.insert(nb.end(), {tx * r, ty * r, tw * r, th * r});
         }
+      }
     }
     parents = nb;
     prev.swap(f);
@@ -403,7 +413,7 @@ void sgn_amr_destroy(sgn_amr* a) {
 }
 
 int sgn_amr_regrid_flagged(sgn_amr* h, const double* b_finest, double tol, int tile, int buffer, int* nboxes) {
-  if (!h || !b_finest || !(tol > 0) || !isfinite(tol) || tile < 1 || buffer < 0) return SGN_EINVAL;
+  if (!h || !b_finest || !(tol > 0) || !isfinite(tol) || tile < 2 || buffer < 0) return SGN_EINVAL;
   const int L = h->args.L;
   if (L < 2) return SGN_EINVAL;
   std::vector<std::vector<int>> bl;

@@ -322,3 +322,29 @@ def test_flagged_boxes_follow_the_wave(A, oracle_mod):
     assert e_moved < 0.5 * e_static, (e_moved, e_static)
     crest = int(np.argmax(eu[0]))
     assert any(i0 <= crest < i0 + nx for (i0, j0, nx, ny) in moved.boxes[1])
+
+
+@pytest.mark.parametrize("seed,tol,tile,buffer", [(41, 0.005, 4, 1), (42, 0.02, 6, 2), (43, 0.001, 3, 0)])
+def test_flagged_boxes_obey_the_hierarchy_rules(A, seed, tol, tile, buffer):
+    """A12 produces box lists that A1 accepts (aligned to parent cells, inside
+    one parent, two parent cells from its edges except at the domain boundary,
+    disjoint: the constructor validates all of it), for several states and
+    settings; every flagged level-0 cell inside the refinable region lies under
+    a level-1 box."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=seed, amp=0.3)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
+    am.set_state(qs)
+    assert am.step(2) == 0
+    boxes = am.flag_boxes(tol, tile, buffer)
+    A.AmrOracle(b, 24, 20, 0.2, 2, boxes, model=2, **CFG)     # raises on a rule violation
+    e = am.patch_state(0, 0)[0]
+    jump = np.zeros(e.shape, dtype=bool)
+    jump[:, 1:] |= np.abs(np.diff(e, axis=1)) > tol
+    jump[:, :-1] |= np.abs(np.diff(e, axis=1)) > tol
+    jump[1:, :] |= np.abs(np.diff(e, axis=0)) > tol
+    jump[:-1, :] |= np.abs(np.diff(e, axis=0)) > tol
+    cov = np.zeros(e.shape, dtype=bool)
+    for (i0, j0, nx, ny) in boxes[0]:
+        cov[j0 // 2:(j0 + ny) // 2, i0 // 2:(i0 + nx) // 2] = True
+    assert cov[jump].all()
+    assert sum(len(bl) for bl in boxes) > 0

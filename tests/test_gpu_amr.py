@@ -299,3 +299,28 @@ def test_regrid_arguments_and_boxes_query(M):
     assert g.status() == 0
     with pytest.raises(sgn.SGNError):
         M.Hierarchy(b[::4, ::4], nx0, ny0, 0.2, r, [], model=2, **CFG).regrid_flagged(b[::4, ::4], 0.01, 4, 2)
+
+
+@pytest.mark.parametrize("seed,tol,tile,buffer", [(43, 0.001, 3, 0), (41, 0.005, 5, 1)])
+def test_flagged_boxes_with_remainders_match_the_oracle(M, A, seed, tol, tile, buffer):
+    """Tiles that do not divide the refinable regions (one-cell remainders at
+    the domain boundary are joined to the tile before them): the library's
+    boxes equal the oracle's A12 boxes on both refined levels, the hierarchy
+    accepts them, and the regridded states match the oracle's regrid."""
+    nx0, ny0, r = 24, 20, 2
+    b, qs = W.amr_small_case(2, nx0, ny0, r, 3, seed=seed, amp=0.3)
+    g = M.Hierarchy(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=2, **CFG)
+    g.set_state(qs)
+    o = A.AmrOracle(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=2, **CFG)
+    o.set_state(qs)
+    g.step(2)
+    assert o.step(2) == 0
+    want = o.flag_boxes(tol, tile, buffer)
+    g.regrid_flagged(b, tol, tile, buffer)
+    assert g.boxes[1] == want[0] and g.boxes[2] == want[1]
+    o.regrid(want)
+    g.step(2)
+    assert o.step(2) == 0
+    for l in range(3):
+        for k in range(len(g.boxes[l])):
+            assert (rel_l2(g.get_patch(l, k), o.patch_state(l, k)) <= FP64_TOL).all(), (l, k)
