@@ -348,3 +348,18 @@ def test_flagged_boxes_obey_the_hierarchy_rules(A, seed, tol, tile, buffer):
         cov[j0 // 2:(j0 + ny) // 2, i0 // 2:(i0 + nx) // 2] = True
     assert cov[jump].all()
     assert sum(len(bl) for bl in boxes) > 0
+
+
+@pytest.mark.parametrize("seed,tol,tile", [(51, 0.003, 4), (52, 0.01, 2), (53, 0.002, 5)])
+def test_flag_driven_regrid_keeps_mass_and_steps_on(A, seed, tol, tile):
+    """Over wet bathymetry, regridding to the flagged boxes (A11 + A12) keeps
+    the mass to rounding, and the hierarchy steps on with exact mass."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=seed, amp=0.3, wetdry=False)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
+    am.set_state(qs)
+    assert am.step(3) == 0
+    m0 = am.mass()
+    am.regrid(am.flag_boxes(tol, tile, 1))
+    assert abs(am.mass() - m0) <= 1e-13 * m0
+    assert am.step(3) == 0
+    assert abs(am.mass() - m0 - am.clipped) <= 1e-13 * m0
