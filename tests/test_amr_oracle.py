@@ -363,3 +363,31 @@ def test_flag_driven_regrid_keeps_mass_and_steps_on(A, seed, tol, tile):
     assert abs(am.mass() - m0) <= 1e-13 * m0
     assert am.step(3) == 0
     assert abs(am.mass() - m0 - am.clipped) <= 1e-13 * m0
+
+
+def test_regrid_to_empty_levels_and_back(A):
+    """A state at rest raises no flag: the flagged layout has no patches on the
+    refined levels; the hierarchy steps on at rest, and regridding back to the
+    original boxes (all cells interpolated from level 0) stays at rest."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
+    rest = []
+    for l, q in enumerate(qs):
+        z = np.zeros_like(q)
+        bl = b
+        for _ in range(2 - l):
+            bl = A.block_mean(bl, 2)
+        z[0] = np.maximum(bl, 0.0)
+        rest.append(z)
+    am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
+    am.set_state(rest)
+    assert am.step(1) == 0
+    boxes = am.flag_boxes(0.01, 4, 2)
+    assert boxes == [[], []]
+    am.regrid(boxes)
+    assert am.step(2) == 0
+    assert np.abs(am.patch_state(0, 0)[1:]).max() <= 1e-14
+    am.regrid(W.amr_boxes_small())
+    assert am.step(2) == 0
+    for l, pats in enumerate(am.levels):
+        for k in range(len(pats)):
+            assert np.abs(am.patch_state(l, k)[1:]).max() <= 1e-14

@@ -324,3 +324,39 @@ def test_flagged_boxes_with_remainders_match_the_oracle(M, A, seed, tol, tile, b
     for l in range(3):
         for k in range(len(g.boxes[l])):
             assert (rel_l2(g.get_patch(l, k), o.patch_state(l, k)) <= FP64_TOL).all(), (l, k)
+
+
+def test_regrid_to_empty_levels_and_back(M, A):
+    """A state at rest raises no flag: the flagged layout has no patches on the
+    refined levels (the atlases hold no patch); the hierarchy steps on, then
+    regrids back to the original boxes, all as the oracle does."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
+    rest = []
+    for l in range(3):
+        bl = b
+        for _ in range(2 - l):
+            bl = A.block_mean(bl, 2)
+        z = np.zeros_like(qs[l])
+        z[0] = np.maximum(bl, 0.0)
+        rest.append(z)
+    g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, bc=(0, 0, 1, 1), **CFG)
+    g.set_state(rest)
+    o = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, bc=(0, 0, 1, 1), **CFG)
+    o.set_state(rest)
+    g.step(1)
+    assert o.step(1) == 0
+    assert g.regrid_flagged(b, 0.01, 4, 2) == [0, 0]
+    o.regrid(o.flag_boxes(0.01, 4, 2))
+    g.step(2)
+    assert o.step(2) == 0
+    assert g.status() == 0
+    assert (rel_l2(g.get_patch(0, 0), o.patch_state(0, 0)) <= FP64_TOL).all()
+    g.regrid(b, W.amr_boxes_small())
+    o.regrid(W.amr_boxes_small())
+    g.step(2)
+    assert o.step(2) == 0
+    for l in range(3):
+        for k in range(len(g.boxes[l])):
+            q = g.get_patch(l, k)
+            assert np.abs(q[1:]).max() <= 1e-14
+            assert (rel_l2(q, o.patch_state(l, k)) <= FP64_TOL).all()
