@@ -224,23 +224,35 @@ int sgn_launches_per_step(sgn_solver* s);
  *     thread-block shape of that kernel, 0 .. SGN_TUNE_OPTS-1 (0 = default);
  *     sgn_get_tuning reports the block dimensions each index stands for;
  *   SGN_TUNE_SCHEDULE: 0 = one stream; 1 = the x and y face kernels, then the
- *     two transverse kernels, as two concurrent branches.
- * Every option computes the same values bit for bit; only the time differs.
+ *     two transverse kernels, as two concurrent branches; 2 = the one-pass
+ *     kernel: the whole step in one launch that keeps every intermediate
+ *     quantity on chip and moves only the state through HBM (mixed precision on
+ *     a single grid only: EINVAL for an FP64 solver; a refined level falls back
+ *     to 0).  With schedule 2 the SGN_TUNE_UPDATE option selects the rows one
+ *     block of the one-pass kernel marches over: 128, 64 or 256 (its block is
+ *     128 columns wide).
+ * The block-shape options and schedules 0 and 1 compute the same values bit
+ * for bit; schedule 2 evaluates the same expressions in one kernel and agrees
+ * with them to FP32 rounding (the compiler may fuse a different set of
+ * multiply-adds).
  *
  * sgn_autotune times, on the current state and in step order, reps launches
  * of each option of each kernel (CUDA events on the solver stream, after one
- * untimed launch), keeps the fastest, then times the first phase of the step
- * (prep to positivity factors) as a CUDA graph in both schedules.  It leaves
+ * untimed launch), keeps the fastest, then times the whole step as a CUDA graph
+ * in every schedule (schedule 2 with each of its row counts) and keeps the
+ * fastest.  It leaves
  * the state, time, next dt and status unchanged: the next step is the one that
  * would have run without it.  choice (SGN_TUNE_N ints, may be NULL) receives
  * the tuning kept; ms (SGN_TUNE_N * SGN_TUNE_OPTS doubles, may be NULL) the
  * mean time per launch [ms] of option o of slot k at ms[k*SGN_TUNE_OPTS + o]
- * (for the schedule slot: of the first phase; -1 where not measured).
+ * (for the schedule slot: of the whole step, the best row count for schedule
+ * 2; -1 where not measured).
  * Synchronises the stream.  Errors: EINVAL (reps outside 1..10000), ECUDA.
  *
  * sgn_set_tuning installs a tuning (EINVAL for an index out of range);
  * sgn_get_tuning reports the current one and, per slot, the block dimensions
- * (bx, by; 0 for the schedule slot).  Any pointer of sgn_get_tuning may be
+ * (bx, by; 0 for the schedule slot; with schedule 2 the update slot reports
+ * 128 columns by the rows per block).  Any pointer of sgn_get_tuning may be
  * NULL. */
 #define SGN_TUNE_N 8
 #define SGN_TUNE_OPTS 3

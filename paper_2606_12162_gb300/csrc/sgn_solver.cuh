@@ -9,6 +9,7 @@
 
 #include "../../include/sgn.h"
 #include "sgn_kernels.cuh"
+#include "sgn_fused.cuh"
 
 namespace sgn {
 
@@ -64,15 +65,22 @@ inline int status_to_error(unsigned st) {
     if (e_ != cudaSuccess) return SGN_ECUDA; \
   } while (0)
 
-enum { KN_PREP, KN_FACEX, KN_FACEY, KN_TRANSX, KN_TRANSY, KN_THETA, KN_UPDATE, KN_FINAL, KN_GAUGE, KN_COUNT };
-static const char* const kKernelNames[KN_COUNT] = {
-    "k_prep", "k_face_x", "k_face_y", "k_trans_x", "k_trans_y", "k_theta", "k_update", "k_finalize", "k_gauge"};
+enum { KN_PREP, KN_FACEX, KN_FACEY, KN_TRANSX, KN_TRANSY, KN_THETA, KN_UPDATE, KN_FINAL, KN_GAUGE, KN_FUSED,
+       KN_COUNT };
+static const char* const kKernelNames[KN_COUNT] = {"k_prep",   "k_face_x",   "k_face_y", "k_trans_x",
+                                                   "k_trans_y", "k_theta",   "k_update", "k_finalize",
+                                                   "k_gauge",  "k_step_fused"};
 
 // Autotuner choices (include/sgn.h, SGN_TUNE_*): one launch-shape option per
-// tuned kernel, in step order, then the schedule of the first phase.  Option 0
+// tuned kernel, in step order, then the schedule of the step.  Option 0
 // is the default of each slot.
 enum { TU_PREP, TU_FACEX, TU_FACEY, TU_TRANSX, TU_TRANSY, TU_THETA, TU_UPDATE, TU_SCHED, TU_N };
 static const int TU_OPTS = 3;
+// schedules of the step: serial, two branches in the first phase, and the one-pass kernel
+// (k_step_fused: the whole step in one launch; FP32 bulk, uniform grids only)
+enum { SCHED_SERIAL = 0, SCHED_FORK = 1, SCHED_FUSED = 2, SCHED_N = 3 };
+// rows per block of the one-pass kernel, by the option of its slot (SGN_TUNE_UPDATE)
+static const int kFusedRows[3] = {128, 64, 256};
 static_assert(TU_N == SGN_TUNE_N && TU_OPTS == SGN_TUNE_OPTS, "tuning table size");
 
 // Face block shapes (BX, BY) per option; they are template arguments of
@@ -115,6 +123,7 @@ class Solver : public SolverBase {
   cudaStream_t aux_ = nullptr;  // second branch of the forked schedule
   cudaEvent_t fork_[4] = {nullptr, nullptr, nullptr, nullptr};
   unsigned long long* save_ = nullptr;   // accumulators kept across autotuning
+  float ms_sched_[SCHED_N] = {0.f, 0.f, 0.f};   // autotuner: best step time per schedule
 
   Dev<Real> d_{};
   sgn_allocator al_{};
@@ -255,6 +264,9 @@ class Solver : public SolverBase {
     gInt_ = dim3((g.nx + 31) / 32, (g.ny + 7) / 8);
     set_geometry();
     SGN_CK(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
+    if constexpr (kFusedBuilt)
+      SGN_CK(cudaFuncSetAttribute(k_step_fused<MODEL, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(FusedSmem<MODEL, Real>)));
     for (int k = 0; k < 4; k++) SGN_CK(cudaEventCreateWithFlags(&fork_[k], cudaEventDisableTiming));
     save_ = dnew<unsigned long long>(4);
     if (!save_) return SGN_ENOMEM;
@@ -340,13 +352,31 @@ class Solver : public SolverBase {
   // in two phases (a refined level exchanges ghost positivity factors and
   // records reflux fluxes in between).
   void launch_step(cudaStream_t s, int c) {
-    launch_phase1(s, c);
-    launch_phase2(s, c);
+    if (tune_[TU_SCHED] == SCHED_FUSED) {
+      pre(s, KN_FUSED);
+      launch_fused(s, c);
+      post(s);
+    } else {
+      launch_phase1(s, c);
+      launch_phase2(s, c);
+    }
     pre(s, KN_FINAL);
     k_finalize<Real><<<1, 32, 0, s>>>(d_, 1); post(s);
     if (d_.ngauge > 0) {
       pre(s, KN_GAUGE);
       k_gauge<Real><<<1, 256, 0, s>>>(d_, 1 - c); post(s);
+    }
+  }
+
+  // The one-pass step (k_step_fused): strips of FUSED_OUT columns by chunks of
+  // kFusedRows[option of the update slot] rows, one block each.
+  static constexpr bool kFusedBuilt = sizeof(Real) == 4;
+  bool fused_ok() const { return kFusedBuilt && !d_.kind; }
+  void launch_fused(cudaStream_t s, int c) {
+    if constexpr (kFusedBuilt) {
+      const int H = kFusedRows[tune_[TU_UPDATE]];
+      const dim3 g((d_.nx + FUSED_OUT - 1) / FUSED_OUT, (d_.ny + H - 1) / H);
+      k_step_fused<MODEL, Real><<<g, FUSED_NT, sizeof(FusedSmem<MODEL, Real>), s>>>(d_, c, H);
     }
   }
 
@@ -415,11 +445,15 @@ class Solver : public SolverBase {
     SGN_CK(cudaMemcpyAsync(kp, h.data(), d_.fs, cudaMemcpyHostToDevice, st_));
     SGN_CK(cudaStreamSynchronize(st_));
     d_.kind = kp;
+    if (tune_[TU_SCHED] == SCHED_FUSED) tune_[TU_SCHED] = SCHED_SERIAL;   // uniform grids only
     drop_graphs();
     return SGN_OK;
   }
 
-  int launches_per_step() override { return d_.ngauge > 0 ? 9 : 8; }
+  int launches_per_step() override {
+    const int n = tune_[TU_SCHED] == SCHED_FUSED ? 2 : 8;
+    return d_.ngauge > 0 ? n + 1 : n;
+  }
 
   int build_graph(int c) {
     cudaGraph_t gr;
@@ -632,7 +666,8 @@ class Solver : public SolverBase {
   int set_tuning(const int* ch) override {
     if (!ch) return SGN_EINVAL;
     for (int k = 0; k < TU_N; k++)
-      if (ch[k] < 0 || ch[k] >= (k == TU_SCHED ? 2 : TU_OPTS)) return SGN_EINVAL;
+      if (ch[k] < 0 || ch[k] >= (k == TU_SCHED ? SCHED_N : TU_OPTS)) return SGN_EINVAL;
+    if (ch[TU_SCHED] == SCHED_FUSED && !fused_ok()) return SGN_EINVAL;
     SGN_CK(cudaStreamSynchronize(st_));
     for (int k = 0; k < TU_N; k++) tune_[k] = ch[k];
     set_geometry();
@@ -641,22 +676,27 @@ class Solver : public SolverBase {
   }
 
   int get_tuning(int* ch, int* bx, int* by) override {
+    const bool fz = tune_[TU_SCHED] == SCHED_FUSED;
     for (int k = 0; k < TU_N; k++) {
       if (ch) ch[k] = tune_[k];
-      if (bx) bx[k] = k == TU_SCHED ? 0 : (int)tb_[k].x;
-      if (by) by[k] = k == TU_SCHED ? 0 : (int)tb_[k].y;
+      // with the one-pass schedule the update slot stands for its block: NT columns by H rows
+      const int x = k == TU_SCHED ? 0 : (fz && k == TU_UPDATE ? FUSED_NT : (int)tb_[k].x);
+      const int y = k == TU_SCHED ? 0 : (fz && k == TU_UPDATE ? kFusedRows[tune_[k]] : (int)tb_[k].y);
+      if (bx) bx[k] = x;
+      if (by) by[k] = y;
     }
     return SGN_OK;
   }
 
   // Times every option of each tuned kernel on the current state, in step
-  // order, keeping the fastest (ties keep the lower option), then the two
-  // schedules of the first phase replayed as graphs.  Every option of a kernel
-  // writes the same values (a block shape changes only which thread computes
-  // what), so each kernel leaves the next one's inputs as a step would.  The
-  // speed and Courant maxima and the status word are saved first and put back
-  // at the end, and the planes the trials rewrite are recomputed by every
-  // step, so the next step is the one that would have run without tuning.
+  // order, keeping the fastest (ties keep the lower option), then the whole
+  // step in every schedule replayed as a graph (the one-pass kernel with each
+  // row count).  Every option of a kernel writes the same values (a block shape
+  // changes only which thread computes what), so each kernel leaves the next
+  // one's inputs as a step would; every trial reads q[cur] and writes only
+  // scratch planes or q[1 - cur].  The speed and Courant maxima and the status
+  // word are saved first and put back at the end, so the next step is the one
+  // that would have run without tuning (on the schedule kept).
   int autotune(int reps, int* ch, double* ms) override {
     if (reps < 1 || reps > 10000) return SGN_EINVAL;
     if (ms)
@@ -696,23 +736,41 @@ class Solver : public SolverBase {
       tune_[k] = bo;
       set_geometry();
     }
-    float serial = 0.f;
-    for (int o = 0; o < 2 && rc == SGN_OK; o++) {
-      tune_[TU_SCHED] = o;
-      cudaGraph_t gr = nullptr;
-      cudaGraphExec_t gx = nullptr;
-      if (cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SGN_ECUDA; break; }
-      launch_phase1(cap_, c);
-      if (cudaStreamEndCapture(cap_, &gr) != cudaSuccess) { rc = SGN_ECUDA; break; }
-      cudaError_t e = cudaGraphInstantiate(&gx, gr, 0);
-      cudaGraphDestroy(gr);
-      if (e != cudaSuccess) { rc = SGN_ECUDA; break; }
-      float t = 0.f;
-      rc = time_it([&]() { cudaGraphLaunch(gx, st_); }, &t);
-      cudaGraphExecDestroy(gx);
-      if (ms) ms[TU_SCHED * TU_OPTS + o] = t;
-      if (o == 0) serial = t;
-      else tune_[TU_SCHED] = (rc == SGN_OK && t < serial) ? 1 : 0;
+    // schedules: the whole step (first phase and update, or the one-pass
+    // kernel with each of its row counts) replayed as a CUDA graph
+    {
+      const int upd0 = tune_[TU_UPDATE];
+      float best = 0.f;
+      int bo = -1, bu = upd0;
+      for (int o = 0; o < SCHED_N && rc == SGN_OK; o++) {
+        if (o == SCHED_FUSED && !fused_ok()) continue;
+        const int nu = o == SCHED_FUSED ? TU_OPTS : 1;
+        for (int u = 0; u < nu && rc == SGN_OK; u++) {
+          tune_[TU_SCHED] = o;
+          tune_[TU_UPDATE] = o == SCHED_FUSED ? u : upd0;
+          set_geometry();
+          cudaGraph_t gr = nullptr;
+          cudaGraphExec_t gx = nullptr;
+          if (cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = SGN_ECUDA; break; }
+          if (o == SCHED_FUSED) launch_fused(cap_, c);
+          else { launch_phase1(cap_, c); launch_phase2(cap_, c); }
+          if (cudaStreamEndCapture(cap_, &gr) != cudaSuccess) { rc = SGN_ECUDA; break; }
+          cudaError_t e = cudaGraphInstantiate(&gx, gr, 0);
+          cudaGraphDestroy(gr);
+          if (e != cudaSuccess) { rc = SGN_ECUDA; break; }
+          float t = 0.f;
+          rc = time_it([&]() { cudaGraphLaunch(gx, st_); }, &t);
+          cudaGraphExecDestroy(gx);
+          if (rc) break;
+          float& slot = ms_sched_[o];
+          if (u == 0 || t < slot) slot = t;
+          if (bo < 0 || t < best) { best = t; bo = o; bu = tune_[TU_UPDATE]; }
+        }
+        if (ms && rc == SGN_OK) ms[TU_SCHED * TU_OPTS + o] = ms_sched_[o];
+      }
+      tune_[TU_SCHED] = bo < 0 ? SCHED_SERIAL : bo;
+      tune_[TU_UPDATE] = bo == SCHED_FUSED ? bu : upd0;
+      set_geometry();
     }
     if (rc) tune_[TU_SCHED] = 0;
     if (e0) cudaEventDestroy(e0);

@@ -96,16 +96,24 @@ def test_autotune_report(S):
     s.set_state(q)
     ch, ms = s.autotune(reps=5)
     assert len(ch) == S.TUNE_N
-    assert all(0 <= c < S.TUNE_OPTS for c in ch[:-1]) and ch[-1] in (0, 1)
-    # every kernel option timed; the schedule slot has two options
+    assert all(0 <= c < S.TUNE_OPTS for c in ch[:-1]) and ch[-1] in (0, 1, 2)
+    # every kernel option timed; the schedule slot has three options (the
+    # one-pass kernel is built for the mixed path of uniform grids)
     assert (ms[:-1] > 0).all()
-    assert (ms[-1, :2] > 0).all() and ms[-1, 2] == -1
-    # the kept option is the fastest measured
+    assert (ms[-1] > 0).all()
+    # the kept schedule is the fastest whole step measured
+    assert ms[-1, ch[-1]] == ms[-1].min()
+    # the kept option is the fastest measured (with the one-pass schedule the
+    # update slot selects that kernel's rows per block instead)
     for k in range(S.TUNE_N - 1):
+        if ch[-1] == 2 and k == 6:
+            continue
         assert ms[k, ch[k]] == ms[k].min()
     tun = s.tuning()
     assert [tun[n][0] for n in S.TUNE_SLOTS] == ch
     assert tun["face_x"][1][0] * tun["face_x"][1][1] in (128, 256, 512)
+    if ch[-1] == 2:
+        assert tun["update"][1][0] == 128 and tun["update"][1][1] in (64, 128, 256)
     assert tun["schedule"][1] == (0, 0)
     s.step(3)
     assert s.status()[0] == 0
