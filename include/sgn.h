@@ -275,6 +275,14 @@ void sgn_destroy(sgn_solver* s);
  * Errors: EINVAL, ECUDA. */
 int sgn_math_check(const double* x_dev, int n, double* err_dev);
 
+/* Diagnostic: the FP32 reciprocal and square root of the mixed path (the
+ * hardware approximations refined by one Newton-Raphson step) against CUDA's
+ * correctly rounded FP32 division and square root.  x_dev: n positive floats
+ * in device memory, x and 1/x normal (the approximations flush subnormals); err_dev: 2n doubles in device memory receiving the
+ * errors in FP32 units in the last place.  Synchronises the device.
+ * Errors: EINVAL, ECUDA. */
+int sgn_math_check_f32(const float* x_dev, int n, double* err_dev);
+
 /* Total mass without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory where they
  * need the mass (a host that hands the library a fixed memory pool and forbids

@@ -26,7 +26,29 @@ __global__ void k_math_check(const double* x, int n, double* err) {
   err[2 * i + 1] = uq > 0 ? fabs(q1 - q0) / uq : 0.0;
 }
 
+// The same for the FP32 reciprocal and square root of the mixed path, in units
+// in the last place of the FP32 IEEE result (correctly rounded division and sqrtf).
+__global__ void k_math_check_f32(const float* x, int n, double* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v = x[i];
+  float r0 = __fdiv_rn(1.0f, v), r1 = sgn::rcp(v);
+  float q0 = __fsqrt_rn(v), q1 = sgn::sqrt_nr(v);
+  float ur = fabsf(__int_as_float(__float_as_int(r0) + 1) - r0);
+  float uq = fabsf(__int_as_float(__float_as_int(q0) + 1) - q0);
+  err[2 * i] = ur > 0 ? fabs((double)r1 - (double)r0) / ur : 0.0;
+  err[2 * i + 1] = uq > 0 ? fabs((double)q1 - (double)q0) / uq : 0.0;
+}
+
 extern "C" {
+
+int sgn_math_check_f32(const float* x_dev, int n, double* err_dev) {
+  if (!x_dev || !err_dev || n < 0) return SGN_EINVAL;
+  if (n == 0) return SGN_OK;
+  k_math_check_f32<<<(n + 255) / 256, 256>>>(x_dev, n, err_dev);
+  if (cudaGetLastError() != cudaSuccess) return SGN_ECUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? SGN_OK : SGN_ECUDA;
+}
 
 int sgn_math_check(const double* x_dev, int n, double* err_dev) {
   if (!x_dev || !err_dev || n < 0) return SGN_EINVAL;

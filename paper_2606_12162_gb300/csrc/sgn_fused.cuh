@@ -268,21 +268,21 @@ template <int MODEL, typename Real> struct FusedSmem {
   Real uy[NV][FUSED_NT];                  // sum of the y fluctuations entering each cell
   Real gx[2][NV][FUSED_NT];               // slot 0: total x mass flux, 1..: L + T of each x face (by row parity)
   Real th[2][FUSED_NT];                   // positivity factors (by row parity)
+  int tile;                               // tile taken by the block
 };
 
+// One tile: the strip `sx` of FUSED_OUT output columns by the chunk `sy` of H
+// output rows, marched by the block.
 template <int MODEL, typename Real>
-__global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Real> d, int cur, int H) {
+__device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, Real>& sm, int cur, int H, int sx,
+                                           int sy, Real& courmax, Real& spmax) {
   typedef MT<MODEL> M;
   constexpr int NV = M::NV;
-  typedef FusedSmem<MODEL, Real> SM;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  SM& sm = *reinterpret_cast<SM*>(smraw);
-
   const int t = threadIdx.x;
   const int nx = d.nx, ny = d.ny, nxp = d.nxp, nyp = d.nyp;
-  const int a0 = NG + blockIdx.x * FUSED_OUT;       // first output column of the strip
+  const int a0 = NG + sx * FUSED_OUT;               // first output column of the strip
   const int I = a0 - 3 + t;                         // this thread's column
-  const int b0 = NG + blockIdx.y * H;               // first output row of the chunk
+  const int b0 = NG + sy * H;                       // first output row of the chunk
   const int b1 = min(b0 + H, NG + ny);              // one past the last output row
   const int rs = b0 - 3;                            // first row of the march
   const int re = b1 + 2;                            // last row of the march
@@ -337,7 +337,6 @@ __global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Rea
   rp.wet = false;
   fxE.un = fxE.ut = fxE.w = fxE.sg = fxE.pb = fxE.K = fxE.gh = fxE.C = Real(0);
 
-  Real courmax = Real(0), spmax = Real(0);
   // outputs of this thread: strip columns, inside the grid
   const bool outcol = t >= 3 && t < 3 + FUSED_OUT && I < NG + nx;
 
@@ -611,8 +610,37 @@ __global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Rea
     rp = rc;
   }
   cp_async_wait<0>();
+}
+
+// The one-pass step.  A persistent grid (as many blocks as stay resident) takes
+// tiles in row-chunk-major order from a device counter, so that the blocks in
+// flight work on neighbouring strips of the same rows (their halo columns meet
+// in L2) and wet and dry tiles, whose costs differ, balance over the SMs.  The
+// last block to finish clears the counters for the next launch.
+template <int MODEL, typename Real>
+__global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Real> d, int cur, int H, int nsx,
+                                                                        int ntiles) {
+  typedef FusedSmem<MODEL, Real> SM;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SM& sm = *reinterpret_cast<SM*>(smraw);
+  Real courmax = Real(0), spmax = Real(0);
+  for (;;) {
+    if (threadIdx.x == 0) sm.tile = (int)atomicAdd(&d.tiles[0], 1u);
+    __syncthreads();
+    const int tile = sm.tile;
+    __syncthreads();
+    if (tile >= ntiles) break;
+    fused_tile<MODEL, Real>(d, sm, cur, H, tile % nsx, tile / nsx, courmax, spmax);
+  }
   warp_max_to(d.cmax, courmax);
   warp_max_to(d.smax, spmax);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&d.tiles[1], 1u) == gridDim.x - 1) {
+      d.tiles[0] = 0u;
+      d.tiles[1] = 0u;
+    }
+  }
 }
 
 }  // namespace sgn

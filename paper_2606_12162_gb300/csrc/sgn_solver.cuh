@@ -259,14 +259,20 @@ class Solver : public SolverBase {
     d_.inv_dx_r = (Real)d_.inv_dx;
     d_.inv_dy_r = (Real)d_.inv_dy;
     d_.status = si; d_.gn = (int*)(si + 1);
+    d_.tiles = si + 4;   // two words, zeroed below and by the last block of every one-pass launch
     // launch geometry
     gPad_ = dim3((d_.nxp + 31) / 32, (d_.nyp + 7) / 8);
     gInt_ = dim3((g.nx + 31) / 32, (g.ny + 7) / 8);
     set_geometry();
     SGN_CK(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
-    if constexpr (kFusedBuilt)
-      SGN_CK(cudaFuncSetAttribute(k_step_fused<MODEL, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sizeof(FusedSmem<MODEL, Real>)));
+    if constexpr (kFusedBuilt) {
+      const int smb = (int)sizeof(FusedSmem<MODEL, Real>);
+      SGN_CK(cudaFuncSetAttribute(k_step_fused<MODEL, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+      int per_sm = 0, nsm = 0;
+      SGN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<MODEL, Real>, FUSED_NT, smb));
+      SGN_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      fused_resident_ = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
+    }
     for (int k = 0; k < 4; k++) SGN_CK(cudaEventCreateWithFlags(&fork_[k], cudaEventDisableTiming));
     save_ = dnew<unsigned long long>(4);
     if (!save_) return SGN_ENOMEM;
@@ -372,11 +378,14 @@ class Solver : public SolverBase {
   // kFusedRows[option of the update slot] rows, one block each.
   static constexpr bool kFusedBuilt = sizeof(Real) == 4;
   bool fused_ok() const { return kFusedBuilt && !d_.kind; }
+  int fused_resident_ = 0;   // blocks of the one-pass kernel resident on the device
   void launch_fused(cudaStream_t s, int c) {
     if constexpr (kFusedBuilt) {
       const int H = kFusedRows[tune_[TU_UPDATE]];
-      const dim3 g((d_.nx + FUSED_OUT - 1) / FUSED_OUT, (d_.ny + H - 1) / H);
-      k_step_fused<MODEL, Real><<<g, FUSED_NT, sizeof(FusedSmem<MODEL, Real>), s>>>(d_, c, H);
+      const int nsx = (d_.nx + FUSED_OUT - 1) / FUSED_OUT, nsy = (d_.ny + H - 1) / H;
+      const int ntiles = nsx * nsy;
+      const int nb = ntiles < fused_resident_ ? ntiles : fused_resident_;
+      k_step_fused<MODEL, Real><<<nb, FUSED_NT, sizeof(FusedSmem<MODEL, Real>), s>>>(d_, c, H, nsx, ntiles);
     }
   }
 

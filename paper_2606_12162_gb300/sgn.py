@@ -89,6 +89,7 @@ SIGNATURES = [
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("sgn_destroy", None, [ctypes.c_void_p]),
     ("sgn_math_check", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("sgn_math_check_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("sgn_mass_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
 ]

@@ -292,6 +292,25 @@ def test_fp64_reciprocal_and_sqrt_against_ieee(sgn):
     assert e[:, 0].max() <= 2.0 and e[:, 1].max() <= 2.0, e.max(axis=0)
 
 
+def test_fp32_reciprocal_and_sqrt_against_ieee(sgn):
+    """The mixed path's FP32 reciprocal and square root (hardware approximation
+    plus one Newton-Raphson step) stay within 2 ulp of CUDA's correctly rounded
+    FP32 division and sqrt wherever x and 1/x are normal floats (the kernels
+    never meet subnormal depths, speeds or sums; the approximations flush them
+    to zero)."""
+    import ctypes
+    import torch
+    rng = np.random.default_rng(1)
+    x = np.concatenate([10.0 ** rng.uniform(-36, 36, 40000), rng.uniform(0.5, 2.0, 40000),
+                        np.array([1.0, 2.0, 3.0, 1e-37, 8e37, 7.0 / 3.0])]).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    err = torch.empty(2 * len(x), dtype=torch.float64, device="cuda")
+    rc = sgn.load().sgn_math_check_f32(ctypes.c_void_p(xd.data_ptr()), len(x), ctypes.c_void_p(err.data_ptr()))
+    assert rc == 0
+    e = err.cpu().numpy().reshape(-1, 2)
+    assert e[:, 0].max() <= 2.0 and e[:, 1].max() <= 2.0, e.max(axis=0)
+
+
 def _arrival_times(rec, frac=0.01):
     """First time at which |eta| reaches frac of the gauge's maximum |eta|."""
     t = rec[:, 0, 0]
