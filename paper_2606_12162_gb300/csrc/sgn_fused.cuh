@@ -35,7 +35,14 @@
 
 namespace sgn {
 
-constexpr int FUSED_NT = 128;          // threads (columns) per block
+#ifndef SGN_FUSED_NT
+#define SGN_FUSED_NT 128
+#endif
+#ifndef SGN_FUSED_UNROLL
+#define SGN_FUSED_UNROLL 1
+#endif
+constexpr int FUSED_NT = SGN_FUSED_NT;  // threads (columns) per block
+constexpr int FUSED_UNROLL = SGN_FUSED_UNROLL;   // rows per unrolled march iteration
 #ifndef SGN_FUSED_MINB
 #define SGN_FUSED_MINB 2                // resident blocks per SM the register bound aims at
 #endif
@@ -271,19 +278,45 @@ template <int MODEL, typename Real> struct FusedSmem {
   int tile;                               // tile taken by the block
 };
 
-// One tile: the strip `sx` of FUSED_OUT output columns by the chunk `sy` of H
-// output rows, marched by the block.
+// Tiles of the one-pass kernel: strips of FUSED_OUT output columns by chunks of
+// rows.  The rows are cut into three bands -- chunks of H1 rows up to R1, of H2
+// up to R2, of H3 to the top -- and the tiles are numbered band by band, strip
+// fastest: blocks take tiles in that order, so the last tiles handed out are
+// the shortest and the blocks finish close together, while most rows pay the
+// small march start-up of the long chunks.
+struct FusedPlan {
+  int nsx;              // strips
+  int H1, R1, H2, R2, H3;
+  int n1, n2, ntiles;   // tiles in band 1, in band 2, in all
+};
+
+inline FusedPlan fused_plan(int nx, int ny, int H) {
+  FusedPlan p;
+  p.nsx = (nx + FUSED_OUT - 1) / FUSED_OUT;
+  p.H1 = H;
+  p.H2 = H / 2 > 16 ? H / 2 : 16;
+  p.H3 = H / 4 > 16 ? H / 4 : 16;
+  p.R1 = (ny - ny / 4) / p.H1 * p.H1;                       // about 3/4 of the rows in long chunks
+  p.R2 = p.R1 + (ny - p.R1) / 2 / p.H2 * p.H2;              // half of the rest in half chunks
+  p.n1 = p.nsx * (p.R1 / p.H1);
+  p.n2 = p.nsx * ((p.R2 - p.R1) / p.H2);
+  p.ntiles = p.n1 + p.n2 + p.nsx * ((ny - p.R2 + p.H3 - 1) / p.H3);
+  return p;
+}
+
+// One tile: the strip `sx` by the output rows [r0, r0 + nr) (interior row
+// indices), marched by the block.
 template <int MODEL, typename Real>
-__device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, Real>& sm, int cur, int H, int sx,
-                                           int sy, Real& courmax, Real& spmax) {
+__device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, Real>& sm, int cur, int sx, int r0,
+                                           int nr, Real& courmax, Real& spmax) {
   typedef MT<MODEL> M;
   constexpr int NV = M::NV;
   const int t = threadIdx.x;
   const int nx = d.nx, ny = d.ny, nxp = d.nxp, nyp = d.nyp;
   const int a0 = NG + sx * FUSED_OUT;               // first output column of the strip
   const int I = a0 - 3 + t;                         // this thread's column
-  const int b0 = NG + sy * H;                       // first output row of the chunk
-  const int b1 = min(b0 + H, NG + ny);              // one past the last output row
+  const int b0 = NG + r0;                           // first output row of the chunk
+  const int b1 = min(b0 + nr, NG + ny);             // one past the last output row
   const int rs = b0 - 3;                            // first row of the march
   const int re = b1 + 2;                            // last row of the march
   const bool colok = I >= 0 && I < nxp;
@@ -341,6 +374,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
   const bool outcol = t >= 3 && t < 3 + FUSED_OUT && I < NG + nx;
 
   stage(rs);
+#pragma unroll FUSED_UNROLL
   for (int r = rs; r <= re; r++) {
     const int par = r & 1;
     stage(r + 1);
@@ -618,8 +652,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
 // in L2) and wet and dry tiles, whose costs differ, balance over the SMs.  The
 // last block to finish clears the counters for the next launch.
 template <int MODEL, typename Real>
-__global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Real> d, int cur, int H, int nsx,
-                                                                        int ntiles) {
+__global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Real> d, int cur, FusedPlan p) {
   typedef FusedSmem<MODEL, Real> SM;
   extern __shared__ __align__(16) unsigned char smraw[];
   SM& sm = *reinterpret_cast<SM*>(smraw);
@@ -629,8 +662,17 @@ __global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Rea
     __syncthreads();
     const int tile = sm.tile;
     __syncthreads();
-    if (tile >= ntiles) break;
-    fused_tile<MODEL, Real>(d, sm, cur, H, tile % nsx, tile / nsx, courmax, spmax);
+    if (tile >= p.ntiles) break;
+    int r0, nr, u = tile;
+    if (u < p.n1) {
+      r0 = u / p.nsx * p.H1; nr = p.H1;
+    } else if ((u -= p.n1) < p.n2) {
+      r0 = p.R1 + u / p.nsx * p.H2; nr = p.H2;
+    } else {
+      u -= p.n2;
+      r0 = p.R2 + u / p.nsx * p.H3; nr = p.H3;
+    }
+    fused_tile<MODEL, Real>(d, sm, cur, tile % p.nsx, r0, nr, courmax, spmax);
   }
   warp_max_to(d.cmax, courmax);
   warp_max_to(d.smax, spmax);

@@ -381,11 +381,9 @@ class Solver : public SolverBase {
   int fused_resident_ = 0;   // blocks of the one-pass kernel resident on the device
   void launch_fused(cudaStream_t s, int c) {
     if constexpr (kFusedBuilt) {
-      const int H = kFusedRows[tune_[TU_UPDATE]];
-      const int nsx = (d_.nx + FUSED_OUT - 1) / FUSED_OUT, nsy = (d_.ny + H - 1) / H;
-      const int ntiles = nsx * nsy;
-      const int nb = ntiles < fused_resident_ ? ntiles : fused_resident_;
-      k_step_fused<MODEL, Real><<<nb, FUSED_NT, sizeof(FusedSmem<MODEL, Real>), s>>>(d_, c, H, nsx, ntiles);
+      const FusedPlan p = fused_plan(d_.nx, d_.ny, kFusedRows[tune_[TU_UPDATE]]);
+      const int nb = p.ntiles < fused_resident_ ? p.ntiles : fused_resident_;
+      k_step_fused<MODEL, Real><<<nb, FUSED_NT, sizeof(FusedSmem<MODEL, Real>), s>>>(d_, c, p);
     }
   }
 
