@@ -33,6 +33,10 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP32 CUDA-core peak: 152 SMs x 128 FFMA/clk/SM x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction/clk x 32
+# threads x 2.07 GHz, in thread instructions per second (the bound of a kernel
+# whose time goes to issuing FP32/integer/select work, not to HBM)
+ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
 
 # Counters per cell-update of each kernel, keyed by (model, precision, kernel,
 # block shape) -- the shape the launch used, since the halo work of a face
@@ -45,8 +49,20 @@ FLOPS_PER_CELL = {
     ("hsgn", "fp64", "k_face_y", "16x16"): 320.1, ("hsgn", "fp64", "k_theta", "32x8"): 29.4,
     ("hsgn", "fp64", "k_update", "32x8"): 217.4,
 }
+# Issue slots per cell-update (ncu smsp__inst_executed x 32: thread instructions
+# issued, predicated-off lanes included) of the one-pass kernel, HSGN mixed,
+# 2048^2 (profiles/k_step_fused_2048_counters.md); the block key is 128 columns
+# x the rows of its long chunks:
+INSTR_PER_CELL = {
+    ("hsgn", "mixed", "k_step_fused", "128x128"): 2129.5,
+    ("hsgn", "mixed", "k_step_fused", "128x64"): 2231.8,
+    ("hsgn", "mixed", "k_step_fused", "128x256"): 2078.1,
+}
 # DRAM bytes (read + write):
 TRAFFIC_PER_CELL = {
+    ("hsgn", "mixed", "k_step_fused", "128x128"): 67.1,
+    ("hsgn", "mixed", "k_step_fused", "128x64"): 68.0,
+    ("hsgn", "mixed", "k_step_fused", "128x256"): 66.1,
     **{("hsgn", "mixed", "k_prep", sh): 58 for sh in ("32x8", "32x4", "64x4")},
     ("hsgn", "mixed", "k_face_x", "128x2"): 128, ("hsgn", "mixed", "k_face_x", "256x1"): 128,
     ("hsgn", "mixed", "k_face_x", "64x4"): 129,
@@ -76,6 +92,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the refined-hierarchy (config 4) line")
     ap.add_argument("--batched-n0", type=int, default=1024, help="level-0 size of the config-4 hierarchy")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector (config 5) line")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 8192^2 (config 3) mixed and FP64 rows")
+    ap.add_argument("--config3-steps", type=int, default=30, help="timed mixed steps of the config-3 row")
     ap.add_argument("--tuning", default=None,
                     help="force a launch tuning (8 comma-separated option indices of sgn_set_tuning) instead of "
                          "autotuning")
@@ -221,11 +239,14 @@ def kernel_bytes(name, nv, s):
         return 4 * s + 8
     if name == "k_update":      # W, 4 face vectors, transverse fluxes, theta, b, c2 -> q
         return (nv + 4 * (nv - 1) + 2 * nv + 2 + nv) * s + 8
+    if name == "k_step_fused":  # q, b, c2, psi_x, psi_y -> q
+        return (2 * nv + 4) * s
     return 0
 
 
 SLOT = {"k_prep": "prep", "k_face_x": "face_x", "k_face_y": "face_y", "k_trans_x": "trans_x",
-        "k_trans_y": "trans_y", "k_theta": "theta", "k_update": "update"}
+        "k_trans_y": "trans_y", "k_theta": "theta", "k_update": "update",
+        "k_step_fused": "update"}       # the one-pass kernel's block: 128 columns x rows per chunk
 
 
 def roofline(model, prec, kt, cells, b_alg, nv, esize, hbm, hbm_src, shapes=None):
@@ -243,10 +264,29 @@ def roofline(model, prec, kt, cells, b_alg, nv, esize, hbm, hbm_src, shapes=None
     out = {"kernel": name, "block": shape, "launch_ms": per * 1e3, "share": kms / sum(v[0] for v in kt.values()),
            "traffic": tr * cells if tr else None}
     fl = FLOPS_PER_CELL.get((model, prec, name, shape))
-    if prec == "fp64" and fl:
+    ins = INSTR_PER_CELL.get((model, prec, name, shape))
+    if ins:
+        # one-pass kernel: HBM roof (the step's algorithmic bytes) and issue roof
+        # (ncu-counted thread instructions per cell); the lower one bounds it
+        ach_b = b_alg * cells / per / 1e9
+        ach_i = ins * cells / per / 1e12
+        roof_b = hbm * 1e9 / b_alg
+        roof_i = ISSUE_PEAK_TINST * 1e12 / ins
+        alu = {"achieved": ach_i, "peak": ISSUE_PEAK_TINST, "unit": "Tinst/s", "frac": ach_i / ISSUE_PEAK_TINST,
+               "inst_per_cell": ins, "roof_cell_updates_per_s": roof_i,
+               "peak_source": "152 SMs x 4 schedulers x 32 threads x 2.07 GHz"}
+        hb = {"achieved": ach_b, "peak": hbm, "unit": "GB/s", "frac": ach_b / hbm, "bytes_per_cell": b_alg,
+              "roof_cell_updates_per_s": roof_b, "peak_source": hbm_src}
+        main = alu if roof_i < roof_b else hb
+        out.update({"bound": "alu" if roof_i < roof_b else "hbm", "achieved": main["achieved"],
+                    "peak": main["peak"], "unit": main["unit"], "frac": main["frac"],
+                    "hbm_frac": hb["frac"], "alu_frac": alu["frac"], "hbm": hb, "alu": alu})
+    elif prec == "fp64" and fl:
         ach = fl * cells / per / 1e12
+        ach_b = b_alg * cells / per / 1e9
         out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "flops_per_cell": fl,
+                    "frac": ach / FP64_PEAK_TFLOPS, "flops_per_cell": fl, "alu_frac": ach / FP64_PEAK_TFLOPS,
+                    "hbm_frac": ach_b / hbm,
                     "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (1.19 measured)"})
     else:
         ach = b_alg * cells / per / 1e9
@@ -319,12 +359,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_path(S, c, args, precision, profile):
-    """Warm-up, then exactly K steps between CUDA events on the solver stream."""
+def time_path(S, c, args, precision, prof_steps=None):
+    """Warm-up, then exactly K steps between CUDA events on the solver stream:
+    the product path (each step one CUDA-graph replay of the tuned schedule,
+    no per-kernel events).  A separate pass of prof_steps steps afterwards
+    (outside the timed region) launches the same kernels without the graph,
+    each between two CUDA events, for the per-kernel times."""
     import torch
     s = S.Solver(c["b"], precision=precision, **cfg_kwargs(c))
     s.set_state(c["q"])
-    s.add_gauges(c["gauges"], args.steps + args.warmup + 8)
+    kp = args.steps if prof_steps is None else prof_steps
+    s.add_gauges(c["gauges"], args.steps + args.warmup + kp + 8)
     s.step(args.warmup)
     tuning = None
     if args.tuning:
@@ -337,8 +382,6 @@ def time_path(S, c, args, precision, profile):
         s.autotune(reps=10)
         tuning = {"s": time.perf_counter() - t0,
                   "shapes": {k: ("%dx%d" % v[1]) if k != "schedule" else v[0] for k, v in s.tuning().items()}}
-    if profile:
-        s.set_profiling(True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -347,10 +390,16 @@ def time_path(S, c, args, precision, profile):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    kt = s.kernel_times() if profile else {}
     f, dt, cr = s.status()
+    kt = {}
+    if kp > 0:
+        s.set_profiling(True)
+        s.step(kp)
+        kt = s.kernel_times()
+        s.set_profiling(False)
     s.tuning_report = tuning
     s.shapes = {k: "%dx%d" % v[1] for k, v in s.tuning().items() if k != "schedule"}
+    s.schedule = s.tuning()["schedule"][0]
     return s, ms, kt, f
 
 
@@ -510,6 +559,50 @@ def results_table(args):
     return rows
 
 
+def time_config3(S, args, hbm, hbm_src, ws):
+    """Configuration 3 (8192^2, dx = 500 m, fractal bathymetry, 2 m uplift, HSGN):
+    mixed (autotuned; one graph replay per step) and FP64 cell-updates/s between
+    CUDA events with the clocks sampled over each timed region, then a profiled
+    pass of each for the dominant kernel's roofline (outside the timed regions)."""
+    import copy
+    import torch
+    from paper_2606_12162_gb300 import workloads as W
+    t0 = time.perf_counter()
+    c = W.config3(model=W.HSGN)
+    c["gauges"] = c.get("gauges")
+    if c["gauges"] is None:
+        c["gauges"] = np.zeros((0, 2))
+    setup = time.perf_counter() - t0
+    cells = c["b"].size
+    nv = S.NVAR[W.HSGN]
+    out = {"workload": "config3: 8192x8192, dx=500 m, fractal bathymetry (|k|^-2, ~20 % land, to -6000 m), "
+                       "2 m Gaussian uplift (r=30 km), HSGN alpha=3, 64 gauges", "setup_s": setup}
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    for prec, key, steps in ((1, "mixed", args.config3_steps), (0, "fp64", max(3, args.config3_steps // 6))):
+        a2 = copy.copy(args)
+        a2.steps, a2.warmup = steps, 3
+        if prec == 0:
+            a2.no_tune, a2.tuning = True, None
+        clk = ClockSampler(local)
+        clk.start()
+        s, ms, kt, f = time_path(S, c, a2, prec, prof_steps=min(steps, 5))
+        clocks = clk.stop()
+        ms = reduce_max(ms, ws)
+        b_alg = nv * 2 * (4 if prec else 8) + (4 if prec else 8) + 1
+        v = cells * steps * ws / (ms / 1e3)
+        out[key] = {"value": v, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps, "status_flags": f,
+                    "dtype": "f32+f64" if prec else "f64", "clocks": clocks, "tuning": s.tuning_report,
+                    "hbm_fraction_step": v / ws * b_alg / (hbm * 1e9),
+                    "roofline": roofline("hsgn", key, kt, cells, b_alg, nv, 4 if prec else 8, hbm, hbm_src,
+                                         s.shapes),
+                    "kernels_ms_per_step": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items() if v2[1]},
+                    "gpu_launches": s.launches_per_step() * steps}
+        del s
+        torch.cuda.empty_cache()
+    del c
+    return out
+
+
 def time_batched(args):
     """Config 4 (three levels, ratio 4, ~2000 patches along a wave front), mixed
     precision: W level-0 steps of warm-up, then K level-0 steps (each with all
@@ -662,7 +755,7 @@ def main():
     clk = ClockSampler(local)
     barrier(ws)
     clk.start()
-    s, ms, kt, flags = time_path(S, c, args, prec, profile=True)
+    s, ms, kt, flags = time_path(S, c, args, prec, prof_steps=min(args.steps, 20))
     clocks = clk.stop()
     ms = reduce_max(ms, ws)
     value = cells * args.steps * ws / (ms / 1e3)
@@ -704,7 +797,7 @@ def main():
         # default launch shapes (the FP64 counters' shapes); tuning gains nothing
         # measurable on this FP64-pipe-bound path (33.0 vs 33.1 ms per step)
         a2.no_tune, a2.tuning = True, None
-        s2, ms2, kt2, f2 = time_path(S, c, a2, 0, profile=True)
+        s2, ms2, kt2, f2 = time_path(S, c, a2, 0, prof_steps=a2.steps)
         ms2 = reduce_max(ms2, ws)
         v2 = cells * a2.steps * ws / (ms2 / 1e3)
         extra = {"value": v2, "unit": UNIT, "steps": a2.steps, "ms_per_step": ms2 / a2.steps,
@@ -715,6 +808,10 @@ def main():
                  "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in kt2.items() if v[1]}}
         del s2
         extra["mixed_vs_fp64"] = mixed_error(S, c, args.fp64_check_steps)
+
+    config3 = None
+    if not args.no_config3:
+        config3 = time_config3(S, args, hbm, hbm_src, ws)
 
     batched = None
     if not args.no_batched:
@@ -762,6 +859,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64": extra,
+            "config3": config3,
             "batched": batched,
             "learned": learned,
         }

@@ -272,6 +272,7 @@ class Solver : public SolverBase {
       SGN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<MODEL, Real>, FUSED_NT, smb));
       SGN_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       fused_resident_ = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
+      tune_[TU_SCHED] = SCHED_FUSED;   // the default schedule of the mixed path on a single grid
     }
     for (int k = 0; k < 4; k++) SGN_CK(cudaEventCreateWithFlags(&fork_[k], cudaEventDisableTiming));
     save_ = dnew<unsigned long long>(4);

@@ -73,7 +73,7 @@ def test_fused_equals_kernel_sequence(S, model, nx, ny, bc, wetdry, steps):
     b, q = W.random_small_case(model, nx, ny, seed=3 * nx + ny + model, dx=0.05, wetdry=wetdry, amp=0.15)
     cfg = dict(model=model, dx=0.05, dy=0.04, bc=bc, h_star=0.6)
     g = np.array([[0.05 * nx * 0.3, 0.04 * ny * 0.6], [0.05 * nx * 0.9, 0.04 * ny * 0.1]])
-    ref = run(S, b, q, steps, gauges=g, **cfg)
+    ref = run(S, b, q, steps, choice=[0] * 8, gauges=g, **cfg)   # the kernel sequence
     assert ref[0].status()[0] == 0
     for opt in range(3):
         got = run(S, b, q, steps, choice=fused_choice(opt), gauges=g, **cfg)
@@ -92,7 +92,7 @@ def test_fused_limiters_and_lie(S):
     b, q = W.random_small_case(2, 140, 150, seed=5, dx=0.05, wetdry=True, amp=0.2)
     for limiter, strang in ((0, 1), (2, 1), (1, 0)):
         cfg = dict(model=2, dx=0.05, bc=(0, 1, 0, 1), h_star=0.6, limiter=limiter, strang=strang)
-        ref = run(S, b, q, 10, **cfg)
+        ref = run(S, b, q, 10, choice=[0] * 8, **cfg)
         got = run(S, b, q, 10, choice=fused_choice(1), **cfg)
         assert close(got[1], ref[1]) and abs(got[2] - ref[2]) <= 1e-6 * ref[2]
 
@@ -116,6 +116,13 @@ def test_fused_against_oracle(S, oracle_mod):
     assert abs(tg - to) <= 1e-5 * to
 
 
+def test_fused_is_the_mixed_default(S):
+    b, q = W.random_small_case(2, 140, 90, seed=2, dx=0.05, wetdry=True, amp=0.15)
+    s = S.Solver(b, model=2, dx=0.05, precision=1, h_star=0.6)
+    assert s.tuning()["schedule"][0] == FUSED
+    assert s.launches_per_step() == 2
+
+
 def test_fused_rejected_where_not_built(S):
     b, q = W.random_small_case(2, 40, 30, seed=1, dx=0.05, wetdry=False)
     s = S.Solver(b, model=2, dx=0.05, precision=0)   # FP64: the one-pass kernel is FP32 only
@@ -129,7 +136,7 @@ def test_fused_autotune_keeps_run(S):
     (the one-pass schedule agrees with the others to FP32 rounding)."""
     b, q = W.random_small_case(2, 260, 200, seed=44, dx=0.05, wetdry=True, amp=0.15)
     cfg = dict(model=2, dx=0.05, bc=(1, 1, 1, 1), h_star=0.6)
-    ref = run(S, b, q, 12, **cfg)
+    ref = run(S, b, q, 12, choice=[0] * 8, **cfg)
     s = S.Solver(b, precision=1, **cfg)
     s.set_state(q)
     s.step(4)

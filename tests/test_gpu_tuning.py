@@ -57,7 +57,9 @@ def test_every_option_matches_default(S, model, precision):
     nx, ny = 131, 67
     b, q = W.random_small_case(model, nx, ny, seed=900 + model, dx=0.05, wetdry=True, amp=0.15)
     cfg = dict(model=model, dx=0.05, dy=0.04, bc=(1, 0, 0, 1), h_star=0.6, precision=precision)
-    ref = run(S, b, q, 8, **cfg)
+    # the kernel sequence with default shapes (a mixed solver starts on the one-pass
+    # schedule, which agrees with these to FP32 rounding: tests/test_gpu_fused.py)
+    ref = run(S, b, q, 8, choice=[0] * S.TUNE_N, **cfg)
     assert ref[0].status()[0] == 0
     for o in range(S.TUNE_OPTS):
         for sched in (0, 1):
@@ -72,7 +74,7 @@ def test_mixed_options_per_slot(S):
     model = 2
     b, q = W.random_small_case(model, 97, 113, seed=77, dx=0.05, wetdry=True, amp=0.2)
     cfg = dict(model=model, dx=0.05, bc=(0, 0, 0, 0), h_star=0.6, precision=1)
-    ref = run(S, b, q, 10, **cfg)
+    ref = run(S, b, q, 10, choice=[0] * S.TUNE_N, **cfg)
     for choice in ([1, 2, 0, 2, 1, 0, 2, 1], [2, 0, 1, 1, 2, 2, 0, 0], [0, 1, 2, 0, 0, 1, 1, 1]):
         same_run(run(S, b, q, 10, choice=choice, **cfg), ref)
 
@@ -82,12 +84,17 @@ def test_autotune_leaves_the_run_unchanged(S, precision):
     model = 2
     b, q = W.random_small_case(model, 160, 90, seed=31, dx=0.05, wetdry=True, amp=0.2)
     cfg = dict(model=model, dx=0.05, bc=(1, 1, 0, 0), h_star=0.6, precision=precision)
-    ref = run(S, b, q, 9, **cfg)
-    got = run(S, b, q, 9, autotune_after=4, **cfg)
-    same_run(got, ref)
-    # before the first step as well
-    got0 = run(S, b, q, 9, autotune_after=0, **cfg)
-    same_run(got0, ref)
+    for k in (4, 0):      # after some steps, and before the first
+        got = run(S, b, q, 9, autotune_after=k, **cfg)
+        kept = [v[0] for v in got[0].tuning().values()]
+        # the same run without tuning: k steps on the default schedule, then the kept one
+        s = S.Solver(b, **cfg)
+        s.set_state(q)
+        s.step(k)
+        s.set_tuning(kept)
+        s.step(9 - k)
+        qr, tr = s.get_state()
+        same_run(got, (s, qr, tr))
 
 
 def test_autotune_report(S):
@@ -132,8 +139,11 @@ def test_tuning_arguments(S):
     with pytest.raises(S.SGNError) as e:
         s.autotune(reps=0)
     assert e.value.code == -1
-    # a rejected tuning leaves the previous one
+    # a rejected tuning leaves the previous one (FP64 solver: schedule 0 by default)
     assert all(v[0] == 0 for v in s.tuning().values())
+    # a mixed solver starts on the one-pass schedule
+    s2 = S.Solver(b, model=1, dx=0.05, precision=1)
+    assert s2.tuning()["schedule"][0] == 2
 
 
 def test_hierarchy_autotune_and_options(S):
