@@ -254,3 +254,44 @@ def test_sdirk_is_stability_function_and_second_order(oracle_mod, model):
         errs.append(np.abs(y - scipy.linalg.expm(tau * M) @ y0).max())
     r1, r2 = math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
     assert 2.7 < r1 < 3.3 and 2.7 < r2 < 3.3  # local error O(tau^3) = global order 2
+
+
+@pytest.mark.parametrize("model", [1, 2])
+def test_uniform_current_is_steady_for_any_relaxation_field(oracle_mod, model):
+    """Reading G24 (the relaxation term h c^2 d_x u with c^2 outside the
+    derivative, as the relaxed divergence constraint d_t p + u d_x p = -c^2 d_x u
+    + ... gives it) against the flux form d_x[h u (p + c^2)]: they differ by
+    h u d_x c^2, which vanishes only for constant c^2.  A uniform current over a
+    flat bottom (h, u uniform, w = sigma = p = p_b = 0) is the SGN solution with
+    zero non-hydrostatic pressure, and with c^2 outside the derivative it is an
+    exact steady solution of the relaxed systems for every c^2(x); the flux form
+    would drive p by u h d_x c^2.  Face level: a face between two copies of the
+    same current with different c^2 carries no fluctuation (the flux form gives
+    delta_hp = h u (c2R - c2L)).  Whole step: with a smooth, strongly varying
+    c^2 field (sgn_set_c2's setting, no SWE transition) the oracle keeps the
+    current to round-off over 40 steps."""
+    O = oracle_mod
+    h, u, v = 1.3, 0.7, -0.2
+    b = -h
+    nv = O.NVAR[model]
+    q = np.zeros(nv)
+    q[0], q[1], q[2] = h + b, h * u, h * v
+    cfg = _cfg(O, model)
+    r = O.face(cfg, q, q, b, b, 20.0, 80.0)
+    assert np.abs(r["delta"]).max() == 0.0
+    assert np.abs(r["Am"]).max() == 0.0 and np.abs(r["Ap"]).max() == 0.0
+    # the flux form's fluctuation of hp here would be h u (c2R - c2L) = 54.6: far from 0
+    # whole step over a varying c^2 field, periodic in x and y
+    nx, ny, dx = 96, 8, 0.05
+    x = (np.arange(nx) + 0.5) * dx
+    c2 = np.tile(60.0 + 45.0 * np.sin(2 * np.pi * x / (nx * dx)), (ny, 1))
+    bb = np.full((ny, nx), b)
+    qs = np.zeros((nv, ny, nx))
+    qs[0], qs[1], qs[2] = h + b, h * u, h * v
+    o = O.Oracle(bb, dx=dx, model=model, bc=(2, 2, 2, 2), h_star=0.0)
+    o.set_c2(c2)
+    o.set_state(qs)
+    assert o.step(40) == 0
+    qe, _ = o.get_state()
+    assert np.abs(qe - qs).max() <= 1e-13 * (1 + np.abs(qs).max())
+    assert np.abs(qe[3:]).max() <= 1e-13

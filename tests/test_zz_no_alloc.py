@@ -6,9 +6,12 @@ further allocations, or a latency-critical loop where cudaMalloc / cudaFree
 (which can synchronise the device) are not acceptable.  Its partial sums live in
 a fixed array compiled into the library, shared by every call.  This test calls
 it through the C ABI twice in a row, on different grids and states, and checks
-each result against sgn_mass (the solver's own reduction in allocated scratch).
+each result against an independent host sum of max(0, eta - b) dx dy over the
+same arrays (math.fsum: correctly rounded) and against sgn_mass (the solver's
+own reduction in allocated scratch).
 """
 import ctypes
+import math
 
 import numpy as np
 import pytest
@@ -55,6 +58,10 @@ def test_mass_static_matches_sgn_mass_on_two_calls(S):
         ref = s.mass()
         got = out.item()
         assert abs(got - ref) <= REL_TOL * ref, (got, ref)
+        # independent of the library: the same eta and b summed on the host
+        eta = qd[0].cpu().numpy()
+        host = math.fsum(np.maximum(eta - b, 0.0).ravel().tolist()) * 0.05 * 0.05
+        assert abs(got - host) <= REL_TOL * host, (got, host)
 
 
 def test_mass_static_rejects_bad_arguments(S):
