@@ -40,11 +40,19 @@ def conv3x3(x, w, b):
     return y
 
 
-def forward(params, layers, x):
+def _id(a):
+    return a
+
+
+def forward(params, layers, x, quant=None):
+    """Activations of every layer.  quant (None: exact) rounds each
+    convolution's input operand first, e.g. bf16_round for a network whose
+    convolutions multiply BF16 operands."""
+    q = quant or _id
     acts = [np.asarray(x, dtype=np.float64)]
     L = len(layers)
     for l, (w, b) in enumerate(unpack(params, layers)):
-        z = conv3x3(acts[-1], w, b)
+        z = conv3x3(q(acts[-1]), w, b)
         acts.append(np.maximum(z, 0.0) if l < L - 1 else z)
     return acts
 
@@ -69,10 +77,18 @@ def unshuffle(fine, r, nout):
     return y
 
 
-def loss_and_grad(params, layers, x, target, r, nout, fw):
+def loss_and_grad(params, layers, x, target, r, nout, fw, quant=None):
     """Weighted MSE of the shuffled output against target and its gradient with
-    respect to the packed parameters."""
-    acts = forward(params, layers, x)
+    respect to the packed parameters.  quant (None: exact) rounds the operands
+    of every convolution -- forward inputs, and in the backward pass the
+    incoming gradient and the layer input of each weight-gradient product and
+    the incoming gradient of each input-gradient convolution -- the way a
+    network on BF16 tensor-core products does.  The bias gradient of the last
+    layer sums the unrounded dL/dy; those of the hidden layers sum their
+    gradient as stored, i.e. rounded (a network that keeps hidden activations
+    and their gradients in BF16)."""
+    q = quant or _id
+    acts = forward(params, layers, x, quant)
     wb = unpack(params, layers)
     y = acts[-1]
     fine = shuffle(y, r, nout)
@@ -86,14 +102,15 @@ def loss_and_grad(params, layers, x, target, r, nout, fw):
         w, b = wb[l]
         a = acts[l]
         _, H, W = a.shape
-        ap = np.pad(a, ((0, 0), (1, 1), (1, 1)))
+        ap = np.pad(q(a), ((0, 0), (1, 1), (1, 1)))
+        gq = q(g)
         gw = np.zeros_like(w)
         for ky in range(3):
             for kx in range(3):
-                gw[:, :, ky, kx] = np.einsum("ohw,chw->oc", g, ap[:, ky:ky + H, kx:kx + W])
-        grads[l] = (gw, g.sum(axis=(1, 2)))
+                gw[:, :, ky, kx] = np.einsum("ohw,chw->oc", gq, ap[:, ky:ky + H, kx:kx + W])
+        grads[l] = (gw, (g if l == len(layers) - 1 else gq).sum(axis=(1, 2)))
         if l > 0:
-            gp = np.pad(g, ((0, 0), (1, 1), (1, 1)))
+            gp = np.pad(gq, ((0, 0), (1, 1), (1, 1)))
             ga = np.zeros_like(a)
             for ky in range(3):
                 for kx in range(3):

@@ -2,10 +2,11 @@
 // with hand-written forward, backward (data and weight gradients), loss and Adam
 // kernels, plus the data kernels that turn solver states into inputs/targets.
 //
-// Convolutions run on the CUDA cores: weights stored as BF16 and expanded to
-// FP32 in shared memory, FP32 activations and accumulation.  The weight
-// gradients are formed per 16x16 pixel tile and summed over tiles in a fixed
-// order, so training is run-to-run reproducible.
+// Convolutions run on the tensor cores (mma.sync, BF16 operands: the BF16
+// weights and the activations or gradients rounded to BF16 as they are staged;
+// FP32 accumulation; FP32 activations, biases, losses and master weights).  The
+// weight gradients are summed per block of a fixed persistent grid, then over
+// blocks in a fixed order, so training is run-to-run reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -18,152 +19,346 @@
 
 namespace {
 
-constexpr int TS = 16;        // output tile edge
-constexpr int CIC = 8;        // input channels per shared-memory chunk
-constexpr int COT = 16;       // output channels per block (forward)
+// ---------------------------------------------------------------------------
+// 3x3 convolutions as implicit GEMMs on the tensor cores: mma.sync m16n8k16
+// with BF16 operands and FP32 accumulation.
+//
+// Layouts.  The network input x and its output y are FP32 channel-major planes
+// [c][y][x] (the data kernels' layout).  Everything in between -- hidden
+// activations and the gradients flowing back through them -- is stored as BF16
+// pixel-major rows [y][x][c] of CS = channels rounded up to 16 (the padding
+// stays zero): the values the tensor cores multiply are BF16 anyway, so this
+// changes no result and halves the bytes.  A block stages a tile of the input
+// in shared memory as [pixel][channel] rows of CS + 8 BF16 (the 8 extra keep
+// the 16-byte ldmatrix rows of consecutive pixels on different banks), so any
+// 3x3 tap offset is a whole-row shift and every operand row stays 16-byte
+// aligned: pixel-major inputs arrive by 16-byte cp.async (zero-filled outside
+// the image), double-buffered across tiles; channel-major FP32 inputs are read,
+// rounded and stored by the threads.
+constexpr int CT_H = 8;              // output tile rows (one per warp)
+constexpr int CT_W = 32;             // output tile columns (two 16-pixel MMA rows)
+constexpr int CT_PIX = (CT_H + 2) * (CT_W + 2);   // staged input pixels (tile + halo)
 
-// Forward 3x3 convolution, padding 1: out[co][y][x] = bias[co] +
-// sum_ci sum_k w[co][ci][k] in[ci][y+ky-1][x+kx-1], then optional ReLU and an
-// optional multiplication by the mask (mask_src > 0) used by the backward pass.
-// WT: weight element type (BF16 network weights or FP32 flipped weights).
-// A block of TS x TS threads computes a TS x (PX TS) output tile: each thread
-// PX pixels TS columns apart, so every weight vector read from shared memory
-// feeds PX pixels' FMAs.
-constexpr int PX = 4;          // output pixels per thread (along x)
-constexpr int TSX = PX * TS;   // output tile width of the convolution
-template <typename WT>
-__global__ void __launch_bounds__(TS * TS) k_conv3x3(const float* __restrict__ in, int cin, int H, int W,
-                                                     const WT* __restrict__ w, const float* __restrict__ bias,
-                                                     int cout, int relu, const float* __restrict__ mask_src,
-                                                     float* __restrict__ out) {
-  __shared__ float sin_[CIC][TS + 2][TSX + 2];
-  __shared__ __align__(16) float sw[CIC][9][COT];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TS + tx;
-  const int x0 = blockIdx.x * TSX + tx, y = blockIdx.y * TS + ty;
-  const int co0 = blockIdx.z * COT;
-  float acc[PX][COT];
-#pragma unroll
-  for (int h = 0; h < PX; h++)
-#pragma unroll
-    for (int c = 0; c < COT; c++) acc[h][c] = 0.f;
-  for (int c0 = 0; c0 < cin; c0 += CIC) {
-    __syncthreads();
-    for (int t = tid; t < CIC * (TS + 2) * (TSX + 2); t += TS * TS) {
-      int ci = t / ((TS + 2) * (TSX + 2)), r = t - ci * (TS + 2) * (TSX + 2);
-      int yy = r / (TSX + 2), xx = r - yy * (TSX + 2);
-      int gy = blockIdx.y * TS + yy - 1, gx = blockIdx.x * TSX + xx - 1;
-      float v = 0.f;
-      if (c0 + ci < cin && gy >= 0 && gy < H && gx >= 0 && gx < W) v = in[((size_t)(c0 + ci) * H + gy) * W + gx];
-      sin_[ci][yy][xx] = v;
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+// D = A B + D for one 16x8x16 tile (A row-major 16x16, B column-major 16x8).
+__device__ __forceinline__ void mma_bf16(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};\n"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<unsigned*>(&v);
+}
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros
+// without reading (the address passed is then any valid one).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Stage rows [y0, y0 + ROWS) x columns [x0, x0 + COLS) of an input into
+// shared-memory rows of PS BF16 (channels 0..CP-1), zero outside the image.
+// Pixel-major BF16 source (nhwc, CP channels per pixel): 16-byte cp.async
+// copies, committed as one group by the caller.  Channel-major FP32 source
+// (planes [0, c)): loads go out in batches of SB element pairs per thread
+// before any of them is stored, so a thread waits for one memory latency per
+// batch, not per pair.
+template <int CP, int PS, int ROWS, int COLS, int SB = 8>
+__device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int nhwc, int c, int H, int W, int y0,
+                                           int x0, __nv_bfloat16* dst) {
+  if (nhwc) {
+    const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(srcv);
+    constexpr int CH = CP / 8, N = ROWS * COLS * CH;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      const int ch = t % CH, pix = t / CH;
+      const int yy = pix / COLS, xx = pix - yy * COLS;
+      const int gy = y0 + yy, gx = x0 + xx;
+      const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+      const __nv_bfloat16* s = in ? src + ((size_t)gy * W + gx) * CP + 8 * ch : src;
+      cp_async16(dst + (size_t)pix * PS + 8 * ch, s, in ? 16 : 0);
     }
-    for (int t = tid; t < CIC * 9 * COT; t += TS * TS) {
-      int ci = t / (9 * COT), r = t - ci * 9 * COT;
-      int k = r / COT, co = r - k * COT;
-      float v = 0.f;
-      if (c0 + ci < cin && co0 + co < cout) v = (float)w[((size_t)(co0 + co) * cin + (c0 + ci)) * 9 + k];
-      sw[ci][k][co] = v;
+    return;
+  }
+  const float* src = static_cast<const float*>(srcv);
+  constexpr int N = ROWS * COLS * (CP / 2);
+  const size_t pl = (size_t)H * W;
+  for (int base = threadIdx.x; base < N; base += SB * blockDim.x) {
+    float v0[SB], v1[SB];
+#pragma unroll
+    for (int j = 0; j < SB; j++) {
+      const int t = base + j * blockDim.x;
+      const int xx = t % COLS, r = t / COLS;
+      const int yy = r % ROWS, ch = 2 * (r / ROWS);
+      const int gy = y0 + yy, gx = x0 + xx;
+      v0[j] = v1[j] = 0.f;
+      if (t < N && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        const size_t o = (size_t)gy * W + gx;
+        if (ch < c) v0[j] = __ldg(src + (size_t)ch * pl + o);
+        if (ch + 1 < c) v1[j] = __ldg(src + (size_t)(ch + 1) * pl + o);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SB; j++) {
+      const int t = base + j * blockDim.x;
+      if (t >= N) break;
+      const int xx = t % COLS, r = t / COLS;
+      const int yy = r % ROWS, ch = 2 * (r / ROWS);
+      *reinterpret_cast<unsigned*>(dst + (size_t)(yy * COLS + xx) * PS + ch) = pack_bf16(v0[j], v1[j]);
+    }
+  }
+}
+
+// Convolution with padding 1: out[o][y][x] = bias[o] + sum_c sum_k
+// B(o, c, k) in[c][y + ky - 1][x + kx - 1] (k = 3 ky + kx), then optional ReLU
+// and an optional mask (out = 0 where mask <= 0; mask pixel-major BF16 like a
+// pixel-major output).  in: pixel-major BF16 with CP channels (in_nhwc) or
+// channel-major FP32 with cin planes; out: pixel-major BF16 with NT*8 channels,
+// padding included (out_nhwc), or channel-major FP32 with cout planes.  The
+// weights B are read from the network's BF16 tensor w: transpose = 0,
+// B(o, c, k) = w[o][c][k] (the layer itself, w of shape cout x cin x 9);
+// transpose = 1, B(o, c, k) = w[c][o][8 - k] (w of shape cin x cout x 9: the
+// transposed, flipped kernel that maps dL/d(out) of that layer to dL/d(in)).
+// Persistent blocks of 8 warps take tiles of 8 x 32 output pixels; warp w
+// computes row w of the tile: 2 m-tiles of 16 pixels x NT n-tiles of 8 output
+// channels, K = 9 taps x CP channels in steps of 16.
+template <int CP, int NT>
+__global__ void __launch_bounds__(256, 2) k_conv_mma(const void* __restrict__ in, int in_nhwc, int cin, int H, int W,
+                                                     const __nv_bfloat16* __restrict__ w, int transpose,
+                                                     const float* __restrict__ bias, int cout, int relu,
+                                                     const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
+                                                     int out_nhwc, int ntx, int ntiles) {
+  constexpr int PS = CP + 8;
+  constexpr int NO = NT * 8;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(sm_raw);    // [9][NO][PS]
+  __nv_bfloat16* sA0 = sB + 9 * NO * PS;                            // [2][CT_PIX][PS]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // weights, once per block: sB[k][o][c] = B(o, c, k), zero-padded
+  for (int t = threadIdx.x; t < 9 * NO * CP; t += blockDim.x) {
+    const int c = t % CP, r = t / CP, o = r % NO, k = r / NO;
+    float v = 0.f;
+    if (o < cout && c < cin)
+      v = (float)(transpose ? w[((size_t)c * cout + o) * 9 + (8 - k)] : w[((size_t)o * cin + c) * 9 + k]);
+    sB[(size_t)(k * NO + o) * PS + c] = __float2bfloat16_rn(v);
+  }
+  const int g = lane >> 2, tq = lane & 3;
+  auto tile_origin = [&](int tile, int& ty0, int& tx0) {
+    ty0 = (tile / ntx) * CT_H;
+    tx0 = (tile % ntx) * CT_W;
+  };
+  if (in_nhwc && (int)blockIdx.x < ntiles) {
+    int ty0, tx0;
+    tile_origin(blockIdx.x, ty0, tx0);
+    stage_tile<CP, PS, CT_H + 2, CT_W + 2>(in, 1, cin, H, W, ty0 - 1, tx0 - 1, sA0);
+    cp_commit();
+  }
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    int ty0, tx0;
+    tile_origin(tile, ty0, tx0);
+    __nv_bfloat16* sA = sA0 + (size_t)(in_nhwc ? (it & 1) : 0) * CT_PIX * PS;
+    if (in_nhwc) {
+      // prefetch the next tile into the other buffer (read by every thread in
+      // the previous iteration, which ended with a barrier), then wait for this one
+      const int nt = tile + gridDim.x;
+      if (nt < ntiles) {
+        int ny0, nx0;
+        tile_origin(nt, ny0, nx0);
+        stage_tile<CP, PS, CT_H + 2, CT_W + 2>(in, 1, cin, H, W, ny0 - 1, nx0 - 1,
+                                               sA0 + (size_t)((it + 1) & 1) * CT_PIX * PS);
+      }
+      cp_commit();
+      cp_wait<1>();
+    } else {
+      stage_tile<CP, PS, CT_H + 2, CT_W + 2>(in, 0, cin, H, W, ty0 - 1, tx0 - 1, sA);
     }
     __syncthreads();
-    for (int ci = 0; ci < CIC; ci++) {
+    float acc[2][NT][4];
 #pragma unroll
-      for (int k = 0; k < 9; k++) {
-        float v[PX];
+    for (int m = 0; m < 2; m++)
 #pragma unroll
-        for (int h = 0; h < PX; h++) v[h] = sin_[ci][ty + k / 3][tx + h * TS + k % 3];
+      for (int n = 0; n < NT; n++)
 #pragma unroll
-        for (int c = 0; c < COT; c += 4) {
-          const float4 w4 = *reinterpret_cast<const float4*>(&sw[ci][k][c]);
+        for (int e = 0; e < 4; e++) acc[m][n][e] = 0.f;
 #pragma unroll
-          for (int h = 0; h < PX; h++) {
-            acc[h][c] += w4.x * v[h];
-            acc[h][c + 1] += w4.y * v[h];
-            acc[h][c + 2] += w4.z * v[h];
-            acc[h][c + 3] += w4.w * v[h];
+    for (int k = 0; k < 9; k++) {
+      const int ky = k / 3, kx = k % 3;
+#pragma unroll
+      for (int c0 = 0; c0 < CP; c0 += 16) {
+        unsigned a[2][4];
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+          // A rows: pixels x = 16 m + (lane & 15) of output row `warp`, shifted by the tap
+          const int px = 16 * m + (lane & 15) + kx, py = warp + ky;
+          const __nv_bfloat16* pa = sA + (size_t)(py * (CT_W + 2) + px) * PS + c0 + 8 * (lane >> 4);
+          ldsm_x4(smem_u32(pa), a[m][0], a[m][1], a[m][2], a[m][3]);
+        }
+#pragma unroll
+        for (int n = 0; n < NT; n += 2) {
+          unsigned b0, b1, b2, b3;
+          const int o = 8 * (n + (lane >> 4)) + (lane & 7);
+          const __nv_bfloat16* pb = sB + (size_t)(k * NO + o) * PS + c0 + 8 * ((lane >> 3) & 1);
+          ldsm_x4(smem_u32(pb), b0, b1, b2, b3);
+#pragma unroll
+          for (int m = 0; m < 2; m++) {
+            mma_bf16(acc[m][n], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
+            mma_bf16(acc[m][n + 1], a[m][0], a[m][1], a[m][2], a[m][3], b2, b3);
           }
         }
       }
     }
-  }
-  if (y >= H) return;
+    // epilogue: rows g and g + 8 of each m-tile are pixels, columns 2 tq, 2 tq + 1 channels
+    const int y = ty0 + warp;
+    if (y < H) {
 #pragma unroll
-  for (int h = 0; h < PX; h++) {
-    const int x = x0 + h * TS;
-    if (x >= W) break;
+      for (int m = 0; m < 2; m++)
 #pragma unroll
-    for (int c = 0; c < COT; c++) {
-      int co = co0 + c;
-      if (co >= cout) break;
-      float v = acc[h][c] + (bias ? bias[co] : 0.f);
-      if (relu) v = v > 0.f ? v : 0.f;
-      size_t o = ((size_t)co * H + y) * W + x;
-      if (mask_src && !(mask_src[o] > 0.f)) v = 0.f;
-      out[o] = v;
+        for (int h = 0; h < 2; h++) {
+          const int x = tx0 + 16 * m + g + 8 * h;
+          if (x >= W) continue;
+          const size_t pix = (size_t)y * W + x;
+#pragma unroll
+          for (int n = 0; n < NT; n++) {
+            const int o = 8 * n + 2 * tq;
+            float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
+            if (bias) {
+              if (o < cout) v0 += bias[o];
+              if (o + 1 < cout) v1 += bias[o + 1];
+            }
+            if (relu) { v0 = v0 > 0.f ? v0 : 0.f; v1 = v1 > 0.f ? v1 : 0.f; }
+            if (mask) {
+              const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + pix * NO + o);
+              if (!(__low2float(mk) > 0.f)) v0 = 0.f;
+              if (!(__high2float(mk) > 0.f)) v1 = 0.f;
+            }
+            if (out_nhwc) {
+              *reinterpret_cast<unsigned*>(static_cast<__nv_bfloat16*>(out) + pix * NO + o) = pack_bf16(v0, v1);
+            } else {
+              float* of = static_cast<float*>(out);
+              if (o < cout) of[(size_t)o * H * W + pix] = v0;
+              if (o + 1 < cout) of[(size_t)(o + 1) * H * W + pix] = v1;
+            }
+          }
+        }
     }
+    __syncthreads();   // this tile's buffer and the other one may be overwritten next
   }
+  cp_wait<0>();
 }
 
-// Weights for the input gradient: wf[ci][co][k] = w[co][ci][8 - k] (the
-// transposed, flipped kernel), so that dL/din = conv3x3(dL/dout, wf).
-__global__ void k_flip(const __nv_bfloat16* __restrict__ w, int cin, int cout, float* __restrict__ wf) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cin * cout * 9) return;
-  int ci = t / (cout * 9), r = t - ci * cout * 9;
-  int co = r / 9, k = r - co * 9;
-  wf[t] = (float)w[((size_t)co * cin + ci) * 9 + (8 - k)];
-}
-
-// Weight and bias gradient partials of one 16x16 pixel tile:
-// part[tile][co][ci][k] = sum_p g[co][p] in[ci][p + off_k], part[tile][bias co] =
-// sum_p g[co][p].  Summed over tiles by k_sum_tiles.
-__global__ void __launch_bounds__(TS * TS) k_wgrad(const float* __restrict__ in, int cin, int H, int W,
-                                                   const float* __restrict__ g, int cout, float* __restrict__ part,
-                                                   long nper) {
-  __shared__ float sg[COT][TS][TS];
-  __shared__ float sin_[CIC][TS + 2][TS + 2];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TS + tx;
-  const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-  float* pt = part + (size_t)tile * nper;
-  for (int co0 = 0; co0 < cout; co0 += COT) {
+// Weight gradient partials: part[blk][o][c][k] = sum over the block's pixels
+// p of g[o][p] in[c][p + off_k] (BF16 operands, FP32 accumulation), as a GEMM
+// with M = output channels, N = input channels and K = pixels.  Both tiles are
+// staged as [pixel][channel] rows (either source layout); ldmatrix.trans turns
+// them into the A (o x p) and B (p x c) fragments.  Nine warps, one per tap;
+// each block sums the tiles blockIdx.x, blockIdx.x + gridDim.x, ... in that
+// order, and the partials of the blocks are summed in block order by
+// k_sum_tiles, so the result does not depend on the schedule.
+template <int OP, int CP>
+__global__ void __launch_bounds__(288, 2) k_wgrad_mma(const void* __restrict__ in, int in_nhwc, int cin, int H,
+                                                      int W, const void* __restrict__ g, int g_nhwc, int cout,
+                                                      float* __restrict__ part, int ntx, int ntiles) {
+  constexpr int PSI = CP + 8, PSG = OP + 8;
+  constexpr int MT = OP / 16, NT = CP / 8;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __nv_bfloat16* sI = reinterpret_cast<__nv_bfloat16*>(sm_raw);     // [CT_PIX][PSI]
+  __nv_bfloat16* sG = sI + CT_PIX * PSI;                             // [CT_H * CT_W][PSG]
+  const int lane = threadIdx.x & 31, tap = threadIdx.x >> 5;
+  const int ky = tap / 3, kx = tap % 3;
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int m = 0; m < MT; m++)
+#pragma unroll
+    for (int n = 0; n < NT; n++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) acc[m][n][e] = 0.f;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int ty0 = (tile / ntx) * CT_H, tx0 = (tile % ntx) * CT_W;
     __syncthreads();
-    for (int t = tid; t < COT * TS * TS; t += TS * TS) {
-      int c = t / (TS * TS), r = t - c * TS * TS;
-      int yy = r / TS, xx = r - yy * TS;
-      int gy = blockIdx.y * TS + yy, gx = blockIdx.x * TS + xx;
-      float v = 0.f;
-      if (co0 + c < cout && gy < H && gx < W) v = g[((size_t)(co0 + c) * H + gy) * W + gx];
-      sg[c][yy][xx] = v;
-    }
+    stage_tile<CP, PSI, CT_H + 2, CT_W + 2, 4>(in, in_nhwc, cin, H, W, ty0 - 1, tx0 - 1, sI);
+    stage_tile<OP, PSG, CT_H, CT_W, 4>(g, g_nhwc, cout, H, W, ty0, tx0, sG);
+    cp_commit();
+    cp_wait<0>();
     __syncthreads();
-    // bias partials
-    if (tid < COT && co0 + tid < cout) {
-      float s = 0.f;
-      for (int p = 0; p < TS * TS; p++) s += sg[tid][p / TS][p % TS];
-      pt[(size_t)cout * cin * 9 + co0 + tid] = s;
-    }
-    for (int c0 = 0; c0 < cin; c0 += CIC) {
-      __syncthreads();
-      for (int t = tid; t < CIC * (TS + 2) * (TS + 2); t += TS * TS) {
-        int ci = t / ((TS + 2) * (TS + 2)), r = t - ci * (TS + 2) * (TS + 2);
-        int yy = r / (TS + 2), xx = r - yy * (TS + 2);
-        int gy = blockIdx.y * TS + yy - 1, gx = blockIdx.x * TS + xx - 1;
-        float v = 0.f;
-        if (c0 + ci < cin && gy >= 0 && gy < H && gx >= 0 && gx < W) v = in[((size_t)(c0 + ci) * H + gy) * W + gx];
-        sin_[ci][yy][xx] = v;
+    // K: the 256 pixels of the tile, 16 at a time (half a tile row)
+    for (int ks = 0; ks < CT_H * CT_W / 16; ks++) {
+      const int row = ks >> 1, xs = 16 * (ks & 1);
+      unsigned a[MT][4];
+#pragma unroll
+      for (int m = 0; m < MT; m++) {
+        // A (o x p) from sG rows = pixels: matrices (o 0-7, p 0-7), (o 8-15, p 0-7), (o 0-7, p 8-15), (o 8-15, p 8-15)
+        const int p = xs + (lane & 7) + 8 * (lane >> 4);
+        const __nv_bfloat16* pa = sG + (size_t)(row * CT_W + p) * PSG + 16 * m + 8 * ((lane >> 3) & 1);
+        ldsm_x4_t(smem_u32(pa), a[m][0], a[m][1], a[m][2], a[m][3]);
       }
-      __syncthreads();
-      for (int t = tid; t < COT * CIC * 9; t += TS * TS) {
-        int c = t / (CIC * 9), r = t - c * CIC * 9;
-        int ci = r / 9, k = r - ci * 9;
-        if (co0 + c >= cout || c0 + ci >= cin) continue;
-        const int ky = k / 3, kx = k % 3;
-        float s = 0.f;
-        for (int yy = 0; yy < TS; yy++)
-#pragma unroll 4
-          for (int xx = 0; xx < TS; xx++) s += sg[c][yy][xx] * sin_[ci][yy + ky][xx + kx];
-        pt[((size_t)(co0 + c) * cin + (c0 + ci)) * 9 + k] = s;
+#pragma unroll
+      for (int n = 0; n < NT; n += 2) {
+        // B (p x c) from sI rows = pixels shifted by the tap: (p 0-7, c), (p 8-15, c), (p 0-7, c+8), (p 8-15, c+8)
+        const int p = xs + (lane & 7) + 8 * ((lane >> 3) & 1) + kx;
+        const __nv_bfloat16* pb = sI + (size_t)((row + ky) * (CT_W + 2) + p) * PSI + 8 * (n + (lane >> 4));
+        unsigned b0, b1, b2, b3;
+        ldsm_x4_t(smem_u32(pb), b0, b1, b2, b3);
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+          mma_bf16(acc[m][n], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
+          mma_bf16(acc[m][n + 1], a[m][0], a[m][1], a[m][2], a[m][3], b2, b3);
+        }
       }
     }
   }
+  // this block's partial: rows g, g + 8 are output channels, columns 2 tq, 2 tq + 1 input channels
+  const long nper = (long)cout * cin * 9;
+  float* pt = part + (size_t)blockIdx.x * nper;
+  const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int m = 0; m < MT; m++)
+#pragma unroll
+    for (int n = 0; n < NT; n++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int o = 16 * m + gq + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+        if (o < cout && c < cin) pt[((size_t)o * cin + c) * 9 + tap] = acc[m][n][e];
+      }
+}
+
+// Bias gradient partials: part[chunk][o] = sum of g[o][p] over the pixels of
+// chunk blockIdx.x (BG_CHUNKS contiguous ranges), in FP32, in a fixed order
+// (strided per-thread sums, then a fixed tree); k_sum_tiles adds the chunks.
+// g: channel-major FP32 (cs = 0) or pixel-major BF16 with cs channels per pixel.
+constexpr int BG_CHUNKS = 64;
+__global__ void k_bias_grad(const void* __restrict__ gv, int cs, long hw, int cout, float* __restrict__ part) {
+  __shared__ float red[256];
+  const long p0 = hw * blockIdx.x / BG_CHUNKS, p1 = hw * (blockIdx.x + 1) / BG_CHUNKS;
+  const int o = blockIdx.y;
+  float s = 0.f;
+  if (cs == 0) {
+    const float* go = static_cast<const float*>(gv) + (size_t)o * hw;
+    for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += go[p];
+  } else {
+    const __nv_bfloat16* gb = static_cast<const __nv_bfloat16*>(gv);
+    for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += (float)gb[(size_t)p * cs + o];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)blockIdx.x * cout + blockIdx.y] = red[0];
 }
 
 // grad[i] = sum over tiles of part[tile][i], in tile order.
@@ -180,10 +375,10 @@ __global__ void k_sum_tiles(const float* __restrict__ part, int ntiles, long n, 
 // of field f.  Per-block loss partials are summed in order by k_sum_loss.
 __global__ void k_loss(const float* __restrict__ yv, const float* __restrict__ tgt, int H, int W, int r, int nout,
                        const float* __restrict__ fw, float* __restrict__ gy, double* __restrict__ lpart) {
-  __shared__ double red[256];
+  __shared__ float red[256];
   long n = (long)nout * r * r * H * W;
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  double l = 0.0;
+  float l = 0.f;
   if (i < n) {
     int c = (int)(i / ((long)H * W));
     long p = i - (long)c * H * W;
@@ -193,7 +388,7 @@ __global__ void k_loss(const float* __restrict__ yv, const float* __restrict__ t
     float d = yv[i] - tgt[((size_t)f * H * r + (size_t)(yy * r + sy)) * Wf + (xx * r + sx)];
     float inv = 1.f / (float)((long)H * W * r * r);
     gy[i] = 2.f * fw[f] * d * inv;
-    l = (double)fw[f] * (double)d * (double)d * (double)inv;
+    l = fw[f] * d * d * inv;
   }
   red[threadIdx.x] = l;
   __syncthreads();
@@ -201,14 +396,22 @@ __global__ void k_loss(const float* __restrict__ yv, const float* __restrict__ t
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) lpart[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) lpart[blockIdx.x] = (double)red[0];
 }
 
-__global__ void k_sum_loss(const double* __restrict__ lpart, int n, double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Sum of the n block partials in FP64: one block, strided per-thread sums and a
+// fixed tree (the same order every call).
+__global__ void __launch_bounds__(1024) k_sum_loss(const double* __restrict__ lpart, int n, double* __restrict__ out) {
+  __shared__ double red[1024];
   double s = 0.0;
-  for (int i = 0; i < n; i++) s += lpart[i];
-  *out = s;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += lpart[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 // Adam on the FP32 master parameters and refresh of their BF16 copy.
@@ -304,6 +507,40 @@ inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+// ---- launch helpers of the tensor-core kernels: padded channel counts are
+// template arguments (16, 32, 48 channels; 2, 4, 6 n-tiles of 8 outputs)
+typedef void (*ConvFn)(const void*, int, int, int, int, const __nv_bfloat16*, int, const float*, int, int,
+                       const __nv_bfloat16*, void*, int, int, int);
+typedef void (*WgradFn)(const void*, int, int, int, int, const void*, int, int, float*, int, int);
+static int pad16(int c) { return (c + 15) / 16 * 16; }
+static ConvFn conv_fn(int cp, int nt) {
+#define CF(C, N) if (cp == C && nt == N) return k_conv_mma<C, N>;
+  CF(16, 2) CF(16, 4) CF(16, 6) CF(32, 2) CF(32, 4) CF(32, 6) CF(48, 2) CF(48, 4) CF(48, 6)
+#undef CF
+  return nullptr;
+}
+static WgradFn wgrad_fn(int op, int cp) {
+#define WF(O, C) if (op == O && cp == C) return k_wgrad_mma<O, C>;
+  WF(16, 16) WF(16, 32) WF(16, 48) WF(32, 16) WF(32, 32) WF(32, 48) WF(48, 16) WF(48, 32) WF(48, 48)
+#undef WF
+  return nullptr;
+}
+static size_t conv_smem(int cp, int nt) { return (size_t)(9 * nt * 8 + 2 * CT_PIX) * (cp + 8) * 2; }
+static size_t wgrad_smem(int op, int cp) { return ((size_t)CT_PIX * (cp + 8) + (size_t)CT_H * CT_W * (op + 8)) * 2; }
+static int set_smem_attrs() {
+  for (int cp = 16; cp <= 48; cp += 16)
+    for (int k = 2; k <= 6; k += 2) {
+      if (cudaFuncSetAttribute(conv_fn(cp, k), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(cp, k)) !=
+          cudaSuccess)
+        return -3;
+      const int op = 8 * k;   // 16, 32, 48
+      if (cudaFuncSetAttribute(wgrad_fn(op, cp), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)wgrad_smem(op, cp)) != cudaSuccess)
+        return -3;
+    }
+  return 0;
+}
+
 struct lc_net {
   int cin, width, depth, cout;
   long max_hw;
@@ -313,12 +550,16 @@ struct lc_net {
   long np;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16* pb = nullptr;
-  std::vector<float*> act;      // act[l]: output of layer l (l = 0..depth-1)
-  float *ga = nullptr, *gb = nullptr, *wf = nullptr, *part = nullptr;
+  // act[l]: output of layer l -- pixel-major BF16 rows of pad16(co[l]) channels
+  // for the hidden layers, channel-major FP32 for the last one
+  std::vector<void*> act;
+  __nv_bfloat16* gh[2] = {nullptr, nullptr};   // pixel-major BF16 gradients of hidden outputs
+  float *ga = nullptr, *part = nullptr, *bpart = nullptr;   // ga: dL/dy, channel-major FP32
   double *lpart = nullptr, *lsum = nullptr;
   float* fw = nullptr;          // loss field weights (device copy)
   long max_layer;
   int max_tiles, max_lblocks;
+  int nsm = 1;                  // SMs of the device (persistent grids: 2 blocks per SM)
   long step = 0;
   std::vector<void*> bufs;
 };
@@ -335,6 +576,7 @@ extern "C" {
 int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned long long seed, void* cuda_stream,
               lc_net** out) {
   if (!out || cin <= 0 || width <= 0 || depth < 2 || cout <= 0 || max_hw <= 0) return -1;
+  if (cin > 48 || width > 48 || cout > 48) return -1;   // tensor-core kernels: at most 48 channels
   *out = nullptr;
   lc_net* n = new (std::nothrow) lc_net;
   if (!n) return -2;
@@ -351,22 +593,30 @@ int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned lon
   }
   n->np = off;
   long maxc = std::max(width, cout);
-  // ceil(H/16) ceil(W/16) <= HW/256 + (H + W)/16 + 1 <= HW/15 + 2 for any H, W >= 1
-  n->max_tiles = (int)((max_hw + 14) / 15 + 2);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n->nsm < 1)
+      n->nsm = 1;
+    if (set_smem_attrs()) { delete n; return -3; }
+  }
+  // weight-gradient partials: one per block of the persistent grid
+  n->max_tiles = 2 * n->nsm;
   n->max_lblocks = (int)((max_hw * cout + 255) / 256) + 1;
   n->p = (float*)dmalloc(n, n->np * 4); n->g = (float*)dmalloc(n, n->np * 4);
   n->m = (float*)dmalloc(n, n->np * 4); n->v = (float*)dmalloc(n, n->np * 4);
   n->pb = (__nv_bfloat16*)dmalloc(n, n->np * 2);
-  for (int l = 0; l < depth; l++) n->act.push_back((float*)dmalloc(n, (size_t)n->co[l] * max_hw * 4));
-  n->ga = (float*)dmalloc(n, (size_t)maxc * max_hw * 4);
-  n->gb = (float*)dmalloc(n, (size_t)maxc * max_hw * 4);
-  n->wf = (float*)dmalloc(n, (size_t)n->max_layer * 4);
+  for (int l = 0; l < depth; l++)
+    n->act.push_back(dmalloc(n, l < depth - 1 ? (size_t)pad16(n->co[l]) * max_hw * 2 : (size_t)n->co[l] * max_hw * 4));
+  n->ga = (float*)dmalloc(n, (size_t)cout * max_hw * 4);
+  for (int k = 0; k < 2; k++) n->gh[k] = (__nv_bfloat16*)dmalloc(n, (size_t)pad16(width) * max_hw * 2);
   n->part = (float*)dmalloc(n, (size_t)n->max_tiles * n->max_layer * 4);
   n->lpart = (double*)dmalloc(n, (size_t)n->max_lblocks * 8);
+  n->bpart = (float*)dmalloc(n, (size_t)BG_CHUNKS * maxc * 4);
   n->lsum = (double*)dmalloc(n, 8);
   n->fw = (float*)dmalloc(n, 8 * sizeof(float));
-  bool ok = n->p && n->g && n->m && n->v && n->pb && n->ga && n->gb && n->wf && n->part && n->lpart && n->lsum &&
-            n->fw;
+  bool ok = n->p && n->g && n->m && n->v && n->pb && n->ga && n->gh[0] && n->gh[1] && n->part && n->bpart &&
+            n->lpart && n->lsum && n->fw;
   for (auto a : n->act) ok = ok && a;
   if (!ok) { lc_destroy(n); return -2; }
   // He initialisation from a counter-based generator (splitmix64 + Box-Muller)
@@ -413,21 +663,30 @@ int lc_set_params(lc_net* n, const float* host, long count) {
   return cudaStreamSynchronize(n->st) == cudaSuccess ? 0 : -3;
 }
 
-static void conv_fwd(lc_net* n, int l, const float* in, int H, int W, float* out) {
-  dim3 grid((W + TSX - 1) / TSX, (H + TS - 1) / TS, (n->co[l] + COT - 1) / COT);
-  k_conv3x3<__nv_bfloat16><<<grid, dim3(TS, TS), 0, n->st>>>(in, n->ci[l], H, W, n->pb + n->woff[l],
-                                                               n->p + n->boff[l], n->co[l],
-                                                               l < n->depth - 1 ? 1 : 0, nullptr, out);
+// 3x3 convolution of `in` (cin planes) into `out` (cout planes) on the tensor
+// cores with the BF16 weights w (transpose: see k_conv_mma).
+static void conv(lc_net* n, const void* in, int in_nhwc, int cin, int H, int W, const __nv_bfloat16* w,
+                 int transpose, const float* bias, int cout, int relu, const __nv_bfloat16* mask, void* out,
+                 int out_nhwc) {
+  const int cp = pad16(cin), nt = (cout + 15) / 16 * 2;
+  const int ntx = (W + CT_W - 1) / CT_W, ntiles = ntx * ((H + CT_H - 1) / CT_H);
+  const int nb = std::min(ntiles, 2 * n->nsm);
+  conv_fn(cp, nt)<<<nb, 256, conv_smem(cp, nt), n->st>>>(in, in_nhwc, cin, H, W, w, transpose, bias, cout, relu,
+                                                          mask, out, out_nhwc, ntx, ntiles);
+}
+
+// Layer l forward: its input is x (channel-major FP32) for l = 0, else the
+// previous hidden output; hidden outputs are pixel-major BF16, the last
+// layer's channel-major FP32 (out).
+static void conv_fwd(lc_net* n, int l, const float* x, int H, int W, void* out) {
+  const bool last = l == n->depth - 1;
+  conv(n, l == 0 ? (const void*)x : n->act[l - 1], l == 0 ? 0 : 1, n->ci[l], H, W, n->pb + n->woff[l], 0,
+       n->p + n->boff[l], n->co[l], last ? 0 : 1, nullptr, out, last ? 0 : 1);
 }
 
 int lc_forward(lc_net* n, const float* x_dev, int H, int W, float* y_dev) {
   if (!n || !x_dev || !y_dev || H <= 0 || W <= 0 || (long)H * W > n->max_hw) return -1;
-  const float* in = x_dev;
-  for (int l = 0; l < n->depth; l++) {
-    float* o = l == n->depth - 1 ? y_dev : n->act[l];
-    conv_fwd(n, l, in, H, W, o);
-    in = o;
-  }
+  for (int l = 0; l < n->depth; l++) conv_fwd(n, l, x_dev, H, W, l == n->depth - 1 ? (void*)y_dev : n->act[l]);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -436,35 +695,39 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
   if (!n || !x_dev || !target_dev || !field_w || H <= 0 || W <= 0 || r <= 0 || nout <= 0) return -1;
   if ((long)H * W > n->max_hw || nout * r * r != n->cout || nout > 8 || lr < 0) return -1;
   // forward, keeping every layer's output
-  const float* in = x_dev;
-  for (int l = 0; l < n->depth; l++) {
-    conv_fwd(n, l, in, H, W, n->act[l]);
-    in = n->act[l];
-  }
+  for (int l = 0; l < n->depth; l++) conv_fwd(n, l, x_dev, H, W, n->act[l]);
   // loss and dL/dy
   long ny = (long)n->cout * H * W;
   int lb = (int)nblk(ny, 256);
   if (lb > n->max_lblocks) return -1;
   if (cudaMemcpyAsync(n->fw, field_w, nout * sizeof(float), cudaMemcpyHostToDevice, n->st) != cudaSuccess) return -3;
-  k_loss<<<lb, 256, 0, n->st>>>(n->act[n->depth - 1], target_dev, H, W, r, nout, n->fw, n->ga, n->lpart);
-  k_sum_loss<<<1, 32, 0, n->st>>>(n->lpart, lb, n->lsum);
+  k_loss<<<lb, 256, 0, n->st>>>(static_cast<const float*>(n->act[n->depth - 1]), target_dev, H, W, r, nout, n->fw,
+                                n->ga, n->lpart);
+  k_sum_loss<<<1, 1024, 0, n->st>>>(n->lpart, lb, n->lsum);
   // backward: g (in ga) is dL/d(pre-activation) of layer l
-  dim3 tiles((W + TS - 1) / TS, (H + TS - 1) / TS);
-  int ntiles = tiles.x * tiles.y;
-  if (ntiles > n->max_tiles) return -1;
+  const int ntx = (W + CT_W - 1) / CT_W, ntiles = ntx * ((H + CT_H - 1) / CT_H);
+  const int nbw = std::min(ntiles, n->max_tiles);
+  // g: dL/dy (channel-major FP32) for the last layer, then the pixel-major
+  // BF16 gradients of the hidden outputs, alternating between gh[0] and gh[1]
+  const void* g = n->ga;
+  int g_nhwc = 0, gk = 0;
   for (int l = n->depth - 1; l >= 0; l--) {
-    const float* lin = l == 0 ? x_dev : n->act[l - 1];
-    long nl = (long)n->ci[l] * n->co[l] * 9 + n->co[l];
-    k_wgrad<<<tiles, dim3(TS, TS), 0, n->st>>>(lin, n->ci[l], H, W, n->ga, n->co[l], n->part, nl);
-    k_sum_tiles<<<nblk(nl, 256), 256, 0, n->st>>>(n->part, ntiles, nl, n->g + n->woff[l]);
+    const void* lin = l == 0 ? (const void*)x_dev : n->act[l - 1];
+    const int a = n->ci[l], b = n->co[l];
+    const long nw = (long)a * b * 9;
+    const int op = pad16(b), cp = pad16(a);
+    wgrad_fn(op, cp)<<<nbw, 288, wgrad_smem(op, cp), n->st>>>(lin, l == 0 ? 0 : 1, a, H, W, g, g_nhwc, b, n->part,
+                                                               ntx, ntiles);
+    k_sum_tiles<<<nblk(nw, 256), 256, 0, n->st>>>(n->part, nbw, nw, n->g + n->woff[l]);
+    k_bias_grad<<<dim3(BG_CHUNKS, b), 256, 0, n->st>>>(g, g_nhwc ? op : 0, (long)H * W, b, n->bpart);
+    k_sum_tiles<<<1, 64, 0, n->st>>>(n->bpart, BG_CHUNKS, b, n->g + n->boff[l]);
     if (l > 0) {
-      int a = n->ci[l], b = n->co[l];
-      k_flip<<<nblk((long)a * b * 9, 256), 256, 0, n->st>>>(n->pb + n->woff[l], a, b, n->wf);
-      dim3 grid((W + TSX - 1) / TSX, (H + TS - 1) / TS, (a + COT - 1) / COT);
-      // dL/d(out of layer l-1), times ReLU'(out of layer l-1)
-      k_conv3x3<float><<<grid, dim3(TS, TS), 0, n->st>>>(n->ga, b, H, W, n->wf, nullptr, a, 0, n->act[l - 1],
-                                                         n->gb);
-      float* t = n->ga; n->ga = n->gb; n->gb = t;
+      // dL/d(out of layer l-1) = transposed, flipped convolution of g, times ReLU'(out of layer l-1)
+      conv(n, g, g_nhwc, b, H, W, n->pb + n->woff[l], 1, nullptr, a, 0,
+           static_cast<const __nv_bfloat16*>(n->act[l - 1]), n->gh[gk], 1);
+      g = n->gh[gk];
+      g_nhwc = 1;
+      gk ^= 1;
     }
   }
   if (cudaGetLastError() != cudaSuccess) return -3;

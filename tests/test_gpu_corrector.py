@@ -31,19 +31,51 @@ def test_gradients_match_fp64_reference(C):
     t = rng.standard_normal((3, 40, 48)).astype(np.float32)
     fw = (1.0, 0.3, 0.3)
     loss, g = net.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), 0.0, fw, want_grad=True)
-    # the kernels use BF16 weights and FP32 biases
+    # the kernels multiply BF16 weights by BF16-rounded activations and
+    # gradients on the tensor cores (FP32 accumulation, FP32 biases); the FP64
+    # reference rounds the same operands
     pr = p.astype(np.float64)
     off = 0
     for ci, co in net.layers():
         pr[off:off + ci * co * 9] = R.bf16_round(p[off:off + ci * co * 9])
         off += ci * co * 9 + co
-    lref, gref = R.loss_and_grad(pr, net.layers(), x, t, 2, 3, fw)
+    lref, gref = R.loss_and_grad(pr, net.layers(), x, t, 2, 3, fw, quant=R.bf16_round)
     assert abs(loss - lref) <= 1e-5 * lref
     assert np.abs(g - gref).max() <= 1e-4 * np.abs(gref).max()
     # forward alone
     y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
-    yref = R.forward(pr, net.layers(), x)[-1]
-    assert np.abs(y - yref).max() <= 1e-5 * np.abs(yref).max()
+    yref = R.forward(pr, net.layers(), x, quant=R.bf16_round)[-1]
+    assert np.abs(y - yref).max() <= 1e-4 * np.abs(yref).max()
+
+
+@pytest.mark.parametrize("cin,width,depth,r,nout,H,W", [(5, 32, 3, 4, 3, 37, 70), (5, 16, 2, 2, 3, 9, 33),
+                                                       (7, 48, 3, 2, 4, 16, 32)])
+def test_tensor_core_layers_match_reference(C, cin, width, depth, r, nout, H, W):
+    """The tensor-core convolutions at the channel counts of the full network
+    (5 -> 32 -> 48 with ratio 4 and 3 fields, the 48-channel gradient into 32
+    channels, 7 -> 48 -> 16) and at ragged
+    tile edges: loss and gradients within 1e-4 of the FP64 reference with the
+    same BF16 operand rounding; the same step twice gives the same bits."""
+    import torch
+    from oracle import conv_ref as R
+    rng = np.random.default_rng(cin + width + H)
+    net = C.Net(cin=cin, width=width, depth=depth, r=r, nout=nout, max_hw=H * W, seed=3)
+    p = net.params()
+    x = rng.standard_normal((cin, H, W)).astype(np.float32)
+    t = rng.standard_normal((nout, H * r, W * r)).astype(np.float32)
+    fw = tuple([1.0] + [0.5] * (nout - 1))
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    loss, g = net.train_step(xd, td, 0.0, fw, want_grad=True)
+    loss2, g2 = net.train_step(xd, td, 0.0, fw, want_grad=True)
+    assert loss == loss2 and np.array_equal(g, g2)
+    pr = p.astype(np.float64)
+    off = 0
+    for ci, co in net.layers():
+        pr[off:off + ci * co * 9] = R.bf16_round(p[off:off + ci * co * 9])
+        off += ci * co * 9 + co
+    lref, gref = R.loss_and_grad(pr, net.layers(), x, t, r, nout, fw, quant=R.bf16_round)
+    assert abs(loss - lref) <= 1e-5 * lref
+    assert np.abs(g - gref).max() <= 1e-4 * np.abs(gref).max()
 
 
 def test_data_kernels(C):
