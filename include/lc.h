@@ -12,10 +12,11 @@
  * Network: `depth` 3x3 convolutions (padding 1), `width` channels, ReLU between
  * layers, last layer r*r*nout channels (pixel-shuffled to the fine grid).
  * Weights are kept as FP32 master copies for Adam and used as BF16 in the forward
- * and backward passes; activations and accumulation are FP32.
+ * and backward passes; the convolutions are implicit GEMMs on the tensor cores
+ * (BF16 operands, FP32 accumulation).
  *
- * Layouts: activations and inputs are channel-major [C][H][W] float32 in device
- * memory (batch 1).  Parameters are packed per layer as weights [cout][cin][3][3]
+ * Layouts: the network input and output are channel-major [C][H][W] float32 in
+ * device memory (batch 1); hidden activations live inside the handle.  Parameters are packed per layer as weights [cout][cin][3][3]
  * then bias [cout].  Every entry point returns 0 or a negative SGN-style code
  * (-1 invalid argument, -2 allocation failure, -3 CUDA error) and issues its work
  * on the stream given to lc_create; entry points that return host values
@@ -32,8 +33,13 @@ extern "C" {
 typedef struct lc_net lc_net;
 
 /* Create a network with cin input channels, `width` hidden channels, `depth`
- * layers (>= 2) and cout = r*r*nout output channels; He-initialised from `seed`.
- * max_hw bounds H*W of the inputs later passed (workspace is sized for it). */
+ * layers (>= 2) and cout = r*r*nout output channels (each at most 48, the
+ * tensor-core kernels' limit; cout * max_hw below 2^31); He-initialised from
+ * `seed`.  max_hw bounds H*W of the inputs later passed (workspace is sized for
+ * it).  The convolutions multiply BF16 operands on the tensor cores with FP32
+ * accumulation: the BF16 copy of the weights, and the layer inputs and
+ * gradients rounded to BF16 (hidden activations and their gradients are kept
+ * in BF16); biases, master weights, the output and the loss are FP32. */
 int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned long long seed,
               void* cuda_stream, lc_net** out);
 void lc_destroy(lc_net* n);

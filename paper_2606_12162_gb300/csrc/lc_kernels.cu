@@ -336,29 +336,43 @@ __global__ void __launch_bounds__(288, 2) k_wgrad_mma(const void* __restrict__ i
 }
 
 // Bias gradient partials: part[chunk][o] = sum of g[o][p] over the pixels of
-// chunk blockIdx.x (BG_CHUNKS contiguous ranges), in FP32, in a fixed order
-// (strided per-thread sums, then a fixed tree); k_sum_tiles adds the chunks.
-// g: channel-major FP32 (cs = 0) or pixel-major BF16 with cs channels per pixel.
-constexpr int BG_CHUNKS = 64;
+// chunk blockIdx.x (gridDim.x contiguous ranges), in FP32, in a fixed order;
+// k_sum_tiles adds the chunks.  g: channel-major FP32 (cs = 0; one block per
+// chunk and channel, blockIdx.y = o) or pixel-major BF16 with cs channels per
+// pixel (one block per chunk for all channels: thread t reads channel t % cs of
+// every (blockDim / cs)-th pixel, so a warp reads consecutive bytes; the
+// threads of one channel are then summed in thread order).
+constexpr int BG_CHUNKS = 64, BG_CHUNKS_NHWC = 1024;
 __global__ void k_bias_grad(const void* __restrict__ gv, int cs, long hw, int cout, float* __restrict__ part) {
   __shared__ float red[256];
-  const long p0 = hw * blockIdx.x / BG_CHUNKS, p1 = hw * (blockIdx.x + 1) / BG_CHUNKS;
-  const int o = blockIdx.y;
-  float s = 0.f;
+  const long p0 = hw * blockIdx.x / gridDim.x, p1 = hw * (blockIdx.x + 1) / gridDim.x;
   if (cs == 0) {
+    const int o = blockIdx.y;
     const float* go = static_cast<const float*>(gv) + (size_t)o * hw;
+    float s = 0.f;
     for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += go[p];
-  } else {
-    const __nv_bfloat16* gb = static_cast<const __nv_bfloat16*>(gv);
-    for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += (float)gb[(size_t)p * cs + o];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * cout + o] = red[0];
+    return;
   }
+  const __nv_bfloat16* gb = static_cast<const __nv_bfloat16*>(gv);
+  const int ppi = blockDim.x / cs;                     // pixels per pass
+  const int o = threadIdx.x % cs, pk = threadIdx.x / cs;
+  float s = 0.f;
+  if (pk < ppi)
+    for (long p = p0 + pk; p < p1; p += ppi) s += (float)gb[(size_t)p * cs + o];
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x < cout) {
+    float t = 0.f;
+    for (int k = 0; k < ppi; k++) t += red[k * cs + threadIdx.x];
+    part[(size_t)blockIdx.x * cout + threadIdx.x] = t;
   }
-  if (threadIdx.x == 0) part[(size_t)blockIdx.x * cout + blockIdx.y] = red[0];
 }
 
 // grad[i] = sum over tiles of part[tile][i], in tile order.
@@ -376,17 +390,16 @@ __global__ void k_sum_tiles(const float* __restrict__ part, int ntiles, long n, 
 __global__ void k_loss(const float* __restrict__ yv, const float* __restrict__ tgt, int H, int W, int r, int nout,
                        const float* __restrict__ fw, float* __restrict__ gy, double* __restrict__ lpart) {
   __shared__ float red[256];
-  long n = (long)nout * r * r * H * W;
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int hw = H * W, n = nout * r * r * hw;          // < 2^31 for every workspace lc_create accepts
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.f;
   if (i < n) {
-    int c = (int)(i / ((long)H * W));
-    long p = i - (long)c * H * W;
-    int yy = (int)(p / W), xx = (int)(p - (long)yy * W);
-    int f = c / (r * r), s = c - f * r * r, sy = s / r, sx = s - sy * r;
-    int Wf = W * r;
-    float d = yv[i] - tgt[((size_t)f * H * r + (size_t)(yy * r + sy)) * Wf + (xx * r + sx)];
-    float inv = 1.f / (float)((long)H * W * r * r);
+    const int c = i / hw, p = i - c * hw;
+    const int yy = p / W, xx = p - yy * W;
+    const int f = c / (r * r), s = c - f * r * r, sy = s / r, sx = s - sy * r;
+    const int Wf = W * r;
+    const float d = yv[i] - tgt[((size_t)f * H * r + (size_t)(yy * r + sy)) * Wf + (xx * r + sx)];
+    const float inv = 1.f / (float)((long)hw * r * r);
     gy[i] = 2.f * fw[f] * d * inv;
     l = fw[f] * d * d * inv;
   }
@@ -577,6 +590,7 @@ int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned lon
               lc_net** out) {
   if (!out || cin <= 0 || width <= 0 || depth < 2 || cout <= 0 || max_hw <= 0) return -1;
   if (cin > 48 || width > 48 || cout > 48) return -1;   // tensor-core kernels: at most 48 channels
+  if ((long)cout * max_hw >= (1L << 31)) return -1;       // 32-bit element indices of the loss
   *out = nullptr;
   lc_net* n = new (std::nothrow) lc_net;
   if (!n) return -2;
@@ -612,7 +626,7 @@ int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned lon
   for (int k = 0; k < 2; k++) n->gh[k] = (__nv_bfloat16*)dmalloc(n, (size_t)pad16(width) * max_hw * 2);
   n->part = (float*)dmalloc(n, (size_t)n->max_tiles * n->max_layer * 4);
   n->lpart = (double*)dmalloc(n, (size_t)n->max_lblocks * 8);
-  n->bpart = (float*)dmalloc(n, (size_t)BG_CHUNKS * maxc * 4);
+  n->bpart = (float*)dmalloc(n, (size_t)BG_CHUNKS_NHWC * maxc * 4);
   n->lsum = (double*)dmalloc(n, 8);
   n->fw = (float*)dmalloc(n, 8 * sizeof(float));
   bool ok = n->p && n->g && n->m && n->v && n->pb && n->ga && n->gh[0] && n->gh[1] && n->part && n->bpart &&
@@ -719,8 +733,10 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
     wgrad_fn(op, cp)<<<nbw, 288, wgrad_smem(op, cp), n->st>>>(lin, l == 0 ? 0 : 1, a, H, W, g, g_nhwc, b, n->part,
                                                                ntx, ntiles);
     k_sum_tiles<<<nblk(nw, 256), 256, 0, n->st>>>(n->part, nbw, nw, n->g + n->woff[l]);
-    k_bias_grad<<<dim3(BG_CHUNKS, b), 256, 0, n->st>>>(g, g_nhwc ? op : 0, (long)H * W, b, n->bpart);
-    k_sum_tiles<<<1, 64, 0, n->st>>>(n->bpart, BG_CHUNKS, b, n->g + n->boff[l]);
+    const int nch = g_nhwc ? BG_CHUNKS_NHWC : BG_CHUNKS;
+    k_bias_grad<<<g_nhwc ? dim3(nch) : dim3(nch, b), g_nhwc ? 256 / op * op : 256, 0, n->st>>>(
+        g, g_nhwc ? op : 0, (long)H * W, b, n->bpart);
+    k_sum_tiles<<<1, 64, 0, n->st>>>(n->bpart, nch, b, n->g + n->boff[l]);
     if (l > 0) {
       // dL/d(out of layer l-1) = transposed, flipped convolution of g, times ReLU'(out of layer l-1)
       conv(n, g, g_nhwc, b, H, W, n->pb + n->woff[l], 1, nullptr, a, 0,
