@@ -103,9 +103,10 @@ int sgn_amr_regrid(sgn_amr* a, const double* b_finest, const int* nboxes, const 
 
 /* Flag-driven regridding, so that the patches follow the flow between calls
  * (Sec. 6.3: cells are flagged where the surface jump to a neighbouring cell
- * exceeds a threshold).  Level by level from the coarsest: a cell of level l
- * is flagged where |eta - eta_n| > tol for a neighbour n in the same patch
- * (where level l has no patch, the cell takes its parent cell's flag); the
+ * exceeds a threshold).  Level by level from the coarsest: a wet cell of
+ * level l (h > dry_tol) is flagged where |eta - eta_n| > tol for a wet
+ * neighbour n in the same patch (a dry cell's eta is its bathymetry, not a
+ * surface; where level l has no patch, the cell takes its parent cell's flag); the
  * flags are widened by `buffer` cells of that level; the part of each new
  * level-l box that may hold finer patches (two cells inside its edges, except
  * along the domain boundary) is cut into tile x tile squares of level-l cells

@@ -71,8 +71,10 @@ below are the readings the CUDA hierarchy implements as well.
     over; the next step is recomputed from the new states.
  A12 Boxes from flags (Sec. 6.3: refine where the surface jump between
     neighbouring cells exceeds a threshold): level by level from the coarsest,
-    a cell is flagged where |eta - eta_n| > tol for a neighbour n in the same
-    patch interior; where the level has no patch the cell takes its parent
+    a wet cell (h > dry_tol) is flagged where |eta - eta_n| > tol for a wet
+    neighbour n in the same patch interior (a dry cell has no free surface:
+    its eta is the bathymetry, and its jumps to land or to the shore are not
+    waves); where the level has no patch the cell takes its parent
     cell's flag; flags are widened by `buffer` cells (a square); the part of
     each new box of the level that may hold finer patches (two cells inside
     its edges except along the domain boundary) is cut into tile x tile
@@ -528,11 +530,14 @@ class AmrOracle:
             for p in self.levels[l]:
                 i0, j0, nx, ny = p["box"]
                 e = p["q"][0, NG:NG + ny, NG:NG + nx]
+                wt = (e - p["b"][NG:NG + ny, NG:NG + nx]) > self.dry_tol
                 g = np.zeros((ny, nx), dtype=bool)
-                g[:, 1:] |= np.abs(e[:, 1:] - e[:, :-1]) > tol
-                g[:, :-1] |= np.abs(e[:, :-1] - e[:, 1:]) > tol
-                g[1:, :] |= np.abs(e[1:, :] - e[:-1, :]) > tol
-                g[:-1, :] |= np.abs(e[:-1, :] - e[1:, :]) > tol
+                jx = (np.abs(e[:, 1:] - e[:, :-1]) > tol) & wt[:, 1:] & wt[:, :-1]
+                jy = (np.abs(e[1:, :] - e[:-1, :]) > tol) & wt[1:, :] & wt[:-1, :]
+                g[:, 1:] |= jx
+                g[:, :-1] |= jx
+                g[1:, :] |= jy
+                g[:-1, :] |= jy
                 f[j0:j0 + ny, i0:i0 + nx] = g
                 have[j0:j0 + ny, i0:i0 + nx] = True
             if l > 0:

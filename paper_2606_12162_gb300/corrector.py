@@ -436,6 +436,161 @@ def correct(net, qc, bcd, phid, out=None):
     return out
 
 
+def fallback_boxes(eta, b, thr, hmin, tile, buffer, r):
+    """Level-1 boxes of the runtime fallback from a coarse surface eta and
+    bathymetry b (nc x nc device tensors): the paper's refinement flag
+    (Sec. 6.3), a surface jump |eta - eta_n| > thr between neighbouring cells,
+    counted only between cells deeper than hmin (away from the shore, where the
+    relaxed system runs as SWE anyway and where a coarse cell partly over land
+    would take its children's mean depth under a patch), widened by `buffer`
+    cells; the grid is cut into tile x tile squares from the low corner (a
+    one-cell remainder joined to the square before it) and every square holding
+    a widened flag and no cell shallower than hmin becomes a box (in fine
+    cells)."""
+    import torch
+    nc = eta.shape[-1]
+    deep = (eta - b) > hmin
+    jx = ((eta[:, 1:] - eta[:, :-1]).abs() > thr) & deep[:, 1:] & deep[:, :-1]
+    jy = ((eta[1:, :] - eta[:-1, :]).abs() > thr) & deep[1:, :] & deep[:-1, :]
+    f = torch.zeros_like(deep)
+    f[:, 1:] |= jx
+    f[:, :-1] |= jx
+    f[1:, :] |= jy
+    f[:-1, :] |= jy
+    if buffer > 0:
+        f = torch.nn.functional.max_pool2d(f[None, None].float(), 2 * buffer + 1, 1, buffer)[0, 0] > 0
+    cuts = []
+    x = 0
+    while x < nc:
+        w = min(tile, nc - x)
+        if nc - (x + w) == 1:
+            w += 1
+        cuts.append((x, w))
+        x += w
+    fh, sh = f.cpu().numpy(), (~deep).cpu().numpy()
+    boxes = []
+    for (y0, h_) in cuts:
+        for (x0, w_) in cuts:
+            if fh[y0:y0 + h_, x0:x0 + w_].any() and not sh[y0:y0 + h_, x0:x0 + w_].any():
+                boxes.append((x0 * r, y0 * r, w_ * r, h_ * r))
+    return boxes
+
+
+def hybrid_run(net, meta, s, times, on_snapshot, thr=0.05, tile=16, buffer=4, regrid_every=8, model=W.HSGN,
+               uniform_input=True, hmin=20.0):
+    """The learned form with its runtime fallback to the plain fine solve, on
+    scenario s: a two-level refined hierarchy whose level 0 is the coarse grid
+    and whose level-1 patches (ratio r, the fine grid's spacing and bathymetry)
+    cover the cells the paper's refinement flag marks on the coarse state
+    (fallback_boxes: a surface jump above `thr` [m] between neighbouring cells
+    deeper than `hmin`, widened by `buffer` coarse cells, tile x tile boxes)
+    and follow the flow by a regrid every `regrid_every` level-0 steps.  The
+    flag is computed from the coarse state alone, never from the fine
+    solution.  At each output time T (reached exactly, as
+    advance_to does) the fine-level surface is the network's corrected
+    prolongation of the coarse state outside the patches and the patches' own
+    fine solve inside.  With uniform_input the network reads a separate plain
+    coarse solve advanced beside the hierarchy -- the state it was trained on;
+    otherwise it reads level 0, which holds the patches' average where they
+    cover it.  net = None gives the plain prolongation outside the patches;
+    on_snapshot(T, fine) receives it (3 x r nc x r nc FP64 on the device, eta,
+    hu, hv; valid during the call).  Returns the wall time split into stepping,
+    regridding and snapshots (network and assembly), the level-0 steps, the
+    regrids, and the patch share of the fine grid at each output time."""
+    import torch
+    from . import amr
+    bf, bc, dxc, r = meta["bf"], meta["bc"], meta["dxc"], meta["r"]
+    nc = bc.shape[0]
+    nf = nc * r
+    nv = W.NVAR[model]
+    cx, cy, amp, rad = scenario_source(bc, dxc, s)
+    h = amr.Hierarchy(bf, nc, nc, dxc, r, [[]], model=model, bc=(1, 1, 1, 1), precision=sgn.MIXED, h_star=20.0,
+                      alpha=3.0)
+    q0 = source_state(model, bc, dxc, cx, cy, amp, rad)
+    h.set_patch(0, 0, q0)
+    sc = None
+    if uniform_input:
+        sc = sgn.Solver(bc, dx=dxc, model=model, bc=(1, 1, 1, 1), h_star=20.0, alpha=3.0, precision=sgn.MIXED)
+        sc.set_state(q0)
+        sc.cfl_dt = 0.0
+        tc = 0.0
+    bcd = torch.from_numpy(np.ascontiguousarray(bc)).cuda()
+    phid = torch.from_numpy(np.ascontiguousarray(meta["phic"])).cuda()
+    qcd = torch.empty((nv, nc, nc), dtype=torch.float64, device="cuda")
+    out = torch.empty((3, nf, nf), dtype=torch.float64, device="cuda")
+    res = dict(step_s=0.0, regrid_s=0.0, snapshot_s=0.0, steps=0, regrids=0, patch_frac=[], patches=[])
+    # as advance_to: single steps first (the step after a new state is computed
+    # by that step), then batches sized by the largest step seen
+    t, since, warm, dmax = 0.0, regrid_every, 4, 0.0
+
+    def clock():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    try:
+        for T in times:
+            while T - t > 1e-9:
+                if since >= regrid_every:
+                    c0 = clock()
+                    e0 = torch.from_numpy(h.get_patch(0, 0)[0]).cuda()
+                    h.regrid(bf, [fallback_boxes(e0, bcd, thr, hmin, tile, buffer, r)])
+                    res["regrid_s"] += clock() - c0
+                    res["regrids"] += 1
+                    since = 0
+                rem = T - t
+                c0 = clock()
+                if warm == 0 and dmax > 0.0 and rem > 4.0 * dmax:
+                    k = max(1, min(regrid_every - since, int(0.5 * rem / dmax) - 1))
+                    t = h.step(k)
+                    if t > T + 1e-9:
+                        raise RuntimeError("hybrid_run passed the output time (%.6g > %.6g)" % (t, T))
+                else:
+                    dn = h.next_dt()
+                    k = 1
+                    if warm > 0 or dn <= 0.0 or rem > 2.0 * dn:
+                        tb = t
+                        t = h.step(1)
+                        dmax = max(dmax, t - tb)
+                        warm = max(0, warm - 1)
+                        if t > T + 1e-9:
+                            raise RuntimeError("hybrid_run passed the output time (%.6g > %.6g)" % (t, T))
+                    elif rem <= dn:
+                        h.step_dt(rem)
+                        t = T
+                    else:
+                        h.step_dt(0.5 * rem)
+                        t += 0.5 * rem
+                if k > 1 or warm == 0:
+                    dmax = max(dmax, h.next_dt())
+                res["step_s"] += clock() - c0
+                res["steps"] += k
+                since += k
+            # fine-level surface: network outside the patches, fine solve inside
+            c0 = clock()
+            if sc is not None:
+                tc, _ = advance_to(sc, tc, T)
+                sc.get_state_device(qcd)
+            else:
+                qcd.copy_(torch.from_numpy(h.get_patch(0, 0)))
+            if net is not None:
+                correct(net, qcd, bcd, phid, out)
+            else:
+                _ck(lib().lc_apply(_p(qcd), None, nc, nc, r, S_ETA, S_Q, 0, _p(out), _stream()), "lc_apply")
+            area = 0
+            for k, (i0, j0, bx, by) in enumerate(h.get_boxes(1)):
+                out[:, j0:j0 + by, i0:i0 + bx] = torch.from_numpy(h.get_patch(1, k)[:3]).cuda()
+                area += bx * by
+            res["snapshot_s"] += clock() - c0
+            res["patch_frac"].append(area / float(nf * nf))
+            res["patches"].append(h.npatches(1))
+            on_snapshot(T, out)
+    finally:
+        h.close()
+        if sc is not None:
+            sc.close()
+    return res
+
+
 def _rel_l2(a, b):
     import torch
     return (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()

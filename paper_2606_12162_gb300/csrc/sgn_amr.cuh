@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "../../include/sgn_amr.h"
@@ -136,21 +137,23 @@ __global__ void k_amr_copy(Dev<Real> c, Dev<Real> o, const int* __restrict__ dst
 }
 
 // refinement flag (Sec. 6.3: the surface jump between neighbouring cells
-// exceeds tol), over the patch interiors of a level's atlas; neighbours that
-// are not interior cells of the same patch are not compared
+// exceeds tol), over the wet patch interiors of a level's atlas; neighbours
+// that are dry or not interior cells of the same patch are not compared (a dry
+// cell's eta is its bathymetry, not a free surface)
 template <typename Real>
 __global__ void k_amr_flag(Dev<Real> d, int cur, double tol, unsigned char* __restrict__ out) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= d.nxp || J >= d.nyp) return;
   const size_t id = at(d.pitch, I, J);
+  const Real* e = d.q[cur];
+  auto wet = [&](size_t c) { return (double)e[c] - (double)d.b[c] > d.dry_tol; };
   unsigned char f = 0;
-  if (d.kind[id] & 1) {
-    const Real* e = d.q[cur];
+  if ((d.kind[id] & 1) && wet(id)) {
     const double c = (double)e[id];
     const size_t nb[4] = {id - 1, id + 1, id - d.pitch, id + d.pitch};
 #pragma unroll
     for (int k = 0; k < 4; k++)
-      if ((d.kind[nb[k]] & 1) && fabs((double)e[nb[k]] - c) > tol) f = 1;
+      if ((d.kind[nb[k]] & 1) && wet(nb[k]) && fabs((double)e[nb[k]] - c) > tol) f = 1;
   }
   out[id] = f;
 }
@@ -353,10 +356,17 @@ struct AmrArgs {
   std::vector<std::vector<int>> boxes;   // per level >= 1: 4 ints per box
   const sgn_allocator* alloc;
   cudaStream_t stream;
+  const struct AmrBase* prev = nullptr;  // regrid: the hierarchy whose state the new one takes
 };
+
+// Bathymetry of the levels coarser than the finest (block means), kept by a
+// hierarchy and shared with the hierarchies its regrids build (the finest
+// bathymetry, and so these means, do not change between regrids).
+typedef std::shared_ptr<const std::vector<std::vector<double>>> CoarseBath;
 
 struct AmrBase {
   virtual ~AmrBase() {}
+  virtual CoarseBath coarse_bath() const = 0;
   virtual int init(const AmrArgs& a) = 0;
   virtual int npatches(int l) const = 0;
   virtual int set_patch(int l, int k, const double* q) = 0;
@@ -439,6 +449,7 @@ class Amr : public AmrBase {
   };
   std::vector<Tabs> tb_;
   std::vector<long long> cells_, atlas_;
+  CoarseBath bath_;            // bathymetry of levels 0 .. L-2
   double* sc_ = nullptr;       // dt0, t, last_dt, courant, clipped
   double* staging_ = nullptr;
   size_t stage_bytes_ = 0;
@@ -470,6 +481,7 @@ class Amr : public AmrBase {
     if (cap_) cudaStreamDestroy(cap_);
   }
 
+  CoarseBath coarse_bath() const override { return bath_; }
   int npatches(int l) const override { return (l >= 0 && l < L_) ? (int)bx_[l].size() : SGN_EINVAL; }
   int launches_per_step() const override { return launches_; }
   int info(long long* cells, long long* atlas) const override {
@@ -531,24 +543,33 @@ class Amr : public AmrBase {
           if (own[l].find(b.i0, y, k) >= 0 || own[l].find(b.i0 + b.nx - 1, y, k) >= 0) return SGN_EINVAL;
       }
     }
-    // bathymetry of every level (finest given; block means upward)
-    std::vector<std::vector<double>> bl(L);
-    bl[L - 1].assign(a.b, a.b + (size_t)NX_[L - 1] * NY_[L - 1]);
-    for (int l = L - 2; l >= 0; l--) {
-      bl[l].assign((size_t)NX_[l] * NY_[l], 0.0);
-      const int NXf = NX_[l + 1];
-      for (int j = 0; j < NY_[l]; j++)
-        for (int i = 0; i < NX_[l]; i++) {
-          double s = 0.0;
-          for (int dj = 0; dj < r; dj++)
-            for (int di = 0; di < r; di++) s += bl[l + 1][(size_t)(j * r + dj) * NXf + (i * r + di)];
-          bl[l][(size_t)j * NX_[l] + i] = s / (double)(r * r);
-        }
+    // bathymetry of every level: the finest as given (read in place), block
+    // means upward -- computed once and shared with the hierarchies of later
+    // regrids
+    if (a.prev && a.prev->coarse_bath() && (int)a.prev->coarse_bath()->size() == L - 1) {
+      bath_ = a.prev->coarse_bath();
+    } else {
+      auto bl = std::make_shared<std::vector<std::vector<double>>>(L > 1 ? L - 1 : 0);
+      for (int l = L - 2; l >= 0; l--) {
+        std::vector<double>& c = (*bl)[l];
+        c.assign((size_t)NX_[l] * NY_[l], 0.0);
+        const int NXf = NX_[l + 1];
+        const double* f = l + 1 == L - 1 ? a.b : (*bl)[l + 1].data();
+        for (int j = 0; j < NY_[l]; j++)
+          for (int i = 0; i < NX_[l]; i++) {
+            double s = 0.0;
+            for (int dj = 0; dj < r; dj++)
+              for (int di = 0; di < r; di++) s += f[(size_t)(j * r + dj) * NXf + (i * r + di)];
+            c[(size_t)j * NX_[l] + i] = s / (double)(r * r);
+          }
+      }
+      bath_ = bl;
     }
+    auto blev = [&](int l) -> const double* { return l == L - 1 ? a.b : (*bath_)[l].data(); };
     auto bval = [&](int l, int X, int Y) {
       bool f;
       int Xs = bc_index(X, NX_[l], g0_.bc[0], g0_.bc[1], f), Ys = bc_index(Y, NY_[l], g0_.bc[2], g0_.bc[3], f);
-      return bl[l][(size_t)Ys * NX_[l] + Xs];
+      return blev(l)[(size_t)Ys * NX_[l] + Xs];
     };
     // phi_T of a level cell by the uniform-grid rule (boundary-mapped first)
     auto phival = [&](int l, int X, int Y) -> unsigned char {
@@ -572,6 +593,7 @@ class Amr : public AmrBase {
     for (int l = 0; l < L; l++) {
       CreateArgs ca{};
       ca.prm = prm_; ca.model = a.model; ca.alloc = a.alloc; ca.stream = st_;
+      ca.no_initial_state = a.prev != nullptr;   // a regrid fills every level from the old hierarchy
       std::vector<double> bd;
       std::vector<unsigned char> pd, kd;
       int nxa, nya;
@@ -579,7 +601,7 @@ class Amr : public AmrBase {
       if (l == 0) {
         nxa = g0_.nx; nya = g0_.ny;
         ca.grid = g0_;
-        bd = bl[0];
+        bd.assign(blev(0), blev(0) + (size_t)NX_[0] * NY_[0]);
       } else {
         // shelf packing of the (nx+4) x (ny+4) frames, tallest first
         std::vector<int> ord(bx_[l].size());

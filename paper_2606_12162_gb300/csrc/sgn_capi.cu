@@ -414,8 +414,10 @@ int sgn_amr_regrid(sgn_amr* h, const double* b_finest, const int* nboxes, const 
   if (h->args.L > 1 && (!nboxes || !boxes)) return SGN_EINVAL;
   sgn::AmrBase* impl = nullptr;
   h->args.b = b_finest;
+  h->args.prev = h->impl;
   int r = amr_build(h->args, nboxes, boxes, &impl);
   h->args.b = nullptr;
+  h->args.prev = nullptr;
   h->args.boxes.clear();
   if (r) return r;
   r = impl->take_state(h->impl);

@@ -21,6 +21,7 @@ struct CreateArgs {
   const unsigned char* phi;
   const sgn_allocator* alloc;
   cudaStream_t stream;
+  bool no_initial_state = false;   // leave the state zero (a caller fills it right away)
 };
 
 struct SolverBase {
@@ -306,10 +307,11 @@ class Solver : public SolverBase {
     k_phi<Real><<<gInt_, dim3(32, 8), 0, st_>>>(d_, a.phi ? 1 : 0);
     k_aux<Real><<<dim3((d_.nxp + 1 + 31) / 32, (d_.nyp + 1 + 7) / 8), dim3(32, 8), 0, st_>>>(d_);
     SGN_CK(cudaGetLastError());
+    SGN_CK(cudaStreamSynchronize(st_));
+    if (a.no_initial_state) return SGN_OK;
     // initial state: lake at rest
     std::vector<double> q0(n * NV, 0.0);
     for (size_t i = 0; i < n; i++) q0[i] = a.b[i] > 0 ? a.b[i] : 0.0;
-    SGN_CK(cudaStreamSynchronize(st_));
     return set_state(q0.data(), 0.0, false);
   }
 

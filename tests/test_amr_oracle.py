@@ -329,8 +329,8 @@ def test_flagged_boxes_obey_the_hierarchy_rules(A, seed, tol, tile, buffer):
     """A12 produces box lists that A1 accepts (aligned to parent cells, inside
     one parent, two parent cells from its edges except at the domain boundary,
     disjoint: the constructor validates all of it), for several states and
-    settings; every flagged level-0 cell inside the refinable region lies under
-    a level-1 box."""
+    settings; every level-0 cell with a surface jump to a neighbour (both wet)
+    lies under a level-1 box."""
     b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=seed, amp=0.3)
     am = A.AmrOracle(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, **CFG)
     am.set_state(qs)
@@ -338,11 +338,16 @@ def test_flagged_boxes_obey_the_hierarchy_rules(A, seed, tol, tile, buffer):
     boxes = am.flag_boxes(tol, tile, buffer)
     A.AmrOracle(b, 24, 20, 0.2, 2, boxes, model=2, **CFG)     # raises on a rule violation
     e = am.patch_state(0, 0)[0]
+    p0 = am.levels[0][0]
+    ny0, nx0 = e.shape
+    wet = (e - p0["b"][A.NG:A.NG + ny0, A.NG:A.NG + nx0]) > CFG["dry_tol"]
+    jx = (np.abs(np.diff(e, axis=1)) > tol) & wet[:, 1:] & wet[:, :-1]
+    jy = (np.abs(np.diff(e, axis=0)) > tol) & wet[1:, :] & wet[:-1, :]
     jump = np.zeros(e.shape, dtype=bool)
-    jump[:, 1:] |= np.abs(np.diff(e, axis=1)) > tol
-    jump[:, :-1] |= np.abs(np.diff(e, axis=1)) > tol
-    jump[1:, :] |= np.abs(np.diff(e, axis=0)) > tol
-    jump[:-1, :] |= np.abs(np.diff(e, axis=0)) > tol
+    jump[:, 1:] |= jx
+    jump[:, :-1] |= jx
+    jump[1:, :] |= jy
+    jump[:-1, :] |= jy
     cov = np.zeros(e.shape, dtype=bool)
     for (i0, j0, nx, ny) in boxes[0]:
         cov[j0 // 2:(j0 + ny) // 2, i0 // 2:(i0 + nx) // 2] = True

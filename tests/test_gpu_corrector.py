@@ -141,6 +141,59 @@ def test_trained_corrector_gains_over_prolongation(C):
         assert r_["err_hybrid"] <= r_["err_net"] + 1e-12, r_
 
 
+def test_runtime_fallback_hybrid_small(C):
+    """The learned form with its runtime fallback (hybrid_run): patches of the
+    plain fine solve where the a-priori surface-jump flag fires on the coarse
+    state (deep water), the trained network's corrected prolongation elsewhere.
+    Coarse 64^2 at 2 km, fine 256^2 at 500 m, 6 training and 2 held-out
+    scenarios.  Bound, at every held-out snapshot: the hybrid's surface error
+    (relative L2 over the ocean against the full fine solve) is at most 1.05 x
+    the network's alone and below the plain prolongation's; the patches cover
+    part of the grid, not all of it, and the fine solve never ran where no flag
+    fired (the flags see the coarse state only)."""
+    import torch
+    times = (60.0, 120.0, 180.0)
+    pairs, meta = C.generate_pairs(nc=64, r=4, dxc=2000.0, scenarios=range(8), times=times)
+    train = [p for p in pairs if p["scenario"] < 6]
+    held = [p for p in pairs if p["scenario"] >= 6]
+    net = C.Net(cin=5, width=16, depth=4, r=4, nout=3, max_hw=64 * 64, seed=11)
+    C.train(net, train, iters=2000, crop=32, lr=2e-3)
+    ocean_f, ocean_c = C.ocean_masks(meta)
+    rows = {(r_["scenario"], r_["time"]): r_ for r_ in C.evaluate(net, held, block=8, bound=0.1, ocean_f=ocean_f,
+                                                                    ocean_c=ocean_c)}
+    m = ocean_f.to(torch.float64)
+    for s in sorted({p["scenario"] for p in held}):
+        ref = {p["time"]: p["qf"][0] for p in held if p["scenario"] == s}
+        errs = {}
+
+        def cb(T, fine):
+            errs[T] = (torch.linalg.norm((fine[0] - ref[T]) * m) / torch.linalg.norm(ref[T] * m)).item()
+
+        res = C.hybrid_run(net, meta, s, times, cb, thr=0.02, tile=8, buffer=2, regrid_every=4)
+        assert len(errs) == len(times) and res["regrids"] >= 2
+        assert max(res["patch_frac"]) < 0.9
+        for T in times:
+            r_ = rows[(s, T)]
+            assert errs[T] <= 1.05 * r_["rel_net"] + 1e-12, (s, T, errs[T], r_["rel_net"])
+            assert errs[T] < r_["rel_prolong"], (s, T, errs[T], r_["rel_prolong"])
+
+
+def test_fallback_boxes_follow_the_flag(C):
+    """fallback_boxes: a deep-water surface jump above the threshold yields a box
+    over it (tile-aligned, in fine cells); jumps at or below it, jumps in
+    shallow water and tiles holding a shallow cell yield none."""
+    import torch
+    nc, r = 32, 4
+    b = torch.full((nc, nc), -100.0, dtype=torch.float64, device="cuda")
+    eta = torch.zeros_like(b)
+    eta[10, 5] = 0.05                                  # jump of 5 cm in deep water
+    eta[25, 25] = 0.01                                 # below the threshold
+    boxes = C.fallback_boxes(eta, b, 0.02, 20.0, 8, 1, r)
+    assert boxes == [(0, 32, 32, 32)]                  # the 8 x 8 tile holding (10, 5), in fine cells
+    b[8:16, 0:8] = -10.0                               # that tile in shallow water: no box
+    assert C.fallback_boxes(eta, b, 0.02, 20.0, 8, 1, r) == []
+
+
 def test_experiment_pipeline_small(C):
     """The whole experiment driver at a small size: pairs with gauges, training,
     evaluation, inference timing, throughput figures and the FP64 fine check."""
