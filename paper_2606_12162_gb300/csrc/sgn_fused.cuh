@@ -591,7 +591,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
         const Real tr = Mr > Real(0) ? th : (Mr < Real(0) ? sm.th[po][t + 1] : Real(1));
         const Real tb = Mb > Real(0) ? th4 : (Mb < Real(0) ? th : Real(1));
         const Real tt = Mt > Real(0) ? th : (Mt < Real(0) ? thn : Real(1));
-        const Real lx = Real(d.lam[0]), ly = Real(d.lam[1]);
+        const Real lx = d.lamr[0], ly = d.lamr[1];   // the FP64 factors rounded once (the same values)
         Real en = wb[0] - lx * (tr * Mr - tl * Ml) - ly * (tt * Mt - tb * Mb);
         Real q[NV];
         bool bad = !isfinite(en);
@@ -609,7 +609,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
         Real hr = en - b;
         hr = hr > Real(0) ? hr : Real(0);
         const bool wet = hr > d.rdry_tol;
-        source_switch<MODEL, Real>(q, wet, hr, c2, Real(d.lam[3]));
+        source_switch<MODEL, Real>(q, wet, hr, c2, d.lamr[3]);
         Real* qo = d.q[1 - cur];
         const size_t id = at(d.pitch, I, J);
 #pragma unroll
