@@ -230,7 +230,8 @@ int sgn_launches_per_step(sgn_solver* s);
  *     a single grid only: EINVAL for an FP64 solver; a refined level falls back
  *     to 0).  With schedule 2 the SGN_TUNE_UPDATE option selects the rows one
  *     block of the one-pass kernel marches over: 128, 64 or 256 (its block is
- *     128 columns wide).
+ *     128 columns wide).  A new mixed-precision solver starts with schedule 2
+ *     (and option 0 elsewhere); an FP64 solver with schedule 0.
  * The block-shape options and schedules 0 and 1 compute the same values bit
  * for bit; schedule 2 evaluates the same expressions in one kernel and agrees
  * with them to FP32 rounding (the compiler may fuse a different set of

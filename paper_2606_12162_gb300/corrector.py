@@ -738,7 +738,23 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--out", default=None, help="JSON summary path")
     ap.add_argument("--weights", default=None, help="trained parameters (.npy)")
+    ap.add_argument("--profile", type=int, default=0, metavar="N",
+                    help="instead of the experiment: one forward pass and one training step of the network on "
+                         "random N x N inputs (a small, fixed launch sequence for a profiler)")
     a = ap.parse_args(argv)
+    if a.profile:
+        import torch
+        lib()
+        n = a.profile
+        net = Net(cin=5, width=32, depth=5, r=a.r, max_hw=n * n, seed=5000)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn((5, n, n), device="cuda", generator=g)
+        t = torch.randn((3, n * a.r, n * a.r), device="cuda", generator=g)
+        net.forward(x)
+        net.train_step(x, t, 0.0)
+        torch.cuda.synchronize()
+        print("profile run done: %d x %d" % (n, n))
+        return
     res = experiment(nc=a.nc, r=a.r, dxc=a.dxc, n_train=a.train, n_held=a.held, iters=a.iters, crop=a.crop,
                      lr=a.lr, block=a.block, bound=a.bound, gauges=a.gauges, fp64_check=not a.no_fp64,
                      log=lambda m: print(m, flush=True))
