@@ -335,32 +335,17 @@ __global__ void __launch_bounds__(288, 2) k_wgrad_mma(const void* __restrict__ i
       }
 }
 
-// Bias gradient partials: part[chunk][o] = sum of g[o][p] over the pixels of
-// chunk blockIdx.x (gridDim.x contiguous ranges), in FP32, in a fixed order;
-// k_sum_tiles adds the chunks.  g: channel-major FP32 (cs = 0; one block per
-// chunk and channel, blockIdx.y = o) or pixel-major BF16 with cs channels per
-// pixel (one block per chunk for all channels: thread t reads channel t % cs of
-// every (blockDim / cs)-th pixel, so a warp reads consecutive bytes; the
-// threads of one channel are then summed in thread order).
-constexpr int BG_CHUNKS = 64, BG_CHUNKS_NHWC = 1024;
-__global__ void k_bias_grad(const void* __restrict__ gv, int cs, long hw, int cout, float* __restrict__ part) {
+// Bias gradient partials of a hidden layer: part[chunk][o] = sum of g[p][o]
+// over the pixels of chunk blockIdx.x (gridDim.x contiguous ranges), in FP32, in
+// a fixed order; k_sum_chunks adds the chunks.  g: pixel-major BF16 with cs
+// channels per pixel; thread t reads channel t % cs of every (blockDim / cs)-th
+// pixel, so a warp reads consecutive bytes; the threads of one channel are then
+// summed in thread order.
+constexpr int BG_CHUNKS = 1024;
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ gb, int cs, long hw, int cout,
+                            float* __restrict__ part) {
   __shared__ float red[256];
   const long p0 = hw * blockIdx.x / gridDim.x, p1 = hw * (blockIdx.x + 1) / gridDim.x;
-  if (cs == 0) {
-    const int o = blockIdx.y;
-    const float* go = static_cast<const float*>(gv) + (size_t)o * hw;
-    float s = 0.f;
-    for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += go[p];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int k = 128; k > 0; k >>= 1) {
-      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * cout + o] = red[0];
-    return;
-  }
-  const __nv_bfloat16* gb = static_cast<const __nv_bfloat16*>(gv);
   const int ppi = blockDim.x / cs;                     // pixels per pass
   const int o = threadIdx.x % cs, pk = threadIdx.x / cs;
   float s = 0.f;
@@ -375,41 +360,112 @@ __global__ void k_bias_grad(const void* __restrict__ gv, int cs, long hw, int co
   }
 }
 
-// grad[i] = sum over tiles of part[tile][i], in tile order.
-__global__ void k_sum_tiles(const float* __restrict__ part, int ntiles, long n, float* __restrict__ grad) {
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float s = 0.f;
-  for (int t = 0; t < ntiles; t++) s += part[(size_t)t * n + i];
-  grad[i] = s;
-}
-
-// Loss of the pixel-shuffled output against the fine target and its gradient:
-// channel f*r*r + sy*r + sx of coarse pixel (y, x) is fine cell (r y + sy, r x + sx)
-// of field f.  Per-block loss partials are summed in order by k_sum_loss.
-__global__ void k_loss(const float* __restrict__ yv, const float* __restrict__ tgt, int H, int W, int r, int nout,
-                       const float* __restrict__ fw, float* __restrict__ gy, double* __restrict__ lpart) {
+// out[o] = sum over chunks k of part[k][o] (n values per chunk): one block per
+// o; thread t adds chunks t, t + 256, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(256) k_sum_chunks(const float* __restrict__ part, int nchunks, int n,
+                                                    float* __restrict__ out) {
   __shared__ float red[256];
-  const int hw = H * W, n = nout * r * r * hw;          // < 2^31 for every workspace lc_create accepts
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float l = 0.f;
-  if (i < n) {
-    const int c = i / hw, p = i - c * hw;
-    const int yy = p / W, xx = p - yy * W;
-    const int f = c / (r * r), s = c - f * r * r, sy = s / r, sx = s - sy * r;
-    const int Wf = W * r;
-    const float d = yv[i] - tgt[((size_t)f * H * r + (size_t)(yy * r + sy)) * Wf + (xx * r + sx)];
-    const float inv = 1.f / (float)((long)hw * r * r);
-    gy[i] = 2.f * fw[f] * d * inv;
-    l = fw[f] * d * d * inv;
-  }
-  red[threadIdx.x] = l;
+  const int o = blockIdx.x;
+  float s = 0.f;
+  for (int k = threadIdx.x; k < nchunks; k += 256) s += part[(size_t)k * n + o];
+  red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) lpart[blockIdx.x] = (double)red[0];
+  if (threadIdx.x == 0) out[o] = red[0];
+}
+
+// grad[i] = sum over tiles t of part[t][i].  A block takes 32 consecutive i
+// and splits the tiles into 8 classes (t mod 8): thread (class, i) adds its
+// class in tile order, then the class sums are added in class order.
+__global__ void __launch_bounds__(256) k_sum_tiles(const float* __restrict__ part, int ntiles, long n,
+                                                   float* __restrict__ grad) {
+  __shared__ float red[8][33];
+  const int j = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const long i = (long)blockIdx.x * 32 + j;
+  float a = 0.f;
+  if (i < n)
+    for (int t = c; t < ntiles; t += 8) a += part[(size_t)t * n + i];
+  red[c][j] = a;
+  __syncthreads();
+  if (c == 0 && i < n) {
+    float b = 0.f;
+    for (int k = 0; k < 8; k++) b += red[k][j];
+    grad[i] = b;
+  }
+}
+
+// Loss of the pixel-shuffled output against the fine target, dL/dy and the
+// last layer's bias-gradient partials.  Channel f r^2 + sy r + sx of coarse
+// pixel (y, x) is fine cell (r y + sy, r x + sx) of field f.  Block (k, g)
+// takes row group g = (f, sy) -- output channels c0 + [0, r), c0 = f r^2 + sy r,
+// and fine rows r y + sy of field f -- for the coarse rows y = k, k +
+// LOSS_CHUNKS, ...: a thread reads the r output planes at its pixel and r
+// consecutive target values (one 16-byte load when r = 4).  dL/dy goes out
+// pixel-major BF16 with cs channels per pixel, the operand layout of the
+// backward convolutions (which multiply it in BF16); the bias partials use the
+// FP32 values.  Loss and bias partials per block are summed in a fixed order
+// by k_sum_loss and k_sum_chunks.
+constexpr int LOSS_CHUNKS = 64, LOSS_MAXR = 8;
+template <bool R4>
+__global__ void __launch_bounds__(256) k_loss(const float* __restrict__ yv, const float* __restrict__ tgt, int H,
+                                              int W, int r, int cs, const float* __restrict__ fw,
+                                              __nv_bfloat16* __restrict__ gy, double* __restrict__ lpart,
+                                              float* __restrict__ bpart, int cout) {
+  __shared__ float red[LOSS_MAXR + 1][256];
+  const int g = blockIdx.y, f = g / r, sy = g - f * r, c0 = f * r * r + sy * r;
+  const size_t hw = (size_t)H * W, Wf = (size_t)W * r;
+  const float inv = 1.f / (float)(hw * r * r), wf = fw[f];
+  float l = 0.f, bs[LOSS_MAXR];
+#pragma unroll
+  for (int j = 0; j < LOSS_MAXR; j++) bs[j] = 0.f;
+  for (int y = blockIdx.x; y < H; y += LOSS_CHUNKS) {
+    const float* trow = tgt + ((size_t)f * H * r + (size_t)y * r + sy) * Wf;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+      const size_t p = (size_t)y * W + x;
+      if constexpr (R4) {
+        const float4 t4 = *reinterpret_cast<const float4*>(trow + (size_t)x * 4);
+        const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+        float gv[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const float d = yv[(size_t)(c0 + j) * hw + p] - tv[j];
+          gv[j] = 2.f * wf * d * inv;
+          bs[j] += gv[j];
+          l += wf * d * d * inv;
+        }
+        uint2 pk;
+        pk.x = pack_bf16(gv[0], gv[1]);
+        pk.y = pack_bf16(gv[2], gv[3]);
+        *reinterpret_cast<uint2*>(gy + p * cs + c0) = pk;
+      } else {
+#pragma unroll
+        for (int j = 0; j < LOSS_MAXR; j++) {
+          if (j < r) {
+            const float d = yv[(size_t)(c0 + j) * hw + p] - trow[(size_t)x * r + j];
+            const float gv = 2.f * wf * d * inv;
+            gy[p * cs + c0 + j] = __float2bfloat16_rn(gv);
+            bs[j] += gv;
+            l += wf * d * d * inv;
+          }
+        }
+      }
+    }
+  }
+  red[0][threadIdx.x] = l;
+#pragma unroll
+  for (int j = 0; j < LOSS_MAXR; j++) red[1 + j][threadIdx.x] = bs[j];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int j = 0; j <= r; j++) red[j][threadIdx.x] += red[j][threadIdx.x + h];
+    __syncthreads();
+  }
+  const int k = blockIdx.x;
+  if (threadIdx.x == 0) lpart[(size_t)g * LOSS_CHUNKS + k] = (double)red[0][0];
+  if (threadIdx.x < r) bpart[(size_t)k * cout + c0 + threadIdx.x] = red[1 + threadIdx.x][0];
 }
 
 // Sum of the n block partials in FP64: one block, strided per-thread sums and a
@@ -567,11 +623,12 @@ struct lc_net {
   // for the hidden layers, channel-major FP32 for the last one
   std::vector<void*> act;
   __nv_bfloat16* gh[2] = {nullptr, nullptr};   // pixel-major BF16 gradients of hidden outputs
-  float *ga = nullptr, *part = nullptr, *bpart = nullptr;   // ga: dL/dy, channel-major FP32
+  __nv_bfloat16* ga = nullptr;  // dL/dy, pixel-major BF16 with pad16(cout) channels (padding zero)
+  float *part = nullptr, *bpart = nullptr;
   double *lpart = nullptr, *lsum = nullptr;
   float* fw = nullptr;          // loss field weights (device copy)
   long max_layer;
-  int max_tiles, max_lblocks;
+  int max_tiles;
   int nsm = 1;                  // SMs of the device (persistent grids: 2 blocks per SM)
   long step = 0;
   std::vector<void*> bufs;
@@ -616,23 +673,23 @@ int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned lon
   }
   // weight-gradient partials: one per block of the persistent grid
   n->max_tiles = 2 * n->nsm;
-  n->max_lblocks = (int)((max_hw * cout + 255) / 256) + 1;
   n->p = (float*)dmalloc(n, n->np * 4); n->g = (float*)dmalloc(n, n->np * 4);
   n->m = (float*)dmalloc(n, n->np * 4); n->v = (float*)dmalloc(n, n->np * 4);
   n->pb = (__nv_bfloat16*)dmalloc(n, n->np * 2);
   for (int l = 0; l < depth; l++)
     n->act.push_back(dmalloc(n, l < depth - 1 ? (size_t)pad16(n->co[l]) * max_hw * 2 : (size_t)n->co[l] * max_hw * 4));
-  n->ga = (float*)dmalloc(n, (size_t)cout * max_hw * 4);
+  n->ga = (__nv_bfloat16*)dmalloc(n, (size_t)pad16(cout) * max_hw * 2);
   for (int k = 0; k < 2; k++) n->gh[k] = (__nv_bfloat16*)dmalloc(n, (size_t)pad16(width) * max_hw * 2);
   n->part = (float*)dmalloc(n, (size_t)n->max_tiles * n->max_layer * 4);
-  n->lpart = (double*)dmalloc(n, (size_t)n->max_lblocks * 8);
-  n->bpart = (float*)dmalloc(n, (size_t)BG_CHUNKS_NHWC * maxc * 4);
+  n->lpart = (double*)dmalloc(n, (size_t)LOSS_CHUNKS * cout * 8);
+  n->bpart = (float*)dmalloc(n, (size_t)std::max(BG_CHUNKS, LOSS_CHUNKS) * maxc * 4);
   n->lsum = (double*)dmalloc(n, 8);
   n->fw = (float*)dmalloc(n, 8 * sizeof(float));
   bool ok = n->p && n->g && n->m && n->v && n->pb && n->ga && n->gh[0] && n->gh[1] && n->part && n->bpart &&
             n->lpart && n->lsum && n->fw;
   for (auto a : n->act) ok = ok && a;
   if (!ok) { lc_destroy(n); return -2; }
+  if (cudaMemset(n->ga, 0, (size_t)pad16(cout) * max_hw * 2) != cudaSuccess) { lc_destroy(n); return -3; }
   // He initialisation from a counter-based generator (splitmix64 + Box-Muller)
   std::vector<float> h(n->np, 0.f);
   unsigned long long s = seed;
@@ -710,39 +767,45 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
   if ((long)H * W > n->max_hw || nout * r * r != n->cout || nout > 8 || lr < 0) return -1;
   // forward, keeping every layer's output
   for (int l = 0; l < n->depth; l++) conv_fwd(n, l, x_dev, H, W, n->act[l]);
-  // loss and dL/dy
-  long ny = (long)n->cout * H * W;
-  int lb = (int)nblk(ny, 256);
-  if (lb > n->max_lblocks) return -1;
+  // loss, dL/dy and the last layer's bias-gradient partials
+  const int ng = n->cout / r;                    // row groups (field, sub-row)
   if (cudaMemcpyAsync(n->fw, field_w, nout * sizeof(float), cudaMemcpyHostToDevice, n->st) != cudaSuccess) return -3;
-  k_loss<<<lb, 256, 0, n->st>>>(static_cast<const float*>(n->act[n->depth - 1]), target_dev, H, W, r, nout, n->fw,
-                                n->ga, n->lpart);
-  k_sum_loss<<<1, 1024, 0, n->st>>>(n->lpart, lb, n->lsum);
-  // backward: g (in ga) is dL/d(pre-activation) of layer l
+  const int cs = pad16(n->cout);
+  if (r == 4 && ((uintptr_t)target_dev & 15) == 0)
+    k_loss<true><<<dim3(LOSS_CHUNKS, ng), 256, 0, n->st>>>(static_cast<const float*>(n->act[n->depth - 1]),
+                                                           target_dev, H, W, r, cs, n->fw, n->ga, n->lpart,
+                                                           n->bpart, n->cout);
+  else
+    k_loss<false><<<dim3(LOSS_CHUNKS, ng), 256, 0, n->st>>>(static_cast<const float*>(n->act[n->depth - 1]),
+                                                            target_dev, H, W, r, cs, n->fw, n->ga, n->lpart,
+                                                            n->bpart, n->cout);
+  k_sum_loss<<<1, 1024, 0, n->st>>>(n->lpart, ng * LOSS_CHUNKS, n->lsum);
+  // backward: g is dL/d(pre-activation) of layer l, pixel-major BF16
   const int ntx = (W + CT_W - 1) / CT_W, ntiles = ntx * ((H + CT_H - 1) / CT_H);
   const int nbw = std::min(ntiles, n->max_tiles);
-  // g: dL/dy (channel-major FP32) for the last layer, then the pixel-major
-  // BF16 gradients of the hidden outputs, alternating between gh[0] and gh[1]
-  const void* g = n->ga;
-  int g_nhwc = 0, gk = 0;
+  // g: dL/dy for the last layer, then the gradients of the hidden outputs,
+  // alternating between gh[0] and gh[1]
+  const __nv_bfloat16* g = n->ga;
+  int gk = 0;
   for (int l = n->depth - 1; l >= 0; l--) {
     const void* lin = l == 0 ? (const void*)x_dev : n->act[l - 1];
     const int a = n->ci[l], b = n->co[l];
     const long nw = (long)a * b * 9;
     const int op = pad16(b), cp = pad16(a);
-    wgrad_fn(op, cp)<<<nbw, 288, wgrad_smem(op, cp), n->st>>>(lin, l == 0 ? 0 : 1, a, H, W, g, g_nhwc, b, n->part,
+    wgrad_fn(op, cp)<<<nbw, 288, wgrad_smem(op, cp), n->st>>>(lin, l == 0 ? 0 : 1, a, H, W, g, 1, b, n->part,
                                                                ntx, ntiles);
-    k_sum_tiles<<<nblk(nw, 256), 256, 0, n->st>>>(n->part, nbw, nw, n->g + n->woff[l]);
-    const int nch = g_nhwc ? BG_CHUNKS_NHWC : BG_CHUNKS;
-    k_bias_grad<<<g_nhwc ? dim3(nch) : dim3(nch, b), g_nhwc ? 256 / op * op : 256, 0, n->st>>>(
-        g, g_nhwc ? op : 0, (long)H * W, b, n->bpart);
-    k_sum_tiles<<<1, 64, 0, n->st>>>(n->bpart, nch, b, n->g + n->boff[l]);
+    k_sum_tiles<<<(unsigned)((nw + 31) / 32), 256, 0, n->st>>>(n->part, nbw, nw, n->g + n->woff[l]);
+    if (l == n->depth - 1) {
+      k_sum_chunks<<<b, 256, 0, n->st>>>(n->bpart, LOSS_CHUNKS, b, n->g + n->boff[l]);
+    } else {
+      k_bias_grad<<<BG_CHUNKS, 256 / op * op, 0, n->st>>>(g, op, (long)H * W, b, n->bpart);
+      k_sum_chunks<<<b, 256, 0, n->st>>>(n->bpart, BG_CHUNKS, b, n->g + n->boff[l]);
+    }
     if (l > 0) {
       // dL/d(out of layer l-1) = transposed, flipped convolution of g, times ReLU'(out of layer l-1)
-      conv(n, g, g_nhwc, b, H, W, n->pb + n->woff[l], 1, nullptr, a, 0,
+      conv(n, g, 1, b, H, W, n->pb + n->woff[l], 1, nullptr, a, 0,
            static_cast<const __nv_bfloat16*>(n->act[l - 1]), n->gh[gk], 1);
       g = n->gh[gk];
-      g_nhwc = 1;
       gk ^= 1;
     }
   }

@@ -14,21 +14,19 @@
 // transverse corrections of the neighbouring faces, and those feed the
 // positivity factors of the ring of cells around each updated cell.  The
 // thread marches up the rows; at iteration r it
-//   A  stages row r + 1 into shared memory with cp.async (ghost cells through
+//   A  stages row r + 2 into shared memory with cp.async (ghost cells through
 //      the boundary index map), builds the record of cell (I, r) (first source
-//      half step, primitives, FP64 g h / 2) and publishes it for the right
-//      neighbour, solves the y face below row r and limits the y face below
-//      row r - 1 (the faces below and above it are the thread's own, in
-//      registers), and solves the x face I of row r - 1 (its left cell's
-//      record was published one row earlier) -- two independent normal solves
-//      in one phase;
-//   C  limits the x face with the x faces I - 1 and I + 1 (shared memory);
+//      half step, primitives, FP64 g h / 2), solves the y face below row r and
+//      limits the y face below row r - 1 (the faces below and above it are the
+//      thread's own, in registers);
+//   B  solves the x face I of row r - 1 (left cell record from shared memory);
+//   C  limits it with the x faces I - 1 and I + 1 (shared memory);
 //   D  transverse corrections of the y face below row r - 1 (x fluctuations of
 //      rows r - 2 and r - 1) and of the x face I of row r - 2 (y fluctuations of
 //      columns I - 1 and I);
 //   E  positivity factor of cell (I, r - 2) and the update of cell (I, r - 3).
 // Values along a column stay in the thread's registers from row to row; values
-// of neighbouring columns pass through shared memory (three barriers per row).
+// of neighbouring columns pass through shared memory (four barriers per row).
 // The index ranges over which each quantity is computed are those of the
 // kernel sequence (faces of ghost rows and columns included), so the result is
 // the same.
@@ -268,10 +266,10 @@ template <int MODEL, typename Real> struct FusedSmem {
                                           // W, P, b, c^2, h, sqrt(h), C
   static constexpr int NIN = NV + 4;      // staged fields: state, b, c^2, psi_x, psi_y
   Real in[2][NIN][FUSED_NT];
-  Real rec[2][NX][FUSED_NT];              // by row parity: written for row r, read one row later
-  double g2[2][FUSED_NT];
-  double e64[2][FUSED_NT];
-  unsigned char wet[2][FUSED_NT];
+  Real rec[NX][FUSED_NT];
+  double g2[FUSED_NT];
+  double e64[FUSED_NT];
+  unsigned char wet[FUSED_NT];
   Real xw[WR_N][FUSED_NT];                // x-face wave records of the row being limited
   Real lx[NV][FUSED_NT];                  // A^- + Ftil of each x face (for the transverse sums)
   Real uy[NV][FUSED_NT];                  // sum of the y fluctuations entering each cell
@@ -442,41 +440,41 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
     Real uy[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) { uy[k] = ry1[k] + fyL[k]; sm.uy[k][t] = uy[k]; }
-    // record of row r for the x solve of its right neighbour one row later
+    // record of row r - 1 for the x solve of its right neighbour
     {
-      const int pw = r & 1;
 #pragma unroll
-      for (int k = 0; k < NV; k++) sm.rec[pw][k][t] = rc.W[k];
+      for (int k = 0; k < NV; k++) sm.rec[k][t] = rp.W[k];
 #pragma unroll
-      for (int k = 0; k < NV - 1; k++) sm.rec[pw][NV + k][t] = rc.P[k];
-      sm.rec[pw][2 * NV - 1][t] = rc.b;
-      sm.rec[pw][2 * NV][t] = rc.c2;
-      sm.rec[pw][2 * NV + 1][t] = rc.hr;
-      sm.rec[pw][2 * NV + 2][t] = rc.sqh;
-      sm.rec[pw][2 * NV + 3][t] = rc.C;
-      sm.wet[pw][t] = rc.wet ? 1 : 0;
-      sm.g2[pw][t] = rc.g2;
-      sm.e64[pw][t] = rc.e64;
+      for (int k = 0; k < NV - 1; k++) sm.rec[NV + k][t] = rp.P[k];
+      sm.rec[2 * NV - 1][t] = rp.b;
+      sm.rec[2 * NV][t] = rp.c2;
+      sm.rec[2 * NV + 1][t] = rp.hr;
+      sm.rec[2 * NV + 2][t] = rp.sqh;
+      sm.rec[2 * NV + 3][t] = rp.C;
+      sm.wet[t] = rp.wet ? 1 : 0;
+      sm.g2[t] = rp.g2;
+      sm.e64[t] = rp.e64;
     }
-    // x face I of row r - 1 (between columns I - 1 and I): the left record was
-    // published one row ago, so this solve runs beside the y solve above
+    __syncthreads();
+
+    // ===== B: x face I of row r - 1 (between columns I - 1 and I)
     Waves<Real> xv = zero_waves<Real>();
     {
-      const int J = r - 1, pr = (r - 1) & 1;
+      const int J = r - 1;
       if (t >= 1 && J >= 1 && J <= ny + 2 && I >= 1 && I <= nx + 3 && J >= rs) {
         Rec<MODEL, Real> lf;
 #pragma unroll
-        for (int k = 0; k < NV; k++) lf.W[k] = sm.rec[pr][k][t - 1];
+        for (int k = 0; k < NV; k++) lf.W[k] = sm.rec[k][t - 1];
 #pragma unroll
-        for (int k = 0; k < NV - 1; k++) lf.P[k] = sm.rec[pr][NV + k][t - 1];
-        lf.b = sm.rec[pr][2 * NV - 1][t - 1];
-        lf.c2 = sm.rec[pr][2 * NV][t - 1];
-        lf.hr = sm.rec[pr][2 * NV + 1][t - 1];
-        lf.sqh = sm.rec[pr][2 * NV + 2][t - 1];
-        lf.C = sm.rec[pr][2 * NV + 3][t - 1];
-        lf.wet = sm.wet[pr][t - 1] != 0;
-        lf.g2 = sm.g2[pr][t - 1];
-        lf.e64 = sm.e64[pr][t - 1];
+        for (int k = 0; k < NV - 1; k++) lf.P[k] = sm.rec[NV + k][t - 1];
+        lf.b = sm.rec[2 * NV - 1][t - 1];
+        lf.c2 = sm.rec[2 * NV][t - 1];
+        lf.hr = sm.rec[2 * NV + 1][t - 1];
+        lf.sqh = sm.rec[2 * NV + 2][t - 1];
+        lf.C = sm.rec[2 * NV + 3][t - 1];
+        lf.wet = sm.wet[t - 1] != 0;
+        lf.g2 = sm.g2[t - 1];
+        lf.e64 = sm.e64[t - 1];
         lf.psx = Real(0);
         xv = normal_solve<MODEL, Real>(d, rec_side<MODEL, Real, 0>(lf), rec_side<MODEL, Real, 0>(rp), rp.psx);
       }
