@@ -54,15 +54,15 @@ FLOPS_PER_CELL = {
 # 2048^2 (profiles/k_step_fused_2048_counters.md); the block key is 128 columns
 # x the rows of its long chunks:
 INSTR_PER_CELL = {
-    ("hsgn", "mixed", "k_step_fused", "128x128"): 2129.5,
-    ("hsgn", "mixed", "k_step_fused", "128x64"): 2231.8,
-    ("hsgn", "mixed", "k_step_fused", "128x256"): 2078.1,
+    ("hsgn", "mixed", "k_step_fused", "128x128"): 2126.4,
+    ("hsgn", "mixed", "k_step_fused", "128x64"): 2228.7,
+    ("hsgn", "mixed", "k_step_fused", "128x256"): 2075.0,
 }
 # DRAM bytes (read + write):
 TRAFFIC_PER_CELL = {
-    ("hsgn", "mixed", "k_step_fused", "128x128"): 67.1,
-    ("hsgn", "mixed", "k_step_fused", "128x64"): 68.0,
-    ("hsgn", "mixed", "k_step_fused", "128x256"): 66.1,
+    ("hsgn", "mixed", "k_step_fused", "128x128"): 67.4,
+    ("hsgn", "mixed", "k_step_fused", "128x64"): 68.3,
+    ("hsgn", "mixed", "k_step_fused", "128x256"): 66.5,
     **{("hsgn", "mixed", "k_prep", sh): 58 for sh in ("32x8", "32x4", "64x4")},
     ("hsgn", "mixed", "k_face_x", "128x2"): 128, ("hsgn", "mixed", "k_face_x", "256x1"): 128,
     ("hsgn", "mixed", "k_face_x", "64x4"): 129,

@@ -12,8 +12,11 @@
  * Network: `depth` 3x3 convolutions (padding 1), `width` channels, ReLU between
  * layers, last layer r*r*nout channels (pixel-shuffled to the fine grid).
  * Weights are kept as FP32 master copies for Adam and used as BF16 in the forward
- * and backward passes; the convolutions are implicit GEMMs on the tensor cores
- * (BF16 operands, FP32 accumulation).
+ * and backward passes; the convolutions (forward and input gradient) are
+ * implicit GEMMs on the fifth-generation tensor cores (tcgen05.mma: BF16
+ * operands from shared memory, FP32 accumulators in tensor memory), the weight
+ * gradients on the warp-level tensor-core instructions (mma.sync, BF16
+ * operands, FP32 accumulation).
  *
  * Layouts: the network input and output are channel-major [C][H][W] float32 in
  * device memory (batch 1); hidden activations live inside the handle.  Parameters are packed per layer as weights [cout][cin][3][3]
@@ -50,6 +53,13 @@ int lc_set_params(lc_net* n, const float* host, long count);
 
 /* y[cout][H][W] = net(x[cin][H][W]); device pointers. */
 int lc_forward(lc_net* n, const float* x_dev, int H, int W, float* y_dev);
+
+/* Wait for the work issued on the handle's stream; 0, -3 on a CUDA error, or
+ * -4 when a convolution gave up waiting for its tensor-core instructions (each
+ * such wait is bounded to about two seconds; the kernel then releases its
+ * tensor memory and ends, leaving its output incomplete).  lc_train_step
+ * returns this value too. */
+int lc_sync(lc_net* n);
 
 /* Loss and gradients for one sample.  target_dev: fine-grid target
  * [nout][r*H][r*W]; field_w: nout host weights.  Loss = sum over fields f of

@@ -25,6 +25,7 @@ LC_SIGS = [
     ("lc_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long]),
     ("lc_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long]),
     ("lc_forward", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.c_int, ctypes.c_int, DP]),
+    ("lc_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("lc_train_step", ctypes.c_int, [ctypes.c_void_p, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_float,
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -112,6 +113,10 @@ class Net:
         y = torch.empty((self.cout, H, Wd), dtype=torch.float32, device=x.device)
         _ck(lib().lc_forward(self.h, _p(x), H, Wd, _p(y)), "lc_forward")
         return y
+
+    def sync(self):
+        """Wait for the network's kernels; raises if one reported a failure."""
+        _ck(lib().lc_sync(self.h), "lc_sync")
 
     def train_step(self, x, t, lr, fw=(1.0, 1.0, 1.0), want_grad=False):
         _, H, Wd = x.shape

@@ -20,31 +20,27 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// 3x3 convolutions as implicit GEMMs on the tensor cores: mma.sync m16n8k16
-// with BF16 operands and FP32 accumulation.
-//
 // Layouts.  The network input x and its output y are FP32 channel-major planes
 // [c][y][x] (the data kernels' layout).  Everything in between -- hidden
 // activations and the gradients flowing back through them -- is stored as BF16
 // pixel-major rows [y][x][c] of CS = channels rounded up to 16 (the padding
 // stays zero): the values the tensor cores multiply are BF16 anyway, so this
-// changes no result and halves the bytes.  A block stages a tile of the input
-// in shared memory as [pixel][channel] rows of CS + 8 BF16 (the 8 extra keep
-// the 16-byte ldmatrix rows of consecutive pixels on different banks), so any
-// 3x3 tap offset is a whole-row shift and every operand row stays 16-byte
-// aligned: pixel-major inputs arrive by 16-byte cp.async (zero-filled outside
-// the image), double-buffered across tiles; channel-major FP32 inputs are read,
-// rounded and stored by the threads.
-constexpr int CT_H = 8;              // output tile rows (one per warp)
-constexpr int CT_W = 32;             // output tile columns (two 16-pixel MMA rows)
+// changes no result and halves the bytes.
+//
+// Weight gradients (k_wgrad_mma) run on the warp-level tensor-core
+// instructions, mma.sync m16n8k16 with BF16 operands and FP32 accumulation: a
+// block stages a tile of the layer input and of the gradient in shared memory
+// as [pixel][channel] rows of CS + 8 BF16 (the 8 extra keep the 16-byte
+// ldmatrix rows of consecutive pixels on different banks); pixel-major inputs
+// arrive by 16-byte cp.async (zero-filled outside the image), channel-major
+// FP32 inputs are read, rounded and stored by the threads.  The convolutions
+// themselves (forward and input gradient) run on tcgen05 (k_conv_tc, below).
+constexpr int CT_H = 8;              // weight-gradient tile rows
+constexpr int CT_W = 32;             // weight-gradient tile columns
 constexpr int CT_PIX = (CT_H + 2) * (CT_W + 2);   // staged input pixels (tile + halo)
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
-}
 __device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
@@ -122,142 +118,355 @@ __device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int nh
   }
 }
 
-// Convolution with padding 1: out[o][y][x] = bias[o] + sum_c sum_k
-// B(o, c, k) in[c][y + ky - 1][x + kx - 1] (k = 3 ky + kx), then optional ReLU
-// and an optional mask (out = 0 where mask <= 0; mask pixel-major BF16 like a
-// pixel-major output).  in: pixel-major BF16 with CP channels (in_nhwc) or
-// channel-major FP32 with cin planes; out: pixel-major BF16 with NT*8 channels,
-// padding included (out_nhwc), or channel-major FP32 with cout planes.  The
-// weights B are read from the network's BF16 tensor w: transpose = 0,
-// B(o, c, k) = w[o][c][k] (the layer itself, w of shape cout x cin x 9);
-// transpose = 1, B(o, c, k) = w[c][o][8 - k] (w of shape cin x cout x 9: the
-// transposed, flipped kernel that maps dL/d(out) of that layer to dL/d(in)).
-// Persistent blocks of 8 warps take tiles of 8 x 32 output pixels; warp w
-// computes row w of the tile: 2 m-tiles of 16 pixels x NT n-tiles of 8 output
-// channels, K = 9 taps x CP channels in steps of 16.
-template <int CP, int NT>
-__global__ void __launch_bounds__(256, 2) k_conv_mma(const void* __restrict__ in, int in_nhwc, int cin, int H, int W,
-                                                     const __nv_bfloat16* __restrict__ w, int transpose,
-                                                     const float* __restrict__ bias, int cout, int relu,
-                                                     const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
-                                                     int out_nhwc, int ntx, int ntiles) {
-  constexpr int PS = CP + 8;
-  constexpr int NO = NT * 8;
+// ---------------------------------------------------------------------------
+// 3x3 convolutions on the fifth-generation tensor cores (tcgen05): implicit
+// GEMM with M = the 128 output pixels of one tile row, N = the output channels
+// (16, 32 or 48, padding included), K = 16 input channels of one tap per
+// instruction; BF16 operands read by the tensor cores from shared memory
+// through matrix descriptors, FP32 accumulators in tensor memory (TMEM).
+//
+// Shared-memory operand layout (the "no swizzle, K-major" canonical layout of
+// the tcgen05 descriptors: 8 x 16-byte core matrices; LBO = byte distance
+// between the two 8-channel halves of an instruction's K = 16, SBO = byte
+// distance between groups of 8 rows):
+//   A (input tile, TC_R + 2 rows x TC_SW columns with a one-pixel halo):
+//     [channel / 8][pixel][channel % 8], planes TC_PA bytes apart, so the 128
+//     pixels x 16 channels of staged row t shifted by kx start at pixel
+//     t * TC_SW + kx of planes 2j, 2j + 1 (LBO = TC_PA, SBO = 128): a tap shift
+//     is a shift of the descriptor's start address.
+//   B (weights): [kx][channel / 8][n][channel % 8] with n = (2 - ky) NO + o:
+//     the three row taps of one column tap stacked along N (LBO = 3 NO * 16,
+//     SBO = 128).
+// One instruction multiplies staged row t (shifted by kx) by the stacked
+// weights of the row taps ky that map it to output rows of the tile (output
+// row t - ky, 0 <= t - ky < TC_R): N = NO, 2 NO or 3 NO columns, written to the
+// TMEM columns of output rows t - ky_hi .. t - ky_lo (lane p = output pixel p,
+// column r * NO + o = channel o of output row r), which are zeroed before the
+// tile.  Per tile that is (TC_R + 2) x 3 x CP / 16 instructions of up to
+// 3 NO columns instead of TC_R x 9 x CP / 16 of NO columns: each staged row
+// shift is read from shared memory once for its three row taps.  One thread
+// issues them and commits them to an mbarrier; the four warps then read their
+// 32 lanes back (tcgen05.ld 32x32b) and write bias + ReLU (+ mask) pixel by
+// pixel: pixel-major BF16 rows (16-byte stores) or channel-major FP32 planes
+// (coalesced along x).
+constexpr int TC_R = 4;                         // output rows per tile
+constexpr int TC_W = 128;                       // output columns per tile: the instruction's M
+constexpr int TC_SW = TC_W + 2;                 // staged columns
+constexpr int TC_SPIX = (TC_R + 2) * TC_SW;     // staged pixels
+// bytes between two 8-channel planes of the staged tile: the plane size rounded
+// up to 128 bytes, plus 16, so the 16-byte chunks of one pixel in consecutive
+// planes fall on different banks when the copies land
+constexpr int TC_PA = (TC_SPIX * 16 + 127) / 128 * 128 + 16;
+constexpr int TC_THREADS = 128;
+
+__host__ __device__ constexpr int tc_cols(int no) {   // TMEM columns to allocate: a power of 2 >= 32
+  return TC_R * no <= 32 ? 32 : TC_R * no <= 64 ? 64 : TC_R * no <= 128 ? 128 : 256;
+}
+__host__ __device__ constexpr int tc_smem_used(int cp, int no) {
+  return cp / 8 * TC_PA + 9 * cp * no * 2 + 256 + 16;   // A, B, bias, mbarrier + TMEM address
+}
+
+// Shared-memory matrix descriptor: start address, LBO and SBO in 16-byte units,
+// descriptor version 1 (bits 46-47), no swizzle, base offset 0.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((saddr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
+// M >> 4 (bits 24-28).
+__device__ __forceinline__ unsigned tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(TC_W >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       int accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Wait until the mbarrier has completed the phase of the given parity; gives up
+// after about two seconds (returns false).
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
+}
+// The NO consecutive FP32 columns (16, 32 or 48) of this thread's TMEM lane,
+// waited for in the same statement (the registers are only valid after
+// tcgen05.wait::ld).
+#define TC_R16(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), "=r"(r[i + 5]), \
+                  "=r"(r[i + 6]), "=r"(r[i + 7]), "=r"(r[i + 8]), "=r"(r[i + 9]), "=r"(r[i + 10]),          \
+                  "=r"(r[i + 11]), "=r"(r[i + 12]), "=r"(r[i + 13]), "=r"(r[i + 14]), "=r"(r[i + 15])
+template <int NO> __device__ __forceinline__ void tmem_ld(unsigned taddr, float* v) {
+  unsigned r[NO];
+  if constexpr (NO == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : TC_R16(0)
+        : "r"(taddr)
+        : "memory");
+  } else if constexpr (NO == 32) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : TC_R16(0), TC_R16(16)
+        : "r"(taddr)
+        : "memory");
+  } else {
+    static_assert(NO == 48, "16, 32 or 48 output channels");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%48];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,"
+        "%47}, [%49];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : TC_R16(0), TC_R16(16), TC_R16(32)
+        : "r"(taddr), "r"(taddr + 32)
+        : "memory");
+  }
+#pragma unroll
+  for (int i = 0; i < NO; i++) v[i] = __uint_as_float(r[i]);
+}
+#undef TC_R16
+// Zero 32 consecutive TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_zero32(unsigned taddr) {
+  const unsigned z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
+// Convolution with padding 1: out[o][y][x] =
+// bias[o] + sum_c sum_k B(o, c, k) in[c][y + ky - 1][x + kx - 1], optional
+// ReLU, optional mask (out = 0 where mask <= 0).  transpose = 0: B(o, c, k) =
+// w[o][c][k]; transpose = 1: B(o, c, k) = w[c][o][8 - k] (the transposed,
+// flipped kernel mapping dL/d(out) of that layer to dL/d(in)).  in: pixel-major
+// BF16 with CP channels per pixel (in_nhwc) or channel-major FP32 planes (cin
+// of them); out: pixel-major BF16 with NO channels per pixel (out_nhwc) or
+// channel-major FP32 planes (cout).  Persistent blocks of 128 threads take
+// tiles of TC_R x TC_W output pixels.  A wait that does not end within about
+// two seconds sets *err and ends the block (after a second bounded wait for
+// its instructions in flight and the release of its TMEM).
+template <int CP, int NO>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv_tc(const void* __restrict__ in, int in_nhwc, int cin, int H, int W, const __nv_bfloat16* __restrict__ w,
+              int transpose, const float* __restrict__ bias, int cout, int relu,
+              const __nv_bfloat16* __restrict__ mask, void* __restrict__ out, int out_nhwc, int ntx, int ntiles,
+              int* __restrict__ err) {
+  constexpr int C8 = CP / 8;
+  constexpr int A_BYTES = C8 * TC_PA, B_BYTES = 9 * CP * NO * 2;
+  constexpr unsigned NCOL = tc_cols(NO);
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(sm_raw);    // [9][NO][PS]
-  __nv_bfloat16* sA0 = sB + 9 * NO * PS;                            // [2][CT_PIX][PS]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // weights, once per block: sB[k][o][c] = B(o, c, k), zero-padded
-  for (int t = threadIdx.x; t < 9 * NO * CP; t += blockDim.x) {
-    const int c = t % CP, r = t / CP, o = r % NO, k = r / NO;
+  unsigned char* sA = sm_raw;
+  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(sm_raw + A_BYTES);
+  float* sBias = reinterpret_cast<float*>(sm_raw + A_BYTES + B_BYTES);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm_raw + A_BYTES + B_BYTES + 256);
+  unsigned* tslot = reinterpret_cast<unsigned*>(sm_raw + A_BYTES + B_BYTES + 264);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights once per block: sB[kx][c / 8][(2 - ky) NO + o][c % 8] = B(o, c, 3 ky + kx),
+  // zero-padded
+  for (int e = tid; e < 9 * CP * NO; e += TC_THREADS) {
+    const int c = e % CP, o = (e / CP) % NO, k = e / (CP * NO);
+    const int ky = k / 3, kx = k - 3 * ky;
     float v = 0.f;
     if (o < cout && c < cin)
       v = (float)(transpose ? w[((size_t)c * cout + o) * 9 + (8 - k)] : w[((size_t)o * cin + c) * 9 + k]);
-    sB[(size_t)(k * NO + o) * PS + c] = __float2bfloat16_rn(v);
+    sB[((size_t)(kx * C8 + c / 8) * (3 * NO) + (2 - ky) * NO + o) * 8 + (c & 7)] = __float2bfloat16_rn(v);
   }
-  const int g = lane >> 2, tq = lane & 3;
-  auto tile_origin = [&](int tile, int& ty0, int& tx0) {
-    ty0 = (tile / ntx) * CT_H;
-    tx0 = (tile % ntx) * CT_W;
-  };
-  if (in_nhwc && (int)blockIdx.x < ntiles) {
-    int ty0, tx0;
-    tile_origin(blockIdx.x, ty0, tx0);
-    stage_tile<CP, PS, CT_H + 2, CT_W + 2>(in, 1, cin, H, W, ty0 - 1, tx0 - 1, sA0);
+  for (int o = tid; o < NO; o += TC_THREADS) sBias[o] = (bias && o < cout) ? bias[o] : 0.f;
+  const unsigned mb = smem_u32(mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(NCOL)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tslot;
+  const unsigned tlane = tmem + ((unsigned)(32 * warp) << 16);   // this warp's 32 lanes
+  // accumulators of the first tile start at zero (each warp clears its lanes)
+#pragma unroll
+  for (int c = 0; c < TC_R * NO; c += 32) tmem_zero32(tlane + c);
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+  const unsigned aBase = smem_u32(sA), bBase = smem_u32(sB);
+  const size_t hw = (size_t)H * W;
+  // input tile rows ty0 - 1 .. ty0 + TC_R and columns tx0 - 1 .. tx0 + TC_W
+  // (zero outside the image): pixel-major BF16 by 16-byte cp.async copies
+  // (committed, not waited for), channel-major FP32 by the threads
+  auto stage_nhwc = [&](int tile) {
+    const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
+    const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(in);
+    for (int e = tid; e < TC_SPIX * C8; e += TC_THREADS) {
+      const int ch = e % C8, pix = e / C8;
+      const int yy = pix / TC_SW, xx = pix - yy * TC_SW;
+      const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+      const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
+      const __nv_bfloat16* s = ok ? src + ((size_t)gy * W + gx) * CP + 8 * ch : src;
+      cp_async16(sA + ch * TC_PA + pix * 16, s, ok ? 16 : 0);
+    }
     cp_commit();
-  }
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
-    int ty0, tx0;
-    tile_origin(tile, ty0, tx0);
-    __nv_bfloat16* sA = sA0 + (size_t)(in_nhwc ? (it & 1) : 0) * CT_PIX * PS;
-    if (in_nhwc) {
-      // prefetch the next tile into the other buffer (read by every thread in
-      // the previous iteration, which ended with a barrier), then wait for this one
-      const int nt = tile + gridDim.x;
-      if (nt < ntiles) {
-        int ny0, nx0;
-        tile_origin(nt, ny0, nx0);
-        stage_tile<CP, PS, CT_H + 2, CT_W + 2>(in, 1, cin, H, W, ny0 - 1, nx0 - 1,
-                                               sA0 + (size_t)((it + 1) & 1) * CT_PIX * PS);
+  };
+  auto stage_nchw = [&](int tile) {
+    const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
+    const float* src = static_cast<const float*>(in);
+    for (int pix = tid; pix < TC_SPIX; pix += TC_THREADS) {
+      const int yy = pix / TC_SW, xx = pix - yy * TC_SW;
+      const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+      const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
+      const size_t o = ok ? (size_t)gy * W + gx : 0;
+#pragma unroll
+      for (int ch = 0; ch < C8; ch++) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) v[i] = (ok && 8 * ch + i < cin) ? __ldg(src + (size_t)(8 * ch + i) * hw + o) : 0.f;
+        uint4 u;
+        u.x = pack_bf16(v[0], v[1]);
+        u.y = pack_bf16(v[2], v[3]);
+        u.z = pack_bf16(v[4], v[5]);
+        u.w = pack_bf16(v[6], v[7]);
+        *reinterpret_cast<uint4*>(sA + ch * TC_PA + pix * 16) = u;
       }
-      cp_commit();
-      cp_wait<1>();
-    } else {
-      stage_tile<CP, PS, CT_H + 2, CT_W + 2>(in, 0, cin, H, W, ty0 - 1, tx0 - 1, sA);
     }
+  };
+  if (in_nhwc && (int)blockIdx.x < ntiles) stage_nhwc(blockIdx.x);
+  bool failed = false;
+  unsigned phase = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
+    // this tile's input: copies issued during the previous tile's epilogue (or
+    // above), or the FP32 planes read now
+    if (in_nhwc)
+      cp_wait<0>();
+    else
+      stage_nchw(tile);
+    // the threads' shared-memory writes become visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    float acc[2][NT][4];
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int t = 0; t < TC_R + 2; t++) {
+        // row taps that map staged row t to an output row of the tile
+        const int ky_lo = t - (TC_R - 1) > 0 ? t - (TC_R - 1) : 0, ky_hi = t < 2 ? t : 2;
+        const unsigned id = tc_idesc((ky_hi - ky_lo + 1) * NO);
+        const unsigned d = tmem + (t - ky_hi) * NO;
+        const unsigned boff = (2 - ky_hi) * NO / 8 * 128;
 #pragma unroll
-    for (int m = 0; m < 2; m++)
+        for (int kx = 0; kx < 3; kx++)
 #pragma unroll
-      for (int n = 0; n < NT; n++)
+          for (int j = 0; j < CP / 16; j++) {
+            const unsigned long long ad = tc_desc(aBase + 2 * j * TC_PA + (t * TC_SW + kx) * 16, TC_PA, 128);
+            const unsigned long long bd =
+                tc_desc(bBase + (kx * C8 + 2 * j) * (3 * NO) * 16 + boff, 3 * NO * 16, 128);
+            tc_mma(d, ad, bd, id, 1);
+          }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
+                   : "memory");
+    }
+    const bool done = mbar_wait(mb, phase);
+    if (__syncthreads_or(!done)) {
+      failed = true;
+      break;
+    }
+    phase ^= 1;
+    // the instructions have read the input tile: the next tile's copies go out
+    // now and land while this tile's accumulators are written back
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (in_nhwc && tile + (int)gridDim.x < ntiles) stage_nhwc(tile + gridDim.x);
+    tc_fence_after();
+    // epilogue: thread = output pixel x of each tile row
+    const int x = tx0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int r = 0; r < TC_R; r++) {
+      float v[NO];
+      tmem_ld<NO>(tlane + r * NO, v);
+      const int y = ty0 + r;
+      if (y >= H || x >= W) continue;
+      const size_t pix = (size_t)y * W + x;
 #pragma unroll
-        for (int e = 0; e < 4; e++) acc[m][n][e] = 0.f;
+      for (int o = 0; o < NO; o++) {
+        v[o] += sBias[o];
+        if (relu) v[o] = v[o] > 0.f ? v[o] : 0.f;
+      }
+      if (mask) {
+        const uint4* mk = reinterpret_cast<const uint4*>(mask + pix * NO);
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-      const int ky = k / 3, kx = k % 3;
+        for (int c = 0; c < NO / 8; c++) {
+          const uint4 m4 = __ldg(mk + c);
+          const unsigned mw[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-      for (int c0 = 0; c0 < CP; c0 += 16) {
-        unsigned a[2][4];
-#pragma unroll
-        for (int m = 0; m < 2; m++) {
-          // A rows: pixels x = 16 m + (lane & 15) of output row `warp`, shifted by the tap
-          const int px = 16 * m + (lane & 15) + kx, py = warp + ky;
-          const __nv_bfloat16* pa = sA + (size_t)(py * (CT_W + 2) + px) * PS + c0 + 8 * (lane >> 4);
-          ldsm_x4(smem_u32(pa), a[m][0], a[m][1], a[m][2], a[m][3]);
-        }
-#pragma unroll
-        for (int n = 0; n < NT; n += 2) {
-          unsigned b0, b1, b2, b3;
-          const int o = 8 * (n + (lane >> 4)) + (lane & 7);
-          const __nv_bfloat16* pb = sB + (size_t)(k * NO + o) * PS + c0 + 8 * ((lane >> 3) & 1);
-          ldsm_x4(smem_u32(pb), b0, b1, b2, b3);
-#pragma unroll
-          for (int m = 0; m < 2; m++) {
-            mma_bf16(acc[m][n], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
-            mma_bf16(acc[m][n + 1], a[m][0], a[m][1], a[m][2], a[m][3], b2, b3);
+          for (int i = 0; i < 4; i++) {
+            const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
+            if (!(__low2float(m2) > 0.f)) v[8 * c + 2 * i] = 0.f;
+            if (!(__high2float(m2) > 0.f)) v[8 * c + 2 * i + 1] = 0.f;
           }
         }
       }
-    }
-    // epilogue: rows g and g + 8 of each m-tile are pixels, columns 2 tq, 2 tq + 1 channels
-    const int y = ty0 + warp;
-    if (y < H) {
+      if (out_nhwc) {
+        uint4* op = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + pix * NO);
 #pragma unroll
-      for (int m = 0; m < 2; m++)
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const int x = tx0 + 16 * m + g + 8 * h;
-          if (x >= W) continue;
-          const size_t pix = (size_t)y * W + x;
-#pragma unroll
-          for (int n = 0; n < NT; n++) {
-            const int o = 8 * n + 2 * tq;
-            float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
-            if (bias) {
-              if (o < cout) v0 += bias[o];
-              if (o + 1 < cout) v1 += bias[o + 1];
-            }
-            if (relu) { v0 = v0 > 0.f ? v0 : 0.f; v1 = v1 > 0.f ? v1 : 0.f; }
-            if (mask) {
-              const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + pix * NO + o);
-              if (!(__low2float(mk) > 0.f)) v0 = 0.f;
-              if (!(__high2float(mk) > 0.f)) v1 = 0.f;
-            }
-            if (out_nhwc) {
-              *reinterpret_cast<unsigned*>(static_cast<__nv_bfloat16*>(out) + pix * NO + o) = pack_bf16(v0, v1);
-            } else {
-              float* of = static_cast<float*>(out);
-              if (o < cout) of[(size_t)o * H * W + pix] = v0;
-              if (o + 1 < cout) of[(size_t)(o + 1) * H * W + pix] = v1;
-            }
-          }
+        for (int c = 0; c < NO / 8; c++) {
+          uint4 u;
+          u.x = pack_bf16(v[8 * c], v[8 * c + 1]);
+          u.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+          u.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+          u.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+          op[c] = u;
         }
+      } else {
+        float* of = static_cast<float*>(out);
+#pragma unroll
+        for (int o = 0; o < NO; o++)
+          if (o < cout) of[(size_t)o * hw + pix] = v[o];
+      }
     }
-    __syncthreads();   // this tile's buffer and the other one may be overwritten next
+    // clear this warp's accumulators for the next tile; the reads and these
+    // stores are done before the next tile's instructions
+#pragma unroll
+    for (int c = 0; c < TC_R * NO; c += 32) tmem_zero32(tlane + c);
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(mb, phase);   // the instructions in flight, once more bounded
   }
   cp_wait<0>();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
+  }
 }
 
 // Weight gradient partials: part[blk][o][c][k] = sum over the block's pixels
@@ -578,34 +787,59 @@ inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ---- launch helpers of the tensor-core kernels: padded channel counts are
 // template arguments (16, 32, 48 channels; 2, 4, 6 n-tiles of 8 outputs)
-typedef void (*ConvFn)(const void*, int, int, int, int, const __nv_bfloat16*, int, const float*, int, int,
-                       const __nv_bfloat16*, void*, int, int, int);
 typedef void (*WgradFn)(const void*, int, int, int, int, const void*, int, int, float*, int, int);
 static int pad16(int c) { return (c + 15) / 16 * 16; }
-static ConvFn conv_fn(int cp, int nt) {
-#define CF(C, N) if (cp == C && nt == N) return k_conv_mma<C, N>;
-  CF(16, 2) CF(16, 4) CF(16, 6) CF(32, 2) CF(32, 4) CF(32, 6) CF(48, 2) CF(48, 4) CF(48, 6)
-#undef CF
-  return nullptr;
-}
 static WgradFn wgrad_fn(int op, int cp) {
 #define WF(O, C) if (op == O && cp == C) return k_wgrad_mma<O, C>;
   WF(16, 16) WF(16, 32) WF(16, 48) WF(32, 16) WF(32, 32) WF(32, 48) WF(48, 16) WF(48, 32) WF(48, 48)
 #undef WF
   return nullptr;
 }
-static size_t conv_smem(int cp, int nt) { return (size_t)(9 * nt * 8 + 2 * CT_PIX) * (cp + 8) * 2; }
 static size_t wgrad_smem(int op, int cp) { return ((size_t)CT_PIX * (cp + 8) + (size_t)CT_H * CT_W * (op + 8)) * 2; }
+typedef void (*TcFn)(const void*, int, int, int, int, const __nv_bfloat16*, int, const float*, int, int,
+                     const __nv_bfloat16*, void*, int, int, int, int*);
+static TcFn tc_fn(int cp, int no) {
+#define TF(C, N) if (cp == C && no == N) return k_conv_tc<C, N>;
+  TF(16, 16) TF(16, 32) TF(16, 48) TF(32, 16) TF(32, 32) TF(32, 48) TF(48, 16) TF(48, 32) TF(48, 48)
+#undef TF
+  return nullptr;
+}
+// Launch configuration of each tensor-core convolution: dynamic shared memory
+// (padded where needed so that the blocks resident on one SM never ask for more
+// than the 512 TMEM columns between them) and resident blocks per SM.
+struct TcCfg {
+  int smem = 0, per_sm = 0;
+};
+static TcCfg tc_cfg[3][3];
 static int set_smem_attrs() {
   for (int cp = 16; cp <= 48; cp += 16)
-    for (int k = 2; k <= 6; k += 2) {
-      if (cudaFuncSetAttribute(conv_fn(cp, k), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(cp, k)) !=
-          cudaSuccess)
-        return -3;
-      const int op = 8 * k;   // 16, 32, 48
+    for (int op = 16; op <= 48; op += 16)
       if (cudaFuncSetAttribute(wgrad_fn(op, cp), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)wgrad_smem(op, cp)) != cudaSuccess)
         return -3;
+  // resident blocks of a tensor-core convolution = what the SM's shared memory
+  // holds; the request is padded until that is at most 512 / (its TMEM columns)
+  int dev = 0, smax = 0, ssm = 0, sres = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ssm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sres, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+    return -3;
+  for (int cp = 16; cp <= 48; cp += 16)
+    for (int no = 16; no <= 48; no += 16) {
+      TcFn f = tc_fn(cp, no);
+      const int allowed = 512 / tc_cols(no);
+      int sm = tc_smem_used(cp, no);
+      while (ssm / (sm + sres) > allowed) sm += 1024;
+      if (sm > smax) return -3;
+      if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) return -3;
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return -3;
+      const int regs = (fa.numRegs + 7) / 8 * 8;   // per-thread allocation granularity
+      int occ = std::min(ssm / (sm + sres), allowed);
+      occ = std::min(occ, 65536 / (regs * TC_THREADS));
+      if (occ < 1) return -3;
+      tc_cfg[cp / 16 - 1][no / 16 - 1] = {sm, occ};
     }
   return 0;
 }
@@ -627,6 +861,7 @@ struct lc_net {
   float *part = nullptr, *bpart = nullptr;
   double *lpart = nullptr, *lsum = nullptr;
   float* fw = nullptr;          // loss field weights (device copy)
+  int* err = nullptr;           // set by a kernel whose bounded wait ran out
   long max_layer;
   int max_tiles;
   int nsm = 1;                  // SMs of the device (persistent grids: 2 blocks per SM)
@@ -685,11 +920,16 @@ int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned lon
   n->bpart = (float*)dmalloc(n, (size_t)std::max(BG_CHUNKS, LOSS_CHUNKS) * maxc * 4);
   n->lsum = (double*)dmalloc(n, 8);
   n->fw = (float*)dmalloc(n, 8 * sizeof(float));
+  n->err = (int*)dmalloc(n, sizeof(int));
   bool ok = n->p && n->g && n->m && n->v && n->pb && n->ga && n->gh[0] && n->gh[1] && n->part && n->bpart &&
-            n->lpart && n->lsum && n->fw;
+            n->lpart && n->lsum && n->fw && n->err;
   for (auto a : n->act) ok = ok && a;
   if (!ok) { lc_destroy(n); return -2; }
-  if (cudaMemset(n->ga, 0, (size_t)pad16(cout) * max_hw * 2) != cudaSuccess) { lc_destroy(n); return -3; }
+  if (cudaMemset(n->ga, 0, (size_t)pad16(cout) * max_hw * 2) != cudaSuccess ||
+      cudaMemset(n->err, 0, sizeof(int)) != cudaSuccess) {
+    lc_destroy(n);
+    return -3;
+  }
   // He initialisation from a counter-based generator (splitmix64 + Box-Muller)
   std::vector<float> h(n->np, 0.f);
   unsigned long long s = seed;
@@ -734,16 +974,17 @@ int lc_set_params(lc_net* n, const float* host, long count) {
   return cudaStreamSynchronize(n->st) == cudaSuccess ? 0 : -3;
 }
 
-// 3x3 convolution of `in` (cin planes) into `out` (cout planes) on the tensor
-// cores with the BF16 weights w (transpose: see k_conv_mma).
+// 3x3 convolution of `in` (cin channels) into `out` (cout channels) on the
+// tensor cores with the BF16 weights w (transpose: see k_conv_tc).
 static void conv(lc_net* n, const void* in, int in_nhwc, int cin, int H, int W, const __nv_bfloat16* w,
                  int transpose, const float* bias, int cout, int relu, const __nv_bfloat16* mask, void* out,
                  int out_nhwc) {
-  const int cp = pad16(cin), nt = (cout + 15) / 16 * 2;
-  const int ntx = (W + CT_W - 1) / CT_W, ntiles = ntx * ((H + CT_H - 1) / CT_H);
-  const int nb = std::min(ntiles, 2 * n->nsm);
-  conv_fn(cp, nt)<<<nb, 256, conv_smem(cp, nt), n->st>>>(in, in_nhwc, cin, H, W, w, transpose, bias, cout, relu,
-                                                          mask, out, out_nhwc, ntx, ntiles);
+  const int cp = pad16(cin), no = pad16(cout);
+  const TcCfg& c = tc_cfg[cp / 16 - 1][no / 16 - 1];
+  const int ntx = (W + TC_W - 1) / TC_W, ntiles = ntx * ((H + TC_R - 1) / TC_R);
+  const int nb = std::min(ntiles, c.per_sm * n->nsm);
+  tc_fn(cp, no)<<<nb, TC_THREADS, c.smem, n->st>>>(in, in_nhwc, cin, H, W, w, transpose, bias, cout, relu, mask,
+                                                    out, out_nhwc, ntx, ntiles, n->err);
 }
 
 // Layer l forward: its input is x (channel-major FP32) for l = 0, else the
@@ -819,7 +1060,15 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
     if (cudaMemcpyAsync(grad_host, n->g, n->np * 4, cudaMemcpyDeviceToHost, n->st) != cudaSuccess) return -3;
   }
   if (cudaGetLastError() != cudaSuccess) return -3;
-  return cudaStreamSynchronize(n->st) == cudaSuccess ? 0 : -3;
+  return lc_sync(n);
+}
+
+int lc_sync(lc_net* n) {
+  if (!n) return -1;
+  int e = 0;
+  if (cudaMemcpyAsync(&e, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->st) != cudaSuccess) return -3;
+  if (cudaStreamSynchronize(n->st) != cudaSuccess) return -3;
+  return e ? -4 : 0;
 }
 
 int lc_make_input(const double* q_dev, const double* b_dev, const unsigned char* phi_dev, int Hc, int Wc,

@@ -43,18 +43,20 @@ def test_gradients_match_fp64_reference(C):
     assert abs(loss - lref) <= 1e-5 * lref
     assert np.abs(g - gref).max() <= 1e-4 * np.abs(gref).max()
     # forward alone
-    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    yd = net.forward(torch.from_numpy(x).cuda())
+    net.sync()                      # no convolution gave up waiting for its tensor-core work
+    y = yd.cpu().numpy()
     yref = R.forward(pr, net.layers(), x, quant=R.bf16_round)[-1]
     assert np.abs(y - yref).max() <= 1e-4 * np.abs(yref).max()
 
 
 @pytest.mark.parametrize("cin,width,depth,r,nout,H,W", [(5, 32, 3, 4, 3, 37, 70), (5, 16, 2, 2, 3, 9, 33),
-                                                       (7, 48, 3, 2, 4, 16, 32)])
+                                                       (7, 48, 3, 2, 4, 16, 32), (5, 32, 3, 4, 3, 67, 300)])
 def test_tensor_core_layers_match_reference(C, cin, width, depth, r, nout, H, W):
     """The tensor-core convolutions at the channel counts of the full network
     (5 -> 32 -> 48 with ratio 4 and 3 fields, the 48-channel gradient into 32
-    channels, 7 -> 48 -> 16) and at ragged
-    tile edges: loss and gradients within 1e-4 of the FP64 reference with the
+    channels, 7 -> 48 -> 16) and at ragged tile edges (tiles of 4 rows x 128
+    columns: 67 x 300 spans 17 x 3 of them): loss and gradients within 1e-4 of the FP64 reference with the
     same BF16 operand rounding; the same step twice gives the same bits."""
     import torch
     from oracle import conv_ref as R
