@@ -7,7 +7,9 @@
 // FP32 accumulation; FP32 activations, biases, losses and master weights).  The
 // weight gradients are summed per block of a fixed persistent grid, then over
 // blocks in a fixed order, so training is run-to-run reproducible.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -22,17 +24,20 @@ namespace {
 // ---------------------------------------------------------------------------
 // Layouts.  The network input x and its output y are FP32 channel-major planes
 // [c][y][x] (the data kernels' layout).  Everything in between -- hidden
-// activations and the gradients flowing back through them -- is stored as BF16
-// pixel-major rows [y][x][c] of CS = channels rounded up to 16 (the padding
-// stays zero): the values the tensor cores multiply are BF16 anyway, so this
-// changes no result and halves the bytes.
+// activations and the gradients flowing back through them -- is stored in BF16,
+// channel-blocked: [c / 8][y][x][c % 8] with CS = channels rounded up to 16
+// (the padding stays zero).  The values the tensor cores multiply are BF16
+// anyway, so this changes no result and halves the bytes; each block of 8
+// channels is a dense [y][x] image of 16-byte pixels, which is both what the
+// tensor-core descriptors read and what a TMA box copies in long contiguous
+// rows.
 //
 // Weight gradients (k_wgrad_mma) run on the warp-level tensor-core
 // instructions, mma.sync m16n8k16 with BF16 operands and FP32 accumulation: a
 // block stages a tile of the layer input and of the gradient in shared memory
 // as [pixel][channel] rows of CS + 8 BF16 (the 8 extra keep the 16-byte
-// ldmatrix rows of consecutive pixels on different banks); pixel-major inputs
-// arrive by 16-byte cp.async (zero-filled outside the image), channel-major
+// ldmatrix rows of consecutive pixels on different banks); channel-blocked
+// inputs arrive by 16-byte cp.async (zero-filled outside the image), channel-major
 // FP32 inputs are read, rounded and stored by the threads.  The convolutions
 // themselves (forward and input gradient) run on tcgen05 (k_conv_tc, below).
 constexpr int CT_H = 8;              // weight-gradient tile rows
@@ -68,23 +73,23 @@ template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.as
 
 // Stage rows [y0, y0 + ROWS) x columns [x0, x0 + COLS) of an input into
 // shared-memory rows of PS BF16 (channels 0..CP-1), zero outside the image.
-// Pixel-major BF16 source (nhwc, CP channels per pixel): 16-byte cp.async
+// Channel-blocked BF16 source (blk, CP channels): 16-byte cp.async
 // copies, committed as one group by the caller.  Channel-major FP32 source
 // (planes [0, c)): loads go out in batches of SB element pairs per thread
 // before any of them is stored, so a thread waits for one memory latency per
 // batch, not per pair.
 template <int CP, int PS, int ROWS, int COLS, int SB = 8>
-__device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int nhwc, int c, int H, int W, int y0,
+__device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int blk, int c, int H, int W, int y0,
                                            int x0, __nv_bfloat16* dst) {
-  if (nhwc) {
+  if (blk) {
     const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(srcv);
     constexpr int CH = CP / 8, N = ROWS * COLS * CH;
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-      const int ch = t % CH, pix = t / CH;
+      const int pix = t % (ROWS * COLS), ch = t / (ROWS * COLS);   // consecutive threads: consecutive pixels
       const int yy = pix / COLS, xx = pix - yy * COLS;
       const int gy = y0 + yy, gx = x0 + xx;
       const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-      const __nv_bfloat16* s = in ? src + ((size_t)gy * W + gx) * CP + 8 * ch : src;
+      const __nv_bfloat16* s = in ? src + ((size_t)ch * H * W + (size_t)gy * W + gx) * 8 : src;
       cp_async16(dst + (size_t)pix * PS + 8 * ch, s, in ? 16 : 0);
     }
     return;
@@ -130,10 +135,13 @@ __device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int nh
 // between the two 8-channel halves of an instruction's K = 16, SBO = byte
 // distance between groups of 8 rows):
 //   A (input tile, TC_R + 2 rows x TC_SW columns with a one-pixel halo):
-//     [channel / 8][pixel][channel % 8], planes TC_PA bytes apart, so the 128
-//     pixels x 16 channels of staged row t shifted by kx start at pixel
-//     t * TC_SW + kx of planes 2j, 2j + 1 (LBO = TC_PA, SBO = 128): a tap shift
-//     is a shift of the descriptor's start address.
+//     [channel / 8][pixel][channel % 8], planes TC_BOX bytes apart, so the
+//     128 pixels x 16 channels of staged row t shifted by kx start at pixel
+//     t * TC_SW + kx of planes 2j, 2j + 1 (LBO = TC_BOX, SBO = 128): a tap
+//     shift is a shift of the descriptor's start address.  The tile is one
+//     TMA box of the channel-blocked input (8 channels x TC_SW columns x
+//     TC_R + 2 rows x CP / 8 blocks, zero-filled outside the image): each of its
+//     rows is TC_SW x 16 contiguous bytes in global memory.
 //   B (weights): [kx][channel / 8][n][channel % 8] with n = (2 - ky) NO + o:
 //     the three row taps of one column tap stacked along N (LBO = 3 NO * 16,
 //     SBO = 128).
@@ -141,30 +149,39 @@ __device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int nh
 // weights of the row taps ky that map it to output rows of the tile (output
 // row t - ky, 0 <= t - ky < TC_R): N = NO, 2 NO or 3 NO columns, written to the
 // TMEM columns of output rows t - ky_hi .. t - ky_lo (lane p = output pixel p,
-// column r * NO + o = channel o of output row r), which are zeroed before the
+// column r * NO + o = channel o of output row r), which are zero before the
 // tile.  Per tile that is (TC_R + 2) x 3 x CP / 16 instructions of up to
 // 3 NO columns instead of TC_R x 9 x CP / 16 of NO columns: each staged row
-// shift is read from shared memory once for its three row taps.  One thread
-// issues them and commits them to an mbarrier; the four warps then read their
-// 32 lanes back (tcgen05.ld 32x32b) and write bias + ReLU (+ mask) pixel by
-// pixel: pixel-major BF16 rows (16-byte stores) or channel-major FP32 planes
-// (coalesced along x).
+// shift is read from shared memory once for its three row taps.
+//
+// Pipeline (one persistent block per SM, warp-specialised): warp 4 loads
+// input tiles by TMA into a ring of TC_STAGES(CP) shared-memory stages (full /
+// empty mbarriers); warp 5 issues each tile's instructions into one of two
+// TMEM accumulator buffers and commits them to the stage's empty barrier and
+// the buffer's full barrier; warps 0-3 read their 32 lanes of a full buffer
+// back (tcgen05.ld 32x32b), write bias + ReLU (+ mask) pixel by pixel --
+// channel-blocked BF16 (16-byte stores) or channel-major FP32 planes, both
+// coalesced along x -- clear the buffer and release it.  Loads, tensor-core
+// work and write-back of different tiles overlap.
 constexpr int TC_R = 4;                         // output rows per tile
 constexpr int TC_W = 128;                       // output columns per tile: the instruction's M
 constexpr int TC_SW = TC_W + 2;                 // staged columns
 constexpr int TC_SPIX = (TC_R + 2) * TC_SW;     // staged pixels
-// bytes between two 8-channel planes of the staged tile: the plane size rounded
-// up to 128 bytes, plus 16, so the 16-byte chunks of one pixel in consecutive
-// planes fall on different banks when the copies land
-constexpr int TC_PA = (TC_SPIX * 16 + 127) / 128 * 128 + 16;
-constexpr int TC_THREADS = 128;
+constexpr int TC_BOX = TC_SPIX * 16;            // bytes of one 8-channel plane of the staged tile
+constexpr int TC_THREADS = 192;                 // 4 write-back warps, a TMA warp, an MMA warp
 
-__host__ __device__ constexpr int tc_cols(int no) {   // TMEM columns to allocate: a power of 2 >= 32
-  return TC_R * no <= 32 ? 32 : TC_R * no <= 64 ? 64 : TC_R * no <= 128 ? 128 : 256;
+__host__ __device__ constexpr int tc_stages(int cp) { return cp == 48 ? 2 : 3; }
+__host__ __device__ constexpr int tc_bufcols(int no) { return TC_R * no; }   // TMEM columns of one buffer
+__host__ __device__ constexpr int tc_cols(int no) {   // TMEM columns to allocate: a power of 2 >= 2 buffers
+  return 2 * TC_R * no <= 32 ? 32 : 2 * TC_R * no <= 64 ? 64 : 2 * TC_R * no <= 128 ? 128
+         : 2 * TC_R * no <= 256 ? 256 : 512;
 }
 __host__ __device__ constexpr int tc_smem_used(int cp, int no) {
-  return cp / 8 * TC_PA + 9 * cp * no * 2 + 256 + 16;   // A, B, bias, mbarrier + TMEM address
+  // alignment slack, stages, B, bias, 2 S + 4 mbarriers, TMEM address + abort flag
+  return 128 + tc_stages(cp) * (cp / 8) * TC_BOX + 9 * cp * no * 2 + 256 + (2 * tc_stages(cp) + 4) * 8 + 16;
 }
+
+static_assert(TC_BOX % 64 == 0, "stages of an even number of planes stay 128-byte aligned");
 
 // Shared-memory matrix descriptor: start address, LBO and SBO in 16-byte units,
 // descriptor version 1 (bits 46-47), no swizzle, base offset 0.
@@ -193,8 +210,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 // Wait until the mbarrier has completed the phase of the given parity; gives up
-// after about two seconds (returns false).
-__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
+// after about two seconds, or as soon as *abort is set (returns false).
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, const volatile int* abort) {
   const unsigned long long t0 = global_ns();
   for (;;) {
     unsigned ok;
@@ -204,8 +221,24 @@ __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (*abort || global_ns() - t0 > 2000000000ull) return false;
   }
+}
+__device__ __forceinline__ void mbar_arrive(unsigned addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes) : "memory");
+}
+// TMA: box at coordinates (c0, c1, c2, c3) of a 4-D tensor map into shared
+// memory, completion counted on the mbarrier in bytes.
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      : "memory");
 }
 // The NO consecutive FP32 columns (16, 32 or 48) of this thread's TMEM lane,
 // waited for in the same statement (the registers are only valid after
@@ -260,28 +293,34 @@ __device__ __forceinline__ void tmem_zero32(unsigned taddr) {
 // bias[o] + sum_c sum_k B(o, c, k) in[c][y + ky - 1][x + kx - 1], optional
 // ReLU, optional mask (out = 0 where mask <= 0).  transpose = 0: B(o, c, k) =
 // w[o][c][k]; transpose = 1: B(o, c, k) = w[c][o][8 - k] (the transposed,
-// flipped kernel mapping dL/d(out) of that layer to dL/d(in)).  in: pixel-major
-// BF16 with CP channels per pixel (in_nhwc) or channel-major FP32 planes (cin
-// of them); out: pixel-major BF16 with NO channels per pixel (out_nhwc) or
-// channel-major FP32 planes (cout).  Persistent blocks of 128 threads take
-// tiles of TC_R x TC_W output pixels.  A wait that does not end within about
-// two seconds sets *err and ends the block (after a second bounded wait for
-// its instructions in flight and the release of its TMEM).
+// flipped kernel mapping dL/d(out) of that layer to dL/d(in)).  in: the
+// channel-blocked BF16 tensor (CP channels) behind the tensor map; out:
+// channel-blocked BF16 with NO channels (out_blk) or channel-major FP32
+// planes (cout); mask: channel-blocked BF16 with NO channels.  Persistent blocks (one per SM) take tiles of TC_R x TC_W
+// output pixels in the pipeline described above.  Every wait is bounded
+// (about two seconds); one that runs out sets *err and a shared abort flag
+// that ends the other roles' waits, and the block releases its TMEM and ends.
 template <int CP, int NO>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_conv_tc(const void* __restrict__ in, int in_nhwc, int cin, int H, int W, const __nv_bfloat16* __restrict__ w,
+    k_conv_tc(const __grid_constant__ CUtensorMap map, int cin, int H, int W, const __nv_bfloat16* __restrict__ w,
               int transpose, const float* __restrict__ bias, int cout, int relu,
-              const __nv_bfloat16* __restrict__ mask, void* __restrict__ out, int out_nhwc, int ntx, int ntiles,
+              const __nv_bfloat16* __restrict__ mask, void* __restrict__ out, int out_blk, int ntx, int ntiles,
               int* __restrict__ err) {
-  constexpr int C8 = CP / 8;
-  constexpr int A_BYTES = C8 * TC_PA, B_BYTES = 9 * CP * NO * 2;
+  constexpr int C8 = CP / 8, S = tc_stages(CP);
+  constexpr int A_STAGE = C8 * TC_BOX, B_BYTES = 9 * CP * NO * 2, TB = tc_bufcols(NO);
   constexpr unsigned NCOL = tc_cols(NO);
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  unsigned char* sA = sm_raw;
-  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(sm_raw + A_BYTES);
-  float* sBias = reinterpret_cast<float*>(sm_raw + A_BYTES + B_BYTES);
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm_raw + A_BYTES + B_BYTES + 256);
-  unsigned* tslot = reinterpret_cast<unsigned*>(sm_raw + A_BYTES + B_BYTES + 264);
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  const unsigned raw = smem_u32(tc_raw), base = (raw + 127) & ~127u;
+  unsigned char* g0 = tc_raw + (base - raw);                 // 128-byte aligned
+  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(g0 + S * A_STAGE);
+  float* sBias = reinterpret_cast<float*>(g0 + S * A_STAGE + B_BYTES);
+  const unsigned bars = base + S * A_STAGE + B_BYTES + 256;  // full[S], empty[S], tfull[2], tempty[2]
+  unsigned* tslot = reinterpret_cast<unsigned*>(g0 + S * A_STAGE + B_BYTES + 256 + (2 * S + 4) * 8);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  auto full = [&](int st) { return bars + 8 * st; };
+  auto empty = [&](int st) { return bars + 8 * (S + st); };
+  auto tfull = [&](int b) { return bars + 8 * (2 * S + b); };
+  auto tempty = [&](int b) { return bars + 8 * (2 * S + 2 + b); };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // weights once per block: sB[kx][c / 8][(2 - ky) NO + o][c % 8] = B(o, c, 3 ky + kx),
@@ -295,12 +334,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     sB[((size_t)(kx * C8 + c / 8) * (3 * NO) + (2 - ky) * NO + o) * 8 + (c & 7)] = __float2bfloat16_rn(v);
   }
   for (int o = tid; o < NO; o += TC_THREADS) sBias[o] = (bias && o < cout) ? bias[o] : 0.f;
-  const unsigned mb = smem_u32(mbar);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // the weights, for the tensor cores
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    for (int st = 0; st < S; st++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(st)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(st)) : "memory");
+    }
+    for (int b = 0; b < 2; b++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tfull(b)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(tempty(b)) : "memory");
+    }
+    *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
                  "r"(NCOL)
                  : "memory");
@@ -310,162 +357,160 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = *tslot;
-  const unsigned tlane = tmem + ((unsigned)(32 * warp) << 16);   // this warp's 32 lanes
-  // accumulators of the first tile start at zero (each warp clears its lanes)
+  if (warp < 4) {   // both accumulator buffers start at zero (each warp clears its lanes)
+    const unsigned tl = tmem + ((unsigned)(32 * warp) << 16);
 #pragma unroll
-  for (int c = 0; c < TC_R * NO; c += 32) tmem_zero32(tlane + c);
-  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-  const unsigned aBase = smem_u32(sA), bBase = smem_u32(sB);
-  const size_t hw = (size_t)H * W;
-  // input tile rows ty0 - 1 .. ty0 + TC_R and columns tx0 - 1 .. tx0 + TC_W
-  // (zero outside the image): pixel-major BF16 by 16-byte cp.async copies
-  // (committed, not waited for), channel-major FP32 by the threads
-  auto stage_nhwc = [&](int tile) {
-    const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
-    const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(in);
-    for (int e = tid; e < TC_SPIX * C8; e += TC_THREADS) {
-      const int ch = e % C8, pix = e / C8;
-      const int yy = pix / TC_SW, xx = pix - yy * TC_SW;
-      const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
-      const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
-      const __nv_bfloat16* s = ok ? src + ((size_t)gy * W + gx) * CP + 8 * ch : src;
-      cp_async16(sA + ch * TC_PA + pix * 16, s, ok ? 16 : 0);
-    }
-    cp_commit();
-  };
-  auto stage_nchw = [&](int tile) {
-    const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
-    const float* src = static_cast<const float*>(in);
-    for (int pix = tid; pix < TC_SPIX; pix += TC_THREADS) {
-      const int yy = pix / TC_SW, xx = pix - yy * TC_SW;
-      const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
-      const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
-      const size_t o = ok ? (size_t)gy * W + gx : 0;
-#pragma unroll
-      for (int ch = 0; ch < C8; ch++) {
-        float v[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) v[i] = (ok && 8 * ch + i < cin) ? __ldg(src + (size_t)(8 * ch + i) * hw + o) : 0.f;
-        uint4 u;
-        u.x = pack_bf16(v[0], v[1]);
-        u.y = pack_bf16(v[2], v[3]);
-        u.z = pack_bf16(v[4], v[5]);
-        u.w = pack_bf16(v[6], v[7]);
-        *reinterpret_cast<uint4*>(sA + ch * TC_PA + pix * 16) = u;
-      }
-    }
-  };
-  if (in_nhwc && (int)blockIdx.x < ntiles) stage_nhwc(blockIdx.x);
-  bool failed = false;
-  unsigned phase = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
-    // this tile's input: copies issued during the previous tile's epilogue (or
-    // above), or the FP32 planes read now
-    if (in_nhwc)
-      cp_wait<0>();
-    else
-      stage_nchw(tile);
-    // the threads' shared-memory writes become visible to the tensor cores
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll 1
-      for (int t = 0; t < TC_R + 2; t++) {
-        // row taps that map staged row t to an output row of the tile
-        const int ky_lo = t - (TC_R - 1) > 0 ? t - (TC_R - 1) : 0, ky_hi = t < 2 ? t : 2;
-        const unsigned id = tc_idesc((ky_hi - ky_lo + 1) * NO);
-        const unsigned d = tmem + (t - ky_hi) * NO;
-        const unsigned boff = (2 - ky_hi) * NO / 8 * 128;
-#pragma unroll
-        for (int kx = 0; kx < 3; kx++)
-#pragma unroll
-          for (int j = 0; j < CP / 16; j++) {
-            const unsigned long long ad = tc_desc(aBase + 2 * j * TC_PA + (t * TC_SW + kx) * 16, TC_PA, 128);
-            const unsigned long long bd =
-                tc_desc(bBase + (kx * C8 + 2 * j) * (3 * NO) * 16 + boff, 3 * NO * 16, 128);
-            tc_mma(d, ad, bd, id, 1);
-          }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
-                   : "memory");
-    }
-    const bool done = mbar_wait(mb, phase);
-    if (__syncthreads_or(!done)) {
-      failed = true;
-      break;
-    }
-    phase ^= 1;
-    // the instructions have read the input tile: the next tile's copies go out
-    // now and land while this tile's accumulators are written back
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    if (in_nhwc && tile + (int)gridDim.x < ntiles) stage_nhwc(tile + gridDim.x);
-    tc_fence_after();
-    // epilogue: thread = output pixel x of each tile row
-    const int x = tx0 + 32 * warp + lane;
-#pragma unroll 1
-    for (int r = 0; r < TC_R; r++) {
-      float v[NO];
-      tmem_ld<NO>(tlane + r * NO, v);
-      const int y = ty0 + r;
-      if (y >= H || x >= W) continue;
-      const size_t pix = (size_t)y * W + x;
-#pragma unroll
-      for (int o = 0; o < NO; o++) {
-        v[o] += sBias[o];
-        if (relu) v[o] = v[o] > 0.f ? v[o] : 0.f;
-      }
-      if (mask) {
-        const uint4* mk = reinterpret_cast<const uint4*>(mask + pix * NO);
-#pragma unroll
-        for (int c = 0; c < NO / 8; c++) {
-          const uint4 m4 = __ldg(mk + c);
-          const unsigned mw[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-          for (int i = 0; i < 4; i++) {
-            const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[i]);
-            if (!(__low2float(m2) > 0.f)) v[8 * c + 2 * i] = 0.f;
-            if (!(__high2float(m2) > 0.f)) v[8 * c + 2 * i + 1] = 0.f;
-          }
-        }
-      }
-      if (out_nhwc) {
-        uint4* op = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + pix * NO);
-#pragma unroll
-        for (int c = 0; c < NO / 8; c++) {
-          uint4 u;
-          u.x = pack_bf16(v[8 * c], v[8 * c + 1]);
-          u.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
-          u.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
-          u.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
-          op[c] = u;
-        }
-      } else {
-        float* of = static_cast<float*>(out);
-#pragma unroll
-        for (int o = 0; o < NO; o++)
-          if (o < cout) of[(size_t)o * hw + pix] = v[o];
-      }
-    }
-    // clear this warp's accumulators for the next tile; the reads and these
-    // stores are done before the next tile's instructions
-#pragma unroll
-    for (int c = 0; c < TC_R * NO; c += 32) tmem_zero32(tlane + c);
+    for (int c = 0; c < 2 * TB; c += 32) tmem_zero32(tl + c);
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
   }
-  if (failed) {
-    if (tid == 0) atomicExch(err, 1);
-    mbar_wait(mb, phase);   // the instructions in flight, once more bounded
-  }
-  cp_wait<0>();
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  tc_fence_after();
+
+  bool failed = false;
+  if (warp == 4) {
+    // ---- TMA producer
+    if (lane == 0) {
+      int i = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, i++) {
+        const int st = i % S;
+        if (!mbar_wait(empty(st), ((i / S) & 1) ^ 1, abort)) { failed = true; break; }
+        const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
+        mbar_expect_tx(full(st), A_STAGE);
+        tma_load_4d(base + st * A_STAGE, &map, 0, tx0 - 1, ty0 - 1, 0, full(st));
+      }
+    }
+  } else if (warp == 5) {
+    // ---- tensor-core issue
+    if (lane == 0) {
+      int i = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, i++) {
+        const int st = i % S, b = i & 1;
+        if (!mbar_wait(full(st), (i / S) & 1, abort) || !mbar_wait(tempty(b), ((i >> 1) & 1) ^ 1, abort)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        const unsigned aBase = base + st * A_STAGE, bBase = smem_u32(sB), dBase = tmem + b * TB;
+#pragma unroll 1
+        for (int t = 0; t < TC_R + 2; t++) {
+          // row taps that map staged row t to an output row of the tile
+          const int ky_lo = t - (TC_R - 1) > 0 ? t - (TC_R - 1) : 0, ky_hi = t < 2 ? t : 2;
+          const unsigned id = tc_idesc((ky_hi - ky_lo + 1) * NO);
+          const unsigned d = dBase + (t - ky_hi) * NO;
+          const unsigned boff = (2 - ky_hi) * NO / 8 * 128;
+#pragma unroll
+          for (int kx = 0; kx < 3; kx++)
+#pragma unroll
+            for (int j = 0; j < CP / 16; j++) {
+              const unsigned long long ad =
+                  tc_desc(aBase + 2 * j * TC_BOX + (t * TC_SW + kx) * 16, TC_BOX, 128);
+              const unsigned long long bd =
+                  tc_desc(bBase + (kx * C8 + 2 * j) * (3 * NO) * 16 + boff, 3 * NO * 16, 128);
+              tc_mma(d, ad, bd, id, 1);
+            }
+        }
+        // the stage is free and the buffer full once these instructions complete
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         empty(st))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         tfull(b))
+                     : "memory");
+      }
+    }
+  } else {
+    // ---- write-back: warp w owns TMEM lanes 32 w .. 32 w + 31 = output pixels
+    const unsigned tl = tmem + ((unsigned)(32 * warp) << 16);
+    const size_t hw = (size_t)H * W;
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, i++) {
+      const int b = i & 1;
+      const int ok = __shfl_sync(0xffffffffu, lane == 0 ? (int)mbar_wait(tfull(b), (i >> 1) & 1, abort) : 0, 0);
+      if (!ok) { failed = true; break; }
+      tc_fence_after();
+      const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
+      const int x = tx0 + 32 * warp + lane;
+#pragma unroll 1
+      for (int r = 0; r < TC_R; r++) {
+        float v[NO];
+        tmem_ld<NO>(tl + b * TB + r * NO, v);
+        const int y = ty0 + r;
+        if (y >= H || x >= W) continue;
+        const size_t pix = (size_t)y * W + x;
+#pragma unroll
+        for (int o = 0; o < NO; o++) {
+          v[o] += sBias[o];
+          if (relu) v[o] = v[o] > 0.f ? v[o] : 0.f;
+        }
+        if (mask) {
+          const uint4* mk = reinterpret_cast<const uint4*>(mask) + pix;
+#pragma unroll
+          for (int c = 0; c < NO / 8; c++) {
+            const uint4 m4 = __ldg(mk + c * hw);
+            const unsigned mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[q]);
+              if (!(__low2float(m2) > 0.f)) v[8 * c + 2 * q] = 0.f;
+              if (!(__high2float(m2) > 0.f)) v[8 * c + 2 * q + 1] = 0.f;
+            }
+          }
+        }
+        if (out_blk) {
+          uint4* op = reinterpret_cast<uint4*>(out) + pix;
+#pragma unroll
+          for (int c = 0; c < NO / 8; c++) {
+            uint4 u;
+            u.x = pack_bf16(v[8 * c], v[8 * c + 1]);
+            u.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+            u.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+            u.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+            op[c * hw] = u;
+          }
+        } else {
+          float* of = static_cast<float*>(out);
+#pragma unroll
+          for (int o = 0; o < NO; o++)
+            if (o < cout) of[(size_t)o * hw + pix] = v[o];
+        }
+      }
+      // clear the buffer for its next tile and hand it back
+#pragma unroll
+      for (int c = 0; c < TB; c += 32) tmem_zero32(tl + b * TB + c);
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(b));
+    }
+  }
+  if (failed) {
+    *abort = 1;
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
+  }
+}
+
+// FP32 channel-major planes (cin) -> channel-blocked BF16 with cp channels
+// (zero-padded): the network input in the layout the convolutions load.
+__global__ void k_to_blk(const float* __restrict__ x, int cin, long hw, int cp, __nv_bfloat16* __restrict__ y) {
+  const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= hw) return;
+  for (int c0 = 0; c0 < cp; c0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = c0 + i < cin ? x[(size_t)(c0 + i) * hw + p] : 0.f;
+    uint4 u;
+    u.x = pack_bf16(v[0], v[1]);
+    u.y = pack_bf16(v[2], v[3]);
+    u.z = pack_bf16(v[4], v[5]);
+    u.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(y + ((size_t)(c0 / 8) * hw + p) * 8) = u;
   }
 }
 
@@ -478,8 +523,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // order, and the partials of the blocks are summed in block order by
 // k_sum_tiles, so the result does not depend on the schedule.
 template <int OP, int CP>
-__global__ void __launch_bounds__(288, 2) k_wgrad_mma(const void* __restrict__ in, int in_nhwc, int cin, int H,
-                                                      int W, const void* __restrict__ g, int g_nhwc, int cout,
+__global__ void __launch_bounds__(288, 2) k_wgrad_mma(const void* __restrict__ in, int in_blk, int cin, int H,
+                                                      int W, const void* __restrict__ g, int g_blk, int cout,
                                                       float* __restrict__ part, int ntx, int ntiles) {
   constexpr int PSI = CP + 8, PSG = OP + 8;
   constexpr int MT = OP / 16, NT = CP / 8;
@@ -498,8 +543,8 @@ __global__ void __launch_bounds__(288, 2) k_wgrad_mma(const void* __restrict__ i
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ty0 = (tile / ntx) * CT_H, tx0 = (tile % ntx) * CT_W;
     __syncthreads();
-    stage_tile<CP, PSI, CT_H + 2, CT_W + 2, 4>(in, in_nhwc, cin, H, W, ty0 - 1, tx0 - 1, sI);
-    stage_tile<OP, PSG, CT_H, CT_W, 4>(g, g_nhwc, cout, H, W, ty0, tx0, sG);
+    stage_tile<CP, PSI, CT_H + 2, CT_W + 2, 4>(in, in_blk, cin, H, W, ty0 - 1, tx0 - 1, sI);
+    stage_tile<OP, PSG, CT_H, CT_W, 4>(g, g_blk, cout, H, W, ty0, tx0, sG);
     cp_commit();
     cp_wait<0>();
     __syncthreads();
@@ -544,28 +589,40 @@ __global__ void __launch_bounds__(288, 2) k_wgrad_mma(const void* __restrict__ i
       }
 }
 
-// Bias gradient partials of a hidden layer: part[chunk][o] = sum of g[p][o]
+// Bias gradient partials of a hidden layer: part[chunk][o] = sum of g[o][p]
 // over the pixels of chunk blockIdx.x (gridDim.x contiguous ranges), in FP32, in
-// a fixed order; k_sum_chunks adds the chunks.  g: pixel-major BF16 with cs
-// channels per pixel; thread t reads channel t % cs of every (blockDim / cs)-th
-// pixel, so a warp reads consecutive bytes; the threads of one channel are then
-// summed in thread order.
+// a fixed order; k_sum_chunks adds the chunks.  g: channel-blocked BF16 with cs
+// channels; thread t reads the 16-byte pixel (t % 32 + 32 i) of channel block
+// t / 32 (a warp reads 512 contiguous bytes), sums its 8 channels separately,
+// and the 32 lanes of each block are then summed in lane order.
 constexpr int BG_CHUNKS = 1024;
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ gb, int cs, long hw, int cout,
-                            float* __restrict__ part) {
-  __shared__ float red[256];
+__global__ void __launch_bounds__(192) k_bias_grad(const __nv_bfloat16* __restrict__ gb, int cs, long hw, int cout,
+                                                   float* __restrict__ part) {
+  __shared__ float red[6][32][9];
   const long p0 = hw * blockIdx.x / gridDim.x, p1 = hw * (blockIdx.x + 1) / gridDim.x;
-  const int ppi = blockDim.x / cs;                     // pixels per pass
-  const int o = threadIdx.x % cs, pk = threadIdx.x / cs;
-  float s = 0.f;
-  if (pk < ppi)
-    for (long p = p0 + pk; p < p1; p += ppi) s += (float)gb[(size_t)p * cs + o];
-  red[threadIdx.x] = s;
+  const int lane = threadIdx.x & 31, cb = threadIdx.x >> 5;   // channel block of this warp
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (cb < cs / 8) {
+    const uint4* src = reinterpret_cast<const uint4*>(gb) + (size_t)cb * hw;
+    for (long p = p0 + lane; p < p1; p += 32) {
+      const uint4 u = src[p];
+      const unsigned w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162*>(&w4[q]);
+        s[2 * q] += __low2float(b2);
+        s[2 * q + 1] += __high2float(b2);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++) red[cb][lane][q] = s[q];
+  }
   __syncthreads();
   if (threadIdx.x < cout) {
+    const int o = threadIdx.x;
     float t = 0.f;
-    for (int k = 0; k < ppi; k++) t += red[k * cs + threadIdx.x];
-    part[(size_t)blockIdx.x * cout + threadIdx.x] = t;
+    for (int k = 0; k < 32; k++) t += red[o / 8][k][o % 8];
+    part[(size_t)blockIdx.x * cout + o] = t;
   }
 }
 
@@ -613,14 +670,14 @@ __global__ void __launch_bounds__(256) k_sum_tiles(const float* __restrict__ par
 // and fine rows r y + sy of field f -- for the coarse rows y = k, k +
 // LOSS_CHUNKS, ...: a thread reads the r output planes at its pixel and r
 // consecutive target values (one 16-byte load when r = 4).  dL/dy goes out
-// pixel-major BF16 with cs channels per pixel, the operand layout of the
-// backward convolutions (which multiply it in BF16); the bias partials use the
-// FP32 values.  Loss and bias partials per block are summed in a fixed order
+// channel-blocked BF16 (cs channels), the operand layout of the backward
+// convolutions (which multiply it in BF16); the bias partials use the FP32
+// values.  Loss and bias partials per block are summed in a fixed order
 // by k_sum_loss and k_sum_chunks.
 constexpr int LOSS_CHUNKS = 64, LOSS_MAXR = 8;
 template <bool R4>
 __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ yv, const float* __restrict__ tgt, int H,
-                                              int W, int r, int cs, const float* __restrict__ fw,
+                                              int W, int r, const float* __restrict__ fw,
                                               __nv_bfloat16* __restrict__ gy, double* __restrict__ lpart,
                                               float* __restrict__ bpart, int cout) {
   __shared__ float red[LOSS_MAXR + 1][256];
@@ -648,14 +705,14 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ yv, cons
         uint2 pk;
         pk.x = pack_bf16(gv[0], gv[1]);
         pk.y = pack_bf16(gv[2], gv[3]);
-        *reinterpret_cast<uint2*>(gy + p * cs + c0) = pk;
+        *reinterpret_cast<uint2*>(gy + ((size_t)(c0 / 8) * hw + p) * 8 + (c0 & 7)) = pk;
       } else {
 #pragma unroll
         for (int j = 0; j < LOSS_MAXR; j++) {
           if (j < r) {
             const float d = yv[(size_t)(c0 + j) * hw + p] - trow[(size_t)x * r + j];
             const float gv = 2.f * wf * d * inv;
-            gy[p * cs + c0 + j] = __float2bfloat16_rn(gv);
+            gy[((size_t)((c0 + j) / 8) * hw + p) * 8 + ((c0 + j) & 7)] = __float2bfloat16_rn(gv);
             bs[j] += gv;
             l += wf * d * d * inv;
           }
@@ -796,8 +853,9 @@ static WgradFn wgrad_fn(int op, int cp) {
   return nullptr;
 }
 static size_t wgrad_smem(int op, int cp) { return ((size_t)CT_PIX * (cp + 8) + (size_t)CT_H * CT_W * (op + 8)) * 2; }
-typedef void (*TcFn)(const void*, int, int, int, int, const __nv_bfloat16*, int, const float*, int, int,
+typedef void (*TcFn)(const CUtensorMap, int, int, int, const __nv_bfloat16*, int, const float*, int, int,
                      const __nv_bfloat16*, void*, int, int, int, int*);
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encode = nullptr;   // driver entry point
 static TcFn tc_fn(int cp, int no) {
 #define TF(C, N) if (cp == C && no == N) return k_conv_tc<C, N>;
   TF(16, 16) TF(16, 32) TF(16, 48) TF(32, 16) TF(32, 32) TF(32, 48) TF(48, 16) TF(48, 32) TF(48, 48)
@@ -819,6 +877,15 @@ static int set_smem_attrs() {
         return -3;
   // resident blocks of a tensor-core convolution = what the SM's shared memory
   // holds; the request is padded until that is at most 512 / (its TMEM columns)
+  if (!tma_encode) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void**>(&tma_encode), 12000,
+                                         cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !tma_encode) {
+      tma_encode = nullptr;
+      return -3;
+    }
+  }
   int dev = 0, smax = 0, ssm = 0, sres = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
@@ -853,11 +920,12 @@ struct lc_net {
   long np;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16* pb = nullptr;
-  // act[l]: output of layer l -- pixel-major BF16 rows of pad16(co[l]) channels
+  // act[l]: output of layer l -- channel-blocked BF16 with pad16(co[l]) channels
   // for the hidden layers, channel-major FP32 for the last one
   std::vector<void*> act;
-  __nv_bfloat16* gh[2] = {nullptr, nullptr};   // pixel-major BF16 gradients of hidden outputs
-  __nv_bfloat16* ga = nullptr;  // dL/dy, pixel-major BF16 with pad16(cout) channels (padding zero)
+  __nv_bfloat16* gh[2] = {nullptr, nullptr};   // channel-blocked BF16 gradients of hidden outputs
+  __nv_bfloat16* ga = nullptr;  // dL/dy, channel-blocked BF16 with pad16(cout) channels (padding zero)
+  __nv_bfloat16* x16 = nullptr; // the network input, channel-blocked BF16 with pad16(cin) channels
   float *part = nullptr, *bpart = nullptr;
   double *lpart = nullptr, *lsum = nullptr;
   float* fw = nullptr;          // loss field weights (device copy)
@@ -914,6 +982,7 @@ int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned lon
   for (int l = 0; l < depth; l++)
     n->act.push_back(dmalloc(n, l < depth - 1 ? (size_t)pad16(n->co[l]) * max_hw * 2 : (size_t)n->co[l] * max_hw * 4));
   n->ga = (__nv_bfloat16*)dmalloc(n, (size_t)pad16(cout) * max_hw * 2);
+  n->x16 = (__nv_bfloat16*)dmalloc(n, (size_t)pad16(cin) * max_hw * 2);
   for (int k = 0; k < 2; k++) n->gh[k] = (__nv_bfloat16*)dmalloc(n, (size_t)pad16(width) * max_hw * 2);
   n->part = (float*)dmalloc(n, (size_t)n->max_tiles * n->max_layer * 4);
   n->lpart = (double*)dmalloc(n, (size_t)LOSS_CHUNKS * cout * 8);
@@ -922,7 +991,7 @@ int lc_create(int cin, int width, int depth, int cout, long max_hw, unsigned lon
   n->fw = (float*)dmalloc(n, 8 * sizeof(float));
   n->err = (int*)dmalloc(n, sizeof(int));
   bool ok = n->p && n->g && n->m && n->v && n->pb && n->ga && n->gh[0] && n->gh[1] && n->part && n->bpart &&
-            n->lpart && n->lsum && n->fw && n->err;
+            n->lpart && n->lsum && n->fw && n->err && n->x16;
   for (auto a : n->act) ok = ok && a;
   if (!ok) { lc_destroy(n); return -2; }
   if (cudaMemset(n->ga, 0, (size_t)pad16(cout) * max_hw * 2) != cudaSuccess ||
@@ -975,30 +1044,49 @@ int lc_set_params(lc_net* n, const float* host, long count) {
 }
 
 // 3x3 convolution of `in` (cin channels) into `out` (cout channels) on the
-// tensor cores with the BF16 weights w (transpose: see k_conv_tc).
-static void conv(lc_net* n, const void* in, int in_nhwc, int cin, int H, int W, const __nv_bfloat16* w,
-                 int transpose, const float* bias, int cout, int relu, const __nv_bfloat16* mask, void* out,
-                 int out_nhwc) {
+// tensor cores with the BF16 weights w (transpose: see k_conv_tc).  A
+// channel-major FP32 input (in_blk = 0, the network input) is first rounded
+// into the channel-blocked BF16 buffer the TMA loads read.
+static int conv(lc_net* n, const void* in, int in_blk, int cin, int H, int W, const __nv_bfloat16* w,
+                int transpose, const float* bias, int cout, int relu, const __nv_bfloat16* mask, void* out,
+                int out_blk) {
   const int cp = pad16(cin), no = pad16(cout);
+  const long hw = (long)H * W;
+  if (!in_blk) {
+    k_to_blk<<<nblk(hw, 256), 256, 0, n->st>>>(static_cast<const float*>(in), cin, hw, cp, n->x16);
+    in = n->x16;
+  }
+  // the input as a 4-D tensor (8 channels, W, H, cp / 8 blocks) of 16-byte
+  // pixels; boxes of 8 x TC_SW x (TC_R + 2) x cp / 8, zero fill outside
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(cp / 8)};
+  const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)hw * 16};
+  const cuuint32_t box[4] = {8, TC_SW, TC_R + 2, (cuuint32_t)(cp / 8)}, estr[4] = {1, 1, 1, 1};
+  if (tma_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return -3;
   const TcCfg& c = tc_cfg[cp / 16 - 1][no / 16 - 1];
   const int ntx = (W + TC_W - 1) / TC_W, ntiles = ntx * ((H + TC_R - 1) / TC_R);
   const int nb = std::min(ntiles, c.per_sm * n->nsm);
-  tc_fn(cp, no)<<<nb, TC_THREADS, c.smem, n->st>>>(in, in_nhwc, cin, H, W, w, transpose, bias, cout, relu, mask,
-                                                    out, out_nhwc, ntx, ntiles, n->err);
+  tc_fn(cp, no)<<<nb, TC_THREADS, c.smem, n->st>>>(map, cin, H, W, w, transpose, bias, cout, relu, mask, out,
+                                                    out_blk, ntx, ntiles, n->err);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 // Layer l forward: its input is x (channel-major FP32) for l = 0, else the
-// previous hidden output; hidden outputs are pixel-major BF16, the last
+// previous hidden output; hidden outputs are channel-blocked BF16, the last
 // layer's channel-major FP32 (out).
-static void conv_fwd(lc_net* n, int l, const float* x, int H, int W, void* out) {
+static int conv_fwd(lc_net* n, int l, const float* x, int H, int W, void* out) {
   const bool last = l == n->depth - 1;
-  conv(n, l == 0 ? (const void*)x : n->act[l - 1], l == 0 ? 0 : 1, n->ci[l], H, W, n->pb + n->woff[l], 0,
+  return conv(n, l == 0 ? (const void*)x : n->act[l - 1], l == 0 ? 0 : 1, n->ci[l], H, W, n->pb + n->woff[l], 0,
        n->p + n->boff[l], n->co[l], last ? 0 : 1, nullptr, out, last ? 0 : 1);
 }
 
 int lc_forward(lc_net* n, const float* x_dev, int H, int W, float* y_dev) {
   if (!n || !x_dev || !y_dev || H <= 0 || W <= 0 || (long)H * W > n->max_hw) return -1;
-  for (int l = 0; l < n->depth; l++) conv_fwd(n, l, x_dev, H, W, l == n->depth - 1 ? (void*)y_dev : n->act[l]);
+  for (int l = 0; l < n->depth; l++)
+    if (conv_fwd(n, l, x_dev, H, W, l == n->depth - 1 ? (void*)y_dev : n->act[l])) return -3;
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1007,21 +1095,21 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
   if (!n || !x_dev || !target_dev || !field_w || H <= 0 || W <= 0 || r <= 0 || nout <= 0) return -1;
   if ((long)H * W > n->max_hw || nout * r * r != n->cout || nout > 8 || lr < 0) return -1;
   // forward, keeping every layer's output
-  for (int l = 0; l < n->depth; l++) conv_fwd(n, l, x_dev, H, W, n->act[l]);
+  for (int l = 0; l < n->depth; l++)
+    if (conv_fwd(n, l, x_dev, H, W, n->act[l])) return -3;
   // loss, dL/dy and the last layer's bias-gradient partials
   const int ng = n->cout / r;                    // row groups (field, sub-row)
   if (cudaMemcpyAsync(n->fw, field_w, nout * sizeof(float), cudaMemcpyHostToDevice, n->st) != cudaSuccess) return -3;
-  const int cs = pad16(n->cout);
   if (r == 4 && ((uintptr_t)target_dev & 15) == 0)
     k_loss<true><<<dim3(LOSS_CHUNKS, ng), 256, 0, n->st>>>(static_cast<const float*>(n->act[n->depth - 1]),
-                                                           target_dev, H, W, r, cs, n->fw, n->ga, n->lpart,
+                                                           target_dev, H, W, r, n->fw, n->ga, n->lpart,
                                                            n->bpart, n->cout);
   else
     k_loss<false><<<dim3(LOSS_CHUNKS, ng), 256, 0, n->st>>>(static_cast<const float*>(n->act[n->depth - 1]),
-                                                            target_dev, H, W, r, cs, n->fw, n->ga, n->lpart,
+                                                            target_dev, H, W, r, n->fw, n->ga, n->lpart,
                                                             n->bpart, n->cout);
   k_sum_loss<<<1, 1024, 0, n->st>>>(n->lpart, ng * LOSS_CHUNKS, n->lsum);
-  // backward: g is dL/d(pre-activation) of layer l, pixel-major BF16
+  // backward: g is dL/d(pre-activation) of layer l, channel-blocked BF16
   const int ntx = (W + CT_W - 1) / CT_W, ntiles = ntx * ((H + CT_H - 1) / CT_H);
   const int nbw = std::min(ntiles, n->max_tiles);
   // g: dL/dy for the last layer, then the gradients of the hidden outputs,
@@ -1039,13 +1127,14 @@ int lc_train_step(lc_net* n, const float* x_dev, const float* target_dev, int H,
     if (l == n->depth - 1) {
       k_sum_chunks<<<b, 256, 0, n->st>>>(n->bpart, LOSS_CHUNKS, b, n->g + n->boff[l]);
     } else {
-      k_bias_grad<<<BG_CHUNKS, 256 / op * op, 0, n->st>>>(g, op, (long)H * W, b, n->bpart);
+      k_bias_grad<<<BG_CHUNKS, 192, 0, n->st>>>(g, op, (long)H * W, b, n->bpart);
       k_sum_chunks<<<b, 256, 0, n->st>>>(n->bpart, BG_CHUNKS, b, n->g + n->boff[l]);
     }
     if (l > 0) {
       // dL/d(out of layer l-1) = transposed, flipped convolution of g, times ReLU'(out of layer l-1)
-      conv(n, g, 1, b, H, W, n->pb + n->woff[l], 1, nullptr, a, 0,
-           static_cast<const __nv_bfloat16*>(n->act[l - 1]), n->gh[gk], 1);
+      if (conv(n, g, 1, b, H, W, n->pb + n->woff[l], 1, nullptr, a, 0,
+               static_cast<const __nv_bfloat16*>(n->act[l - 1]), n->gh[gk], 1))
+        return -3;
       g = n->gh[gk];
       gk ^= 1;
     }
