@@ -125,7 +125,7 @@ __device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int bl
 
 // ---------------------------------------------------------------------------
 // 3x3 convolutions on the fifth-generation tensor cores (tcgen05): implicit
-// GEMM with M = the 128 output pixels of one tile row, N = the output channels
+// GEMM with M = 128 pixels of one tile row, N = the output channels
 // (16, 32 or 48, padding included), K = 16 input channels of one tap per
 // instruction; BF16 operands read by the tensor cores from shared memory
 // through matrix descriptors, FP32 accumulators in tensor memory (TMEM).
@@ -134,14 +134,16 @@ __device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int bl
 // the tcgen05 descriptors: 8 x 16-byte core matrices; LBO = byte distance
 // between the two 8-channel halves of an instruction's K = 16, SBO = byte
 // distance between groups of 8 rows):
-//   A (input tile, TC_R + 2 rows x TC_SW columns with a one-pixel halo):
-//     [channel / 8][pixel][channel % 8], planes TC_BOX bytes apart, so the
-//     128 pixels x 16 channels of staged row t shifted by kx start at pixel
+//   A (input tile, TC_R + 2 rows x TC_SW = 128 columns, starting one row and
+//     one column before the tile's TC_W = 126 output columns):
+//     [channel / 8][row][column][channel % 8], planes TC_BOX bytes apart, so
+//     the 128 pixels x 16 channels of staged row t shifted by kx start at pixel
 //     t * TC_SW + kx of planes 2j, 2j + 1 (LBO = TC_BOX, SBO = 128): a tap
-//     shift is a shift of the descriptor's start address.  The tile is one
-//     TMA box of the channel-blocked input (8 channels x TC_SW columns x
-//     TC_R + 2 rows x CP / 8 blocks, zero-filled outside the image): each of its
-//     rows is TC_SW x 16 contiguous bytes in global memory.
+//     shift is a shift of the descriptor's start address.  Output pixels 126
+//     and 127 of an instruction read past the row and are discarded.  The tile
+//     is one TMA box of the channel-blocked input seen as 8-byte elements
+//     (256 elements = 128 pixels x TC_R + 2 rows x CP / 8 blocks, zero-filled
+//     outside the image): each box row is 2 KB contiguous in global memory.
 //   B (weights): [kx][channel / 8][n][channel % 8] with n = (2 - ky) NO + o:
 //     the three row taps of one column tap stacked along N (LBO = 3 NO * 16,
 //     SBO = 128).
@@ -154,34 +156,42 @@ __device__ __forceinline__ void stage_tile(const void* __restrict__ srcv, int bl
 // 3 NO columns instead of TC_R x 9 x CP / 16 of NO columns: each staged row
 // shift is read from shared memory once for its three row taps.
 //
-// Pipeline (one persistent block per SM, warp-specialised): warp 4 loads
-// input tiles by TMA into a ring of TC_STAGES(CP) shared-memory stages (full /
-// empty mbarriers); warp 5 issues each tile's instructions into one of two
+// Pipeline (one persistent block per SM, warp-specialised): warp TC_TMA_WARP
+// loads input tiles by TMA into a ring of tc_stages(CP) shared-memory stages
+// (full / empty mbarriers); warp TC_MMA_WARP issues each tile's instructions
+// into one of two
 // TMEM accumulator buffers and commits them to the stage's empty barrier and
-// the buffer's full barrier; warps 0-3 read their 32 lanes of a full buffer
-// back (tcgen05.ld 32x32b), write bias + ReLU (+ mask) pixel by pixel --
+// the buffer's full barrier; the write-back warps (warp w: lanes 32 (w % 4) ..
+// 32 (w % 4) + 31, tile row w / 4) read their part of a full buffer back
+// (tcgen05.ld 32x32b), write bias + ReLU (+ mask) pixel by pixel --
 // channel-blocked BF16 (16-byte stores) or channel-major FP32 planes, both
 // coalesced along x -- clear the buffer and release it.  Loads, tensor-core
 // work and write-back of different tiles overlap.
 constexpr int TC_R = 4;                         // output rows per tile
-constexpr int TC_W = 128;                       // output columns per tile: the instruction's M
-constexpr int TC_SW = TC_W + 2;                 // staged columns
+constexpr int TC_M = 128;                       // pixels per instruction (M)
+constexpr int TC_SW = TC_M;                     // staged columns: one TMA box row of 256 8-byte elements
+constexpr int TC_W = TC_SW - 2;                 // output columns per tile
 constexpr int TC_SPIX = (TC_R + 2) * TC_SW;     // staged pixels
 constexpr int TC_BOX = TC_SPIX * 16;            // bytes of one 8-channel plane of the staged tile
-constexpr int TC_THREADS = 192;                 // 4 write-back warps, a TMA warp, an MMA warp
+constexpr int TC_EW = 4 * TC_R;                 // write-back warps: one per TMEM lane quarter and tile row
+constexpr int TC_TMA_WARP = TC_EW, TC_MMA_WARP = TC_EW + 1;
+constexpr int TC_THREADS = 32 * (TC_EW + 2);
 
 __host__ __device__ constexpr int tc_stages(int cp) { return cp == 48 ? 2 : 3; }
 __host__ __device__ constexpr int tc_bufcols(int no) { return TC_R * no; }   // TMEM columns of one buffer
+// bytes of one stage: the planes plus 128 (the two pixels the last row's
+// shifted instructions read past the end)
+__host__ __device__ constexpr int tc_stage_bytes(int cp) { return cp / 8 * TC_BOX + 128; }
 __host__ __device__ constexpr int tc_cols(int no) {   // TMEM columns to allocate: a power of 2 >= 2 buffers
   return 2 * TC_R * no <= 32 ? 32 : 2 * TC_R * no <= 64 ? 64 : 2 * TC_R * no <= 128 ? 128
          : 2 * TC_R * no <= 256 ? 256 : 512;
 }
 __host__ __device__ constexpr int tc_smem_used(int cp, int no) {
   // alignment slack, stages, B, bias, 2 S + 4 mbarriers, TMEM address + abort flag
-  return 128 + tc_stages(cp) * (cp / 8) * TC_BOX + 9 * cp * no * 2 + 256 + (2 * tc_stages(cp) + 4) * 8 + 16;
+  return 128 + tc_stages(cp) * tc_stage_bytes(cp) + 9 * cp * no * 2 + 256 + (2 * tc_stages(cp) + 4) * 8 + 16;
 }
 
-static_assert(TC_BOX % 64 == 0, "stages of an even number of planes stay 128-byte aligned");
+static_assert(TC_BOX % 128 == 0, "stages stay 128-byte aligned");
 
 // Shared-memory matrix descriptor: start address, LBO and SBO in 16-byte units,
 // descriptor version 1 (bits 46-47), no swizzle, base offset 0.
@@ -193,7 +203,7 @@ __device__ __forceinline__ unsigned long long tc_desc(unsigned saddr, unsigned l
 // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
 // M >> 4 (bits 24-28).
 __device__ __forceinline__ unsigned tc_idesc(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(TC_W >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(TC_M >> 4) << 24);
 }
 __device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
                                        int accumulate) {
@@ -230,14 +240,14 @@ __device__ __forceinline__ void mbar_arrive(unsigned addr) {
 __device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes) : "memory");
 }
-// TMA: box at coordinates (c0, c1, c2, c3) of a 4-D tensor map into shared
-// memory, completion counted on the mbarrier in bytes.
-__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+// TMA: box at coordinates (c0, c1, c2) of a 3-D tensor map into shared memory,
+// completion counted on the mbarrier in bytes.
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             unsigned mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-      "%5}], [%6];\n" ::"r"(dst),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
       : "memory");
 }
 // The NO consecutive FP32 columns (16, 32 or 48) of this thread's TMEM lane,
@@ -279,7 +289,7 @@ template <int NO> __device__ __forceinline__ void tmem_ld(unsigned taddr, float*
   for (int i = 0; i < NO; i++) v[i] = __uint_as_float(r[i]);
 }
 #undef TC_R16
-// Zero 32 consecutive TMEM columns of this warp's 32 lanes.
+// Zero 32 (or 16) consecutive TMEM columns of this warp's 32 lanes.
 __device__ __forceinline__ void tmem_zero32(unsigned taddr) {
   const unsigned z = 0;
   asm volatile(
@@ -287,6 +297,18 @@ __device__ __forceinline__ void tmem_zero32(unsigned taddr) {
       "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
       "r"(z)
       : "memory");
+}
+__device__ __forceinline__ void tmem_zero16(unsigned taddr) {
+  const unsigned z = 0;
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(
+                   taddr),
+               "r"(z)
+               : "memory");
+}
+// Zero NO (16, 32 or 48) consecutive TMEM columns of this warp's lanes.
+template <int NO> __device__ __forceinline__ void tmem_zero(unsigned taddr) {
+  if constexpr (NO >= 32) tmem_zero32(taddr);
+  if constexpr (NO != 32) tmem_zero16(taddr + (NO >= 32 ? 32 : 0));
 }
 
 // Convolution with padding 1: out[o][y][x] =
@@ -307,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const __nv_bfloat16* __restrict__ mask, void* __restrict__ out, int out_blk, int ntx, int ntiles,
               int* __restrict__ err) {
   constexpr int C8 = CP / 8, S = tc_stages(CP);
-  constexpr int A_STAGE = C8 * TC_BOX, B_BYTES = 9 * CP * NO * 2, TB = tc_bufcols(NO);
+  constexpr int A_STAGE = tc_stage_bytes(CP), B_BYTES = 9 * CP * NO * 2, TB = tc_bufcols(NO);
   constexpr unsigned NCOL = tc_cols(NO);
   extern __shared__ __align__(16) unsigned char tc_raw[];
   const unsigned raw = smem_u32(tc_raw), base = (raw + 127) & ~127u;
@@ -342,12 +364,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; b++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tfull(b)) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(tempty(b)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(tempty(b)), "r"(TC_EW) : "memory");
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == TC_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
                  "r"(NCOL)
                  : "memory");
@@ -357,7 +379,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = *tslot;
-  if (warp < 4) {   // both accumulator buffers start at zero (each warp clears its lanes)
+  if (warp < 4) {   // both accumulator buffers start at zero (each lane quarter's warp clears its lanes)
     const unsigned tl = tmem + ((unsigned)(32 * warp) << 16);
 #pragma unroll
     for (int c = 0; c < 2 * TB; c += 32) tmem_zero32(tl + c);
@@ -368,7 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
 
   bool failed = false;
-  if (warp == 4) {
+  if (warp == TC_TMA_WARP) {
     // ---- TMA producer
     if (lane == 0) {
       int i = 0;
@@ -376,11 +398,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int st = i % S;
         if (!mbar_wait(empty(st), ((i / S) & 1) ^ 1, abort)) { failed = true; break; }
         const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
-        mbar_expect_tx(full(st), A_STAGE);
-        tma_load_4d(base + st * A_STAGE, &map, 0, tx0 - 1, ty0 - 1, 0, full(st));
+        mbar_expect_tx(full(st), C8 * TC_BOX);
+        tma_load_3d(base + st * A_STAGE, &map, 2 * (tx0 - 1), ty0 - 1, 0, full(st));
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == TC_MMA_WARP) {
     // ---- tensor-core issue
     if (lane == 0) {
       int i = 0;
@@ -420,8 +442,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else {
-    // ---- write-back: warp w owns TMEM lanes 32 w .. 32 w + 31 = output pixels
-    const unsigned tl = tmem + ((unsigned)(32 * warp) << 16);
+    // ---- write-back: warp w owns TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 =
+    // output pixels of tile row w / 4
+    const int q = warp & 3, r = warp >> 2;
+    const unsigned tl = tmem + ((unsigned)(32 * q) << 16);
     const size_t hw = (size_t)H * W;
     int i = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, i++) {
@@ -430,13 +454,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) { failed = true; break; }
       tc_fence_after();
       const int ty0 = (tile / ntx) * TC_R, tx0 = (tile % ntx) * TC_W;
-      const int x = tx0 + 32 * warp + lane;
-#pragma unroll 1
-      for (int r = 0; r < TC_R; r++) {
+      const int x = tx0 + 32 * q + lane;
+      {
         float v[NO];
         tmem_ld<NO>(tl + b * TB + r * NO, v);
         const int y = ty0 + r;
-        if (y >= H || x >= W) continue;
+        if (y < H && x < W && 32 * q + lane < TC_W) {
         const size_t pix = (size_t)y * W + x;
 #pragma unroll
         for (int o = 0; o < NO; o++) {
@@ -450,10 +473,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint4 m4 = __ldg(mk + c * hw);
             const unsigned mw[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-              const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[q]);
-              if (!(__low2float(m2) > 0.f)) v[8 * c + 2 * q] = 0.f;
-              if (!(__high2float(m2) > 0.f)) v[8 * c + 2 * q + 1] = 0.f;
+            for (int e = 0; e < 4; e++) {
+              const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[e]);
+              if (!(__low2float(m2) > 0.f)) v[8 * c + 2 * e] = 0.f;
+              if (!(__high2float(m2) > 0.f)) v[8 * c + 2 * e + 1] = 0.f;
             }
           }
         }
@@ -474,10 +497,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int o = 0; o < NO; o++)
             if (o < cout) of[(size_t)o * hw + pix] = v[o];
         }
+        }
       }
-      // clear the buffer for its next tile and hand it back
-#pragma unroll
-      for (int c = 0; c < TB; c += 32) tmem_zero32(tl + b * TB + c);
+      // clear this warp's part of the buffer for its next tile and hand it back
+      tmem_zero<NO>(tl + b * TB + r * NO);
       asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       tc_fence_before();
       __syncwarp();
@@ -1056,13 +1079,14 @@ static int conv(lc_net* n, const void* in, int in_blk, int cin, int H, int W, co
     k_to_blk<<<nblk(hw, 256), 256, 0, n->st>>>(static_cast<const float*>(in), cin, hw, cp, n->x16);
     in = n->x16;
   }
-  // the input as a 4-D tensor (8 channels, W, H, cp / 8 blocks) of 16-byte
-  // pixels; boxes of 8 x TC_SW x (TC_R + 2) x cp / 8, zero fill outside
+  // the input as a 3-D tensor of 8-byte elements (2 W per channel-block row, H
+  // rows, cp / 8 blocks); boxes of 2 TC_SW x (TC_R + 2) x cp / 8, zero fill
+  // outside
   CUtensorMap map;
-  const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(cp / 8)};
-  const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)hw * 16};
-  const cuuint32_t box[4] = {8, TC_SW, TC_R + 2, (cuuint32_t)(cp / 8)}, estr[4] = {1, 1, 1, 1};
-  if (tma_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(in), dims, strides, box, estr,
+  const cuuint64_t dims[3] = {(cuuint64_t)W * 2, (cuuint64_t)H, (cuuint64_t)(cp / 8)};
+  const cuuint64_t strides[2] = {(cuuint64_t)W * 16, (cuuint64_t)hw * 16};
+  const cuuint32_t box[3] = {2 * TC_SW, TC_R + 2, (cuuint32_t)(cp / 8)}, estr[3] = {1, 1, 1};
+  if (tma_encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(in), dims, strides, box, estr,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return -3;
