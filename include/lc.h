@@ -87,6 +87,20 @@ int lc_make_target(const double* qf_dev, const double* qc_dev, const double* bf_
  * use_net == 0 the plain prolongation. */
 int lc_apply(const double* qc_dev, const float* y_dev, int Hc, int Wc, int r, float s_eta, float s_q,
              int use_net, double* out_dev, void* cuda_stream);
+/* Fallback tiles of the learned form: the paper's refinement flag (a surface
+ * jump between neighbouring cells, Sec. 6.3) evaluated on a coarse state.
+ * eta_dev, b_dev: surface and bathymetry, H x W doubles on the device.  A cell
+ * is flagged when it and a face neighbour are both deeper than hmin
+ * (eta - b > hmin) and their surfaces differ by more than thr.  The grid is cut
+ * into tiles of `tile` cells from the low corner in each direction, a one-cell
+ * remainder joined to the tile before it (so nt = 1 when n < tile + 2, else
+ * n / tile, plus one when n % tile >= 2); sel_dev[ty * ntx + tx] (device,
+ * ntx * nty bytes, caller-owned) becomes 1 when a flagged cell lies within
+ * Chebyshev distance `buffer` of tile (tx, ty) and none of the tile's cells is
+ * shallower than hmin, else 0.  Asynchronous on cuda_stream; -1 for invalid
+ * arguments (tile < 2, buffer < 0, thr < 0 or not finite). */
+int lc_fallback_tiles(const double* eta_dev, const double* b_dev, int H, int W, double thr, double hmin, int tile,
+                      int buffer, unsigned char* sel_dev, void* cuda_stream);
 /* Restriction: coarse[Hc][Wc] = mean of each r x r block of fine[r Hc][r Wc]. */
 int lc_restrict(const double* fine_dev, int Hc, int Wc, int r, double* coarse_dev, void* cuda_stream);
 

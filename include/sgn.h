@@ -229,9 +229,13 @@ int sgn_launches_per_step(sgn_solver* s);
  *     quantity on chip and moves only the state through HBM (mixed precision on
  *     a single grid only: EINVAL for an FP64 solver; a refined level falls back
  *     to 0).  With schedule 2 the SGN_TUNE_UPDATE option selects the rows one
- *     block of the one-pass kernel marches over: 128, 64 or 256 (its block is
- *     128 columns wide).  A new mixed-precision solver starts with schedule 2
- *     (and option 0 elsewhere); an FP64 solver with schedule 0.
+ *     block of the one-pass kernel marches over: at most 128, 64 or 256 (its
+ *     block is 128 columns wide), halved down to 32 while the grid would give
+ *     fewer tiles than the device holds resident blocks; sgn_get_tuning
+ *     reports the rows used.  A new mixed-precision solver starts with
+ *     schedule 2 when the grid gives at least half as many 32-row tiles as
+ *     resident blocks (on 152 SMs: from about 1024 x 1024 cells), else with
+ *     schedule 0, and with option 0 elsewhere; an FP64 solver with schedule 0.
  * The block-shape options and schedules 0 and 1 compute the same values bit
  * for bit; schedule 2 evaluates the same expressions in one kernel and agrees
  * with them to FP32 rounding (the compiler may fuse a different set of

@@ -61,6 +61,15 @@ int sgn_amr_npatches(const sgn_amr* a, int level);
  * status and the clipped water.  Errors: EINVAL. */
 int sgn_amr_set_patch(sgn_amr* a, int level, int patch, const double* q);
 int sgn_amr_get_patch(sgn_amr* a, int level, int patch, double* q);
+/* Fields 0 .. nfields-1 (field order as in sgn.h) of every patch of `level`,
+ * interior cells only, into out_dev: caller-owned device memory, FP64
+ * [nfields][NY][NX] over the level's full grid (NX = level-0 nx * ratio^level,
+ * likewise NY), row-major, x fastest.  Cells no patch of the level covers are
+ * left unchanged.  For level 0 this is the whole coarse state.  One launch over
+ * all patches (at most 65535; more: SGN_ERANGE); synchronises the hierarchy's
+ * stream.  SGN_EINVAL for a bad level, nfields outside 1 .. nvar or a NULL
+ * pointer. */
+int sgn_amr_get_level_device(sgn_amr* a, int level, int nfields, double* out_dev);
 
 /* n level-0 steps with the CFL step of all levels (subcycling below), or one
  * level-0 step of the given dt0.  Return the status of the batch as an error

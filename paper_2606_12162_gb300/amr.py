@@ -16,6 +16,7 @@ AMR_SIGS = [
     ("sgn_amr_npatches", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sgn_amr_set_patch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, DP]),
     ("sgn_amr_get_patch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, DP]),
+    ("sgn_amr_get_level_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("sgn_amr_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, DP]),
     ("sgn_amr_step_dt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     ("sgn_amr_next_dt", ctypes.c_int, [ctypes.c_void_p, DP]),
@@ -150,6 +151,20 @@ class Hierarchy:
         i0, j0, nx, ny = self.boxes[level][k]
         out = np.empty((self.nvar, ny, nx))
         _ck(lib().sgn_amr_get_patch(self.h, level, k, out.ctypes.data_as(DP)), "sgn_amr_get_patch")
+        return out
+
+    def get_level_device(self, level, out):
+        """Every patch of `level` into the first fields of `out`, a contiguous
+        FP64 CUDA tensor of shape (nfields, NY_l, NX_l); cells without a patch
+        keep their values."""
+        import torch
+        R = self.r ** level
+        if (out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous() or out.dim() != 3
+                or tuple(out.shape[1:]) != (self.ny0 * R, self.nx0 * R)):
+            raise ValueError("out must be a contiguous float64 CUDA tensor (nfields, %d, %d)"
+                             % (self.ny0 * R, self.nx0 * R))
+        _ck(lib().sgn_amr_get_level_device(self.h, level, int(out.shape[0]), ctypes.c_void_p(out.data_ptr())),
+            "sgn_amr_get_level_device")
         return out
 
     def set_state(self, qs):

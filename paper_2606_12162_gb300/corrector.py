@@ -26,6 +26,8 @@ LC_SIGS = [
     ("lc_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long]),
     ("lc_forward", ctypes.c_int, [ctypes.c_void_p, DP, ctypes.c_int, ctypes.c_int, DP]),
     ("lc_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("lc_fallback_tiles", ctypes.c_int, [DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, DP, ctypes.c_void_p]),
     ("lc_train_step", ctypes.c_int, [ctypes.c_void_p, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_float,
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -441,42 +443,41 @@ def correct(net, qc, bcd, phid, out=None):
     return out
 
 
+def _tile_cuts(n, tile):
+    """Tiles of `tile` cells from the low corner, a one-cell remainder joined to
+    the tile before it: (start, width) pairs."""
+    cuts, x = [], 0
+    while x < n:
+        w = min(tile, n - x)
+        if n - (x + w) == 1:
+            w += 1
+        cuts.append((x, w))
+        x += w
+    return cuts
+
+
 def fallback_boxes(eta, b, thr, hmin, tile, buffer, r):
     """Level-1 boxes of the runtime fallback from a coarse surface eta and
-    bathymetry b (nc x nc device tensors): the paper's refinement flag
+    bathymetry b (H x W FP64 device tensors): the paper's refinement flag
     (Sec. 6.3), a surface jump |eta - eta_n| > thr between neighbouring cells,
     counted only between cells deeper than hmin (away from the shore, where the
     relaxed system runs as SWE anyway and where a coarse cell partly over land
     would take its children's mean depth under a patch), widened by `buffer`
-    cells; the grid is cut into tile x tile squares from the low corner (a
-    one-cell remainder joined to the square before it) and every square holding
-    a widened flag and no cell shallower than hmin becomes a box (in fine
-    cells)."""
+    cells; every tile (tile x tile squares from the low corner, a one-cell
+    remainder joined to the square before it) holding a widened flag and no
+    cell shallower than hmin becomes a box (in fine cells).  The flags and the
+    tile selection run in lc_fallback_tiles."""
     import torch
-    nc = eta.shape[-1]
-    deep = (eta - b) > hmin
-    jx = ((eta[:, 1:] - eta[:, :-1]).abs() > thr) & deep[:, 1:] & deep[:, :-1]
-    jy = ((eta[1:, :] - eta[:-1, :]).abs() > thr) & deep[1:, :] & deep[:-1, :]
-    f = torch.zeros_like(deep)
-    f[:, 1:] |= jx
-    f[:, :-1] |= jx
-    f[1:, :] |= jy
-    f[:-1, :] |= jy
-    if buffer > 0:
-        f = torch.nn.functional.max_pool2d(f[None, None].float(), 2 * buffer + 1, 1, buffer)[0, 0] > 0
-    cuts = []
-    x = 0
-    while x < nc:
-        w = min(tile, nc - x)
-        if nc - (x + w) == 1:
-            w += 1
-        cuts.append((x, w))
-        x += w
-    fh, sh = f.cpu().numpy(), (~deep).cpu().numpy()
+    H, Wd = eta.shape[-2], eta.shape[-1]
+    cy, cx = _tile_cuts(H, tile), _tile_cuts(Wd, tile)
+    sel = torch.empty((len(cy), len(cx)), dtype=torch.uint8, device=eta.device)
+    _ck(lib().lc_fallback_tiles(_p(eta), _p(b), H, Wd, float(thr), float(hmin), int(tile), int(buffer), _p(sel),
+                                _stream()), "lc_fallback_tiles")
+    sh = sel.cpu().numpy()
     boxes = []
-    for (y0, h_) in cuts:
-        for (x0, w_) in cuts:
-            if fh[y0:y0 + h_, x0:x0 + w_].any() and not sh[y0:y0 + h_, x0:x0 + w_].any():
+    for ty, (y0, h_) in enumerate(cy):
+        for tx, (x0, w_) in enumerate(cx):
+            if sh[ty, tx]:
                 boxes.append((x0 * r, y0 * r, w_ * r, h_ * r))
     return boxes
 
@@ -522,6 +523,7 @@ def hybrid_run(net, meta, s, times, on_snapshot, thr=0.05, tile=16, buffer=4, re
     bcd = torch.from_numpy(np.ascontiguousarray(bc)).cuda()
     phid = torch.from_numpy(np.ascontiguousarray(meta["phic"])).cuda()
     qcd = torch.empty((nv, nc, nc), dtype=torch.float64, device="cuda")
+    e0 = torch.empty((1, nc, nc), dtype=torch.float64, device="cuda")
     out = torch.empty((3, nf, nf), dtype=torch.float64, device="cuda")
     res = dict(step_s=0.0, regrid_s=0.0, snapshot_s=0.0, steps=0, regrids=0, patch_frac=[], patches=[])
     # as advance_to: single steps first (the step after a new state is computed
@@ -537,8 +539,8 @@ def hybrid_run(net, meta, s, times, on_snapshot, thr=0.05, tile=16, buffer=4, re
             while T - t > 1e-9:
                 if since >= regrid_every:
                     c0 = clock()
-                    e0 = torch.from_numpy(h.get_patch(0, 0)[0]).cuda()
-                    h.regrid(bf, [fallback_boxes(e0, bcd, thr, hmin, tile, buffer, r)])
+                    h.get_level_device(0, e0)
+                    h.regrid(bf, [fallback_boxes(e0[0], bcd, thr, hmin, tile, buffer, r)])
                     res["regrid_s"] += clock() - c0
                     res["regrids"] += 1
                     since = 0
@@ -576,15 +578,13 @@ def hybrid_run(net, meta, s, times, on_snapshot, thr=0.05, tile=16, buffer=4, re
                 tc, _ = advance_to(sc, tc, T)
                 sc.get_state_device(qcd)
             else:
-                qcd.copy_(torch.from_numpy(h.get_patch(0, 0)))
+                h.get_level_device(0, qcd)
             if net is not None:
                 correct(net, qcd, bcd, phid, out)
             else:
                 _ck(lib().lc_apply(_p(qcd), None, nc, nc, r, S_ETA, S_Q, 0, _p(out), _stream()), "lc_apply")
-            area = 0
-            for k, (i0, j0, bx, by) in enumerate(h.get_boxes(1)):
-                out[:, j0:j0 + by, i0:i0 + bx] = torch.from_numpy(h.get_patch(1, k)[:3]).cuda()
-                area += bx * by
+            h.get_level_device(1, out)            # the patches' fine solve over the network's field
+            area = sum(bx * by for (_, _, bx, by) in h.get_boxes(1))
             res["snapshot_s"] += clock() - c0
             res["patch_frac"].append(area / float(nf * nf))
             res["patches"].append(h.npatches(1))

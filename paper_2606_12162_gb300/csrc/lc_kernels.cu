@@ -863,6 +863,51 @@ unsigned long long splitmix(unsigned long long& s) {
 
 inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// The learned form's fallback flag (the paper's refinement flag, a surface jump
+// between neighbouring cells, Sec. 6.3) on the coarse state: cell c is flagged
+// when a face neighbour n and c are both deeper than hmin (eta - b > hmin) and
+// |eta_c - eta_n| > thr.  Tiles: `tile` cells from the low corner, a one-cell
+// remainder joined to the tile before it.  A tile is selected when a flagged
+// cell lies within Chebyshev distance `buffer` of it and none of its own cells
+// is shallower than hmin.  One block per tile; the FP64 comparisons are those
+// of the definition.
+__device__ __forceinline__ void tile_span(int k, int n, int nt, int tile, int& a0, int& a1) {
+  a0 = k * tile;
+  a1 = k == nt - 1 ? n : a0 + tile;
+}
+__global__ void k_fallback_tiles(const double* __restrict__ eta, const double* __restrict__ b, int H, int W, double thr,
+                                 double hmin, int tile, int buffer, int ntx, int nty, unsigned char* __restrict__ sel) {
+  int x0, x1, y0, y1;
+  tile_span(blockIdx.x, W, ntx, tile, x0, x1);
+  tile_span(blockIdx.y, H, nty, tile, y0, y1);
+  const int ex0 = max(0, x0 - buffer), ex1 = min(W, x1 + buffer), ey0 = max(0, y0 - buffer), ey1 = min(H, y1 + buffer);
+  const int ew = ex1 - ex0, ne = ew * (ey1 - ey0);
+  int any = 0;
+  for (int e = threadIdx.x; e < ne && !any; e += blockDim.x) {
+    const int y = ey0 + e / ew, x = ex0 + e % ew;
+    const size_t c = (size_t)y * W + x;
+    const double ec = eta[c];
+    if (!(ec - b[c] > hmin)) continue;
+    const int nx[4] = {x - 1, x + 1, x, x}, ny[4] = {y, y, y - 1, y + 1};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (nx[q] < 0 || nx[q] >= W || ny[q] < 0 || ny[q] >= H) continue;
+      const size_t m = (size_t)ny[q] * W + nx[q];
+      const double em = eta[m];
+      if (em - b[m] > hmin && fabs(ec - em) > thr) any = 1;
+    }
+  }
+  const int tw = x1 - x0, nt = tw * (y1 - y0);
+  int shallow = 0;
+  for (int e = threadIdx.x; e < nt; e += blockDim.x) {
+    const size_t c = (size_t)(y0 + e / tw) * W + x0 + e % tw;
+    if (!(eta[c] - b[c] > hmin)) shallow = 1;
+  }
+  any = __syncthreads_or(any);
+  shallow = __syncthreads_or(shallow);
+  if (threadIdx.x == 0) sel[(size_t)blockIdx.y * ntx + blockIdx.x] = any && !shallow;
+}
+
 }  // namespace
 
 // ---- launch helpers of the tensor-core kernels: padded channel counts are
@@ -1208,6 +1253,19 @@ int lc_apply(const double* qc_dev, const float* y_dev, int Hc, int Wc, int r, fl
   long nn = 3L * Hc * r * Wc * r;
   k_apply<<<nblk(nn, 256), 256, 0, (cudaStream_t)cuda_stream>>>(qc_dev, y_dev, Hc, Wc, r, s_eta, s_q, use_net,
                                                                   out_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+static int tile_count(int n, int tile) { return n < tile + 2 ? 1 : n / tile + (n % tile >= 2 ? 1 : 0); }
+
+int lc_fallback_tiles(const double* eta_dev, const double* b_dev, int H, int W, double thr, double hmin, int tile,
+                      int buffer, unsigned char* sel_dev, void* cuda_stream) {
+  if (!eta_dev || !b_dev || !sel_dev || H <= 0 || W <= 0 || tile < 2 || buffer < 0 || !(thr >= 0) ||
+      !std::isfinite(thr) || !std::isfinite(hmin))
+    return -1;
+  const int ntx = tile_count(W, tile), nty = tile_count(H, tile);
+  k_fallback_tiles<<<dim3(ntx, nty), 256, 0, (cudaStream_t)cuda_stream>>>(eta_dev, b_dev, H, W, thr, hmin, tile,
+                                                                           buffer, ntx, nty, sel_dev);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -279,6 +279,21 @@ __global__ void k_amr_unpack(Dev<Real> d, double* qd, int px, int py, int nx, in
   for (int k = 0; k < NV; k++) qd[k * n + s] = (double)d.q[cur][k * d.fs + id];
 }
 
+// Interior cells of every patch of a level into a dense device field
+// (fields [0, nf) of [field][NY][NX]); tab: px, py, nx, ny, i0, j0 per patch,
+// one patch per blockIdx.z.
+template <int MODEL, typename Real>
+__global__ void k_amr_scatter(Dev<Real> d, const int* __restrict__ tab, int nf, double* __restrict__ out, int NX,
+                              int NY, int cur) {
+  const int* t = tab + 6 * blockIdx.z;
+  const int px = t[0], py = t[1], nx = t[2], ny = t[3], i0 = t[4], j0 = t[5];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  const size_t id = at(d.pitch, px + NG + i, py + NG + j);
+  const size_t o = (size_t)(j0 + j) * NX + (i0 + i), plane = (size_t)NX * NY;
+  for (int k = 0; k < nf; k++) out[k * plane + o] = (double)d.q[cur][k * d.fs + id];
+}
+
 struct AmrDt {
   int L, strang;
   double cfl;
@@ -386,6 +401,9 @@ struct AmrBase {
   virtual void dims(int l, int* NX, int* NY) const = 0;
   virtual void boxes(int l, std::vector<int>& out) const = 0;
   virtual int flags(int l, double tol, std::vector<unsigned char>& flag, std::vector<unsigned char>& have) = 0;
+  // fields [0, nf) of every patch of level l into out (device, [nf][NY][NX] of
+  // the level's full grid); cells without a patch are left as they are
+  virtual int get_level_device(int l, int nf, double* out) = 0;
 };
 
 AmrBase* make_amr_f64(int model);
@@ -454,6 +472,8 @@ class Amr : public AmrBase {
   double* staging_ = nullptr;
   size_t stage_bytes_ = 0;
   unsigned char* flag_buf_ = nullptr;   // atlas-sized flag plane (when staging_ is smaller)
+  int* scat_[AMR_MAXL] = {};            // per level: patch table of k_amr_scatter (built on first use)
+  int scat_mx_[AMR_MAXL] = {}, scat_my_[AMR_MAXL] = {};
   size_t flag_cap_ = 0;
   double* hsc_ = nullptr;      // pinned host scalars
   cudaStream_t st_ = nullptr, cap_ = nullptr;
@@ -995,6 +1015,37 @@ class Amr : public AmrBase {
   }
 
   void dims(int l, int* NX, int* NY) const override { *NX = NX_[l]; *NY = NY_[l]; }
+
+  int get_level_device(int l, int nf, double* out) override {
+    if (l < 0 || l >= L_ || nf < 1 || nf > NV || !out) return SGN_EINVAL;
+    const int nb = (int)bx_[l].size();
+    if (nb == 0) return SGN_OK;
+    if (nb > 65535) return SGN_ERANGE;
+    if (!scat_[l]) {
+      std::vector<int> t(6 * (size_t)nb);
+      int mx = 1, my = 1;
+      for (int k = 0; k < nb; k++) {
+        const Box& b = bx_[l][k];
+        int* e = &t[6 * (size_t)k];
+        e[0] = b.px; e[1] = b.py; e[2] = b.nx; e[3] = b.ny; e[4] = b.i0; e[5] = b.j0;
+        mx = std::max(mx, b.nx);
+        my = std::max(my, b.ny);
+      }
+      int* dt = lv_[0]->template alloc_dev<int>(t.size());
+      if (!dt) return SGN_ENOMEM;
+      SGN_CK(cudaMemcpyAsync(dt, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, st_));
+      SGN_CK(cudaStreamSynchronize(st_));
+      scat_[l] = dt;
+      scat_mx_[l] = mx;
+      scat_my_[l] = my;
+    }
+    dim3 gr((scat_mx_[l] + 31) / 32, (scat_my_[l] + 7) / 8, nb);
+    k_amr_scatter<MODEL, Real><<<gr, dim3(32, 8), 0, st_>>>(lv_[l]->dev(), scat_[l], nf, out, NX_[l], NY_[l],
+                                                             lv_[l]->cur());
+    SGN_CK(cudaGetLastError());
+    SGN_CK(cudaStreamSynchronize(st_));
+    return SGN_OK;
+  }
 
   void boxes(int l, std::vector<int>& out) const override {
     out.clear();

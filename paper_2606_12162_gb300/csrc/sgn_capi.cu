@@ -474,6 +474,11 @@ int sgn_amr_set_patch(sgn_amr* a, int level, int patch, const double* q) {
   return (a && q) ? a->impl->set_patch(level, patch, q) : SGN_EINVAL;
 }
 
+int sgn_amr_get_level_device(sgn_amr* a, int level, int nfields, double* out_dev) {
+  if (!a || !out_dev) return SGN_EINVAL;
+  return a->impl->get_level_device(level, nfields, out_dev);
+}
+
 int sgn_amr_get_patch(sgn_amr* a, int level, int patch, double* q) {
   return (a && q) ? a->impl->get_patch(level, patch, q) : SGN_EINVAL;
 }

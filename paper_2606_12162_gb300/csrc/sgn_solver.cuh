@@ -273,7 +273,9 @@ class Solver : public SolverBase {
       SGN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<MODEL, Real>, FUSED_NT, smb));
       SGN_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       fused_resident_ = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
-      tune_[TU_SCHED] = SCHED_FUSED;   // the default schedule of the mixed path on a single grid
+      // the default schedule of the mixed path on a single grid, unless the grid
+      // is too small to give the resident blocks tiles of at least 32 rows
+      if (fused_plan(g.nx, g.ny, 32).ntiles * 2 >= fused_resident_) tune_[TU_SCHED] = SCHED_FUSED;
     }
     for (int k = 0; k < 4; k++) SGN_CK(cudaEventCreateWithFlags(&fork_[k], cudaEventDisableTiming));
     save_ = dnew<unsigned long long>(4);
@@ -378,13 +380,20 @@ class Solver : public SolverBase {
   }
 
   // The one-pass step (k_step_fused): strips of FUSED_OUT columns by chunks of
-  // kFusedRows[option of the update slot] rows, one block each.
+  // fused_rows() rows (the long chunks), one block each.
   static constexpr bool kFusedBuilt = sizeof(Real) == 4;
   bool fused_ok() const { return kFusedBuilt && !d_.kind; }
   int fused_resident_ = 0;   // blocks of the one-pass kernel resident on the device
+  // rows of the long chunks: the option's, halved (not below 32) while the grid
+  // would give fewer tiles than there are resident blocks
+  int fused_rows() const {
+    int H = kFusedRows[tune_[TU_UPDATE]];
+    while (H > 32 && fused_plan(d_.nx, d_.ny, H).ntiles < fused_resident_) H /= 2;
+    return H;
+  }
   void launch_fused(cudaStream_t s, int c) {
     if constexpr (kFusedBuilt) {
-      const FusedPlan p = fused_plan(d_.nx, d_.ny, kFusedRows[tune_[TU_UPDATE]]);
+      const FusedPlan p = fused_plan(d_.nx, d_.ny, fused_rows());
       const int nb = p.ntiles < fused_resident_ ? p.ntiles : fused_resident_;
       k_step_fused<MODEL, Real><<<nb, FUSED_NT, sizeof(FusedSmem<MODEL, Real>), s>>>(d_, c, p);
     }
@@ -691,7 +700,7 @@ class Solver : public SolverBase {
       if (ch) ch[k] = tune_[k];
       // with the one-pass schedule the update slot stands for its block: NT columns by H rows
       const int x = k == TU_SCHED ? 0 : (fz && k == TU_UPDATE ? FUSED_NT : (int)tb_[k].x);
-      const int y = k == TU_SCHED ? 0 : (fz && k == TU_UPDATE ? kFusedRows[tune_[k]] : (int)tb_[k].y);
+      const int y = k == TU_SCHED ? 0 : (fz && k == TU_UPDATE ? fused_rows() : (int)tb_[k].y);
       if (bx) bx[k] = x;
       if (by) by[k] = y;
     }

@@ -360,3 +360,33 @@ def test_regrid_to_empty_levels_and_back(M, A):
             q = g.get_patch(l, k)
             assert np.abs(q[1:]).max() <= 1e-14
             assert (rel_l2(q, o.patch_state(l, k)) <= FP64_TOL).all()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_level_gather_on_the_device_equals_the_patches(M, precision):
+    """sgn_amr_get_level_device writes every patch's interior at its place in
+    the level's full grid, exactly the values sgn_amr_get_patch returns, and
+    leaves the cells no patch covers untouched; field subsets and bad
+    arguments."""
+    import torch
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=8, amp=0.2)
+    g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, precision=precision, **CFG)
+    g.set_state(qs)
+    g.step(3)
+    for l in range(3):
+        R = 2 ** l
+        out = torch.full((g.nvar, 20 * R, 24 * R), -7.0, dtype=torch.float64, device="cuda")
+        g.get_level_device(l, out)
+        o = out.cpu().numpy()
+        covered = np.zeros((20 * R, 24 * R), dtype=bool)
+        for k, (i0, j0, nx, ny) in enumerate(g.boxes[l]):
+            assert np.array_equal(o[:, j0:j0 + ny, i0:i0 + nx], g.get_patch(l, k))
+            covered[j0:j0 + ny, i0:i0 + nx] = True
+        assert (o[:, ~covered] == -7.0).all()
+        two = torch.full((2, 20 * R, 24 * R), -7.0, dtype=torch.float64, device="cuda")
+        g.get_level_device(l, two)
+        assert np.array_equal(two.cpu().numpy(), o[:2])
+    with pytest.raises(ValueError):
+        g.get_level_device(1, torch.zeros((3, 20, 24), dtype=torch.float64, device="cuda"))
+    with pytest.raises(M.sgn.SGNError):       # more fields than the model has
+        g.get_level_device(0, torch.zeros((g.nvar + 1, 20, 24), dtype=torch.float64, device="cuda"))

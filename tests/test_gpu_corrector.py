@@ -196,6 +196,44 @@ def test_fallback_boxes_follow_the_flag(C):
     assert C.fallback_boxes(eta, b, 0.02, 20.0, 8, 1, r) == []
 
 
+def test_fallback_tiles_match_their_definition(C):
+    """lc_fallback_tiles against the flag written out in NumPy (a cell and a
+    face neighbour both deeper than hmin with surfaces more than thr apart;
+    dilation by `buffer` in the Chebyshev metric; tiles with a remainder of one
+    cell joined to the tile before; no shallow cell in a selected tile), on
+    noisy surfaces with four raised cells over deep water with a shallow
+    rectangle, for several tile and buffer sizes (each case selects some tiles
+    and rejects others both for lack of a flag and for shallow cells)."""
+    import torch
+    rng = np.random.default_rng(17)
+    for (H, Wd, tile, buffer) in ((37, 50, 8, 1), (33, 33, 16, 0), (70, 45, 16, 3), (9, 13, 4, 2)):
+        eta = rng.normal(0.0, 0.005, (H, Wd))
+        for _ in range(4):
+            eta[rng.integers(H), rng.integers(Wd)] += 0.1
+        b = np.full((H, Wd), -100.0)
+        y0, x0 = rng.integers(H // 2), rng.integers(Wd // 2)
+        b[y0:y0 + max(2, H // 4), x0:x0 + max(2, Wd // 4)] = -5.0
+        d = eta - b > 20.0
+        f = np.zeros((H, Wd), dtype=bool)
+        jx = (np.abs(eta[:, 1:] - eta[:, :-1]) > 0.05) & d[:, 1:] & d[:, :-1]
+        jy = (np.abs(eta[1:, :] - eta[:-1, :]) > 0.05) & d[1:, :] & d[:-1, :]
+        f[:, 1:] |= jx
+        f[:, :-1] |= jx
+        f[1:, :] |= jy
+        f[:-1, :] |= jy
+        fw = np.zeros_like(f)
+        for y, x in zip(*np.nonzero(f)):
+            fw[max(0, y - buffer):y + buffer + 1, max(0, x - buffer):x + buffer + 1] = True
+        want = []
+        for (y0, h_) in C._tile_cuts(H, tile):
+            for (x0, w_) in C._tile_cuts(Wd, tile):
+                if fw[y0:y0 + h_, x0:x0 + w_].any() and d[y0:y0 + h_, x0:x0 + w_].all():
+                    want.append((x0 * 4, y0 * 4, w_ * 4, h_ * 4))
+        got = C.fallback_boxes(torch.from_numpy(eta).cuda(), torch.from_numpy(b).cuda(), 0.05, 20.0, tile, buffer, 4)
+        assert got == want, (H, Wd, tile, buffer)
+        assert 0 < len(want) < len(C._tile_cuts(H, tile)) * len(C._tile_cuts(Wd, tile))
+
+
 def test_experiment_pipeline_small(C):
     """The whole experiment driver at a small size: pairs with gauges, training,
     evaluation, inference timing, throughput figures and the FP64 fine check."""

@@ -116,10 +116,17 @@ def test_fused_against_oracle(S, oracle_mod):
     assert abs(tg - to) <= 1e-5 * to
 
 
-def test_fused_is_the_mixed_default(S):
+def test_fused_is_the_mixed_default_on_large_grids(S):
+    """A new mixed solver runs the one-pass step when the grid gives the device
+    enough tiles (1024 x 1024 does on a GB300, with 32-row chunks), the kernel
+    sequence on small grids (140 x 90)."""
     b, q = W.random_small_case(2, 140, 90, seed=2, dx=0.05, wetdry=True, amp=0.15)
     s = S.Solver(b, model=2, dx=0.05, precision=1, h_star=0.6)
-    assert s.tuning()["schedule"][0] == FUSED
+    assert s.tuning()["schedule"][0] == 0
+    b = np.full((1024, 1024), -50.0)
+    s = S.Solver(b, model=2, dx=10.0, precision=1, h_star=20.0)
+    t = s.tuning()
+    assert t["schedule"][0] == FUSED and t["update"][1] == (128, 32)
     assert s.launches_per_step() == 2
 
 

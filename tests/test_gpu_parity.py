@@ -391,6 +391,39 @@ def test_config2_full_size_mixed_against_fp64(sgn):
     assert np.abs(qm[0] - q64[0]).max() <= 1e-3 * 5.0
 
 
+def test_config2_full_size_mixed_against_fp64_1000_steps(sgn):
+    """Full 4096 x 4096 second configuration over 1000 steps, each path on its
+    own CFL steps, at the bar frozen from the measured run: relative L2 over wet
+    cells eta <= 2e-4, hu, hv <= 1e-3; max |eta| error <= 5e-3 of the 5 m source
+    amplitude; the 64 gauges' arrival times (first time |eta| reaches 1 % of
+    its largest value there) within one time step."""
+    c = W.config2(model=2)
+    cfg = dict(dx=c["dx"], model=2, bc=c["bc"], h_star=c["h_star"], alpha=3.0)
+    steps = 1000
+    out, gauges = [], []
+    for prec in (0, 1):
+        s = sgn.Solver(c["b"], precision=prec, **cfg)
+        s.set_state(c["q"])
+        s.add_gauges(c["gauges"], steps + 4)
+        s.step(steps)
+        assert s.status()[0] == 0
+        out.append(s.get_state()[0])
+        gauges.append(s.gauges())
+        if prec == 0:
+            dt = s.status()[1]
+        del s
+    q64, qm = out
+    wet = (q64[0] - c["b"]) > 1e-3
+    err = rel_l2(qm[:3], q64[:3], wet)
+    assert err[0] <= 2e-4 and err[1] <= 1e-3 and err[2] <= 1e-3, err
+    assert np.abs(qm[0] - q64[0]).max() <= 5e-3 * 5.0
+    g64, gm = gauges
+    ta, tb = _arrival_times(g64), _arrival_times(gm)
+    ok = ~np.isnan(ta) & ~np.isnan(tb) & (np.abs(g64[:, :, 1]).max(axis=0) >= 0.01)
+    assert ok.sum() >= 32
+    assert np.nanmax(np.abs(ta[ok] - tb[ok])) <= dt * 1.0001
+
+
 def test_c2_override_matches_oracle(sgn, oracle_mod):
     """A prescribed relaxation field (sgn_set_c2; the constant-c^2 setting of
     the Sec. 5.3 steady-state test, here a varying positive field) gives the

@@ -120,7 +120,7 @@ def test_autotune_report(S):
     assert [tun[n][0] for n in S.TUNE_SLOTS] == ch
     assert tun["face_x"][1][0] * tun["face_x"][1][1] in (128, 256, 512)
     if ch[-1] == 2:
-        assert tun["update"][1][0] == 128 and tun["update"][1][1] in (64, 128, 256)
+        assert tun["update"][1][0] == 128 and tun["update"][1][1] in (32, 64, 128, 256)
     assert tun["schedule"][1] == (0, 0)
     s.step(3)
     assert s.status()[0] == 0
@@ -141,8 +141,12 @@ def test_tuning_arguments(S):
     assert e.value.code == -1
     # a rejected tuning leaves the previous one (FP64 solver: schedule 0 by default)
     assert all(v[0] == 0 for v in s.tuning().values())
-    # a mixed solver starts on the one-pass schedule
+    # a mixed solver on a grid this small starts on the kernel sequence (the
+    # one-pass default on large grids: test_gpu_fused.py); the one-pass schedule
+    # is accepted
     s2 = S.Solver(b, model=1, dx=0.05, precision=1)
+    assert s2.tuning()["schedule"][0] == 0
+    s2.set_tuning([0] * 7 + [2])
     assert s2.tuning()["schedule"][0] == 2
 
 
