@@ -2,16 +2,25 @@
 // patches, refinement ratio r, subcycling in time).
 //
 // Each level is one padded "atlas" grid holding all of its patches (each with
-// its own two-layer ghost frame, packed on shelves), stepped by the uniform
-// solver's kernels with a kind mask (patch interior / covered): every stage is
-// one launch over all patches of the level.  Around them, per level:
-//   k_amr_fill     ghost cells from siblings (copy) and the parent (limited
-//                  interpolation in space of the surface and primitives, linear
-//                  in time), k_amr_fill_bc the boundary-condition ghosts,
-//   k_amr_theta    positivity factors of sibling ghosts,
-//   k_amr_reg_*    mass-flux registers at coarse/fine faces,
-//   k_amr_avg      average-down, k_amr_reflux the mass correction,
-//   k_amr_finalize the level-0 step from the speeds of all levels.
+// its own ghost frame, packed on shelves), stepped with a kind mask (patch
+// interior / covered / sibling ghost / exported cell): every stage is one
+// launch over all patches of the level.
+//
+// Mixed precision (the default): the frames are three cells deep and each
+// level step is ONE launch of the one-pass kernel k_step_fused over the atlas:
+// it computes the positivity factors of the sibling ghosts next to a patch
+// edge itself (the third layer makes them equal to the sibling's own) and
+// writes the theta-weighted mass fluxes of the cells beside coarse/fine faces
+// to the level's export buffer.  FP64 (and the mixed kernel-sequence
+// schedules): two-layer frames, the seven-kernel sequence, k_amr_theta copies
+// the sibling ghosts' positivity factors and k_amr_export reads the exported
+// fluxes from the face planes.  Around the step, per level:
+//   k_amr_fill       ghost cells from siblings (copy) and the parent (limited
+//                    interpolation in space of the surface and primitives,
+//                    linear in time), k_amr_fill_bc the boundary-condition ghosts,
+//   k_amr_avg_reflux average-down and the mass correction at coarse/fine faces
+//                    from the exported fluxes of both levels (one launch),
+//   k_amr_finalize   the level-0 step from the speeds of all levels.
 // A level-0 step with all substeps is captured once per ping-pong state and
 // replayed as a CUDA graph.
 #pragma once
@@ -29,13 +38,18 @@ namespace sgn {
 constexpr int AMR_MAXL = 8;
 
 // ghost-table entry: dst/src padded indices; info: bits 0-1 type, BC: bit 2/3
-// flip hu/hv; PAR: bits 8-15 / 16-23 sub-cell offsets, 24-27 neighbour flags W E S N
+// flip hu/hv; PAR: bits 8-15 / 16-23 sub-cell offsets.  A PAR entry's stencil
+// (the parent-level cells W, E, S, N of its parent cell) is a separate int4 of
+// padded indices into the parent level's atlas, -1 where the level has no patch
+// there or the cell is outside the domain: each stencil cell is read from the
+// patch that holds it, so a ghost's value depends only on where it is, not on
+// which patch's frame holds it.
 struct GEnt { int dst, src, info; };
 enum { GE_SIB = 0, GE_PAR = 1, GE_BC = 2 };
 
 template <int MODEL, typename Real>
-__global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t, int n, int cc, int pold, int pnew,
-                           double a, int r) {
+__global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t, const int4* __restrict__ nbt, int n,
+                           int cc, int pold, int pnew, double a, int r) {
   constexpr int NV = MT<MODEL>::NV;
   // the interpolation runs in the bulk type (the depth of a parent cell, which
   // decides dry or wet, in FP64): a ghost value is an input of the step, not
@@ -50,7 +64,8 @@ __global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t,
     for (int k = 0; k < NV; k++) qc[k * c.fs + g.dst] = qc[k * c.fs + g.src];
     return;
   }
-  const int sx = (g.info >> 8) & 255, sy = (g.info >> 16) & 255, nb = (g.info >> 24) & 15;
+  const int sx = (g.info >> 8) & 255, sy = (g.info >> 16) & 255;
+  const int4 nv = nbt[e];
   const Real* qo = p.q[pold];
   const Real* qn = p.q[pnew];
   const A a1 = A(a), a0 = A(1.0 - a);
@@ -76,8 +91,8 @@ __global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t,
     for (int k = 1; k < NV; k++) qc[k * c.fs + g.dst] = Real(0);
     return;
   }
-  const bool hx = (nb & 1) && (nb & 2) && prim(ic - 1, pw) && prim(ic + 1, pe);
-  const bool hy = (nb & 4) && (nb & 8) && prim(ic - p.pitch, ps) && prim(ic + p.pitch, pn);
+  const bool hx = nv.x >= 0 && nv.y >= 0 && prim((size_t)nv.x, pw) && prim((size_t)nv.y, pe);
+  const bool hy = nv.z >= 0 && nv.w >= 0 && prim((size_t)nv.z, ps) && prim((size_t)nv.w, pn);
   const A xi = A((sx + 0.5) / r - 0.5), yi = A((sy + 0.5) / r - 0.5);
   auto mm = [](A u, A v) -> A { return u * v <= A(0) ? A(0) : (fabs(u) < fabs(v) ? u : v); };
 #pragma unroll
@@ -158,75 +173,85 @@ __global__ void k_amr_flag(Dev<Real> d, int cur, double tol, unsigned char* __re
   out[id] = f;
 }
 
-// theta-weighted mass flux at a face as k_update applies it (bulk precision)
+// Kernel-sequence levels: the theta-weighted mass fluxes of the four faces
+// (left, right, bottom, top) of every exported cell, in the bulk type, from
+// the face planes as k_update applies them; cells[k] has export slot k.  The
+// one-pass kernel writes the same values itself.
 template <typename Real>
-__device__ __forceinline__ double face_phi(const Dev<Real>& d, size_t id, int dir) {
-  const Real M = dir == 0 ? d.TX[id] : d.TY[id];
-  const size_t idL = dir == 0 ? id - 1 : id - d.pitch;
-  const Real t = M > Real(0) ? d.theta[idL] : (M < Real(0) ? d.theta[id] : Real(1));
-  return (double)(t * M);
+__global__ void k_amr_export(Dev<Real> d, const int* __restrict__ cells, int n, Real* __restrict__ xphi) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const size_t id = (size_t)cells[e];
+  auto phi = [&](size_t f, size_t fl, Real M) {   // face f between cells fl and f
+    const Real t = M > Real(0) ? d.theta[fl] : (M < Real(0) ? d.theta[f] : Real(1));
+    return t * M;
+  };
+  Real* o = xphi + 4 * (size_t)e;
+  o[0] = phi(id, id - 1, d.TX[id]);
+  o[1] = phi(id + 1, id, d.TX[id + 1]);
+  o[2] = phi(id, id - d.pitch, d.TY[id]);
+  o[3] = phi(id + d.pitch, id, d.TY[id + d.pitch]);
 }
 
-template <typename Real>
-__global__ void k_amr_reg_coarse(Dev<Real> d, const int* __restrict__ face, const signed char* __restrict__ dir,
-                                 const signed char* __restrict__ sgn, double* __restrict__ val, int n) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const int dr = dir[g];
-  val[g] = ((double)sgn[g] * d.lam[dr]) * face_phi(d, (size_t)face[g], dr);
-}
-
-template <typename Real>
-__global__ void k_amr_reg_fine(Dev<Real> f, const int* __restrict__ face, const signed char* __restrict__ dir,
-                               const signed char* __restrict__ sgn, double* __restrict__ val, int n, int r) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const int dr = dir[g];
-  const size_t stride = dr == 0 ? (size_t)f.pitch : 1;
-  double s = 0.0;
-  for (int m = 0; m < r; m++) s += face_phi(f, (size_t)face[g] + m * stride, dr);
-  const double coef = f.lam[dr] / (double)(r * r);
-  val[g] -= ((double)sgn[g] * coef) * s;
-}
-
+// Average-down and reflux of a coarse level after its finer level's r
+// substeps (one launch; the two touch disjoint cells).  Threads [0, navg):
+// covered coarse cell ci[g] takes the mean of its r x r children (the surface
+// summed in FP64).  Threads [navg, navg + m): uncovered coarse cell cell[g]
+// next to the finer patches gets the mass correction of its coarse/fine faces
+// (registers first[g] .. first[g+1]-1, fixed order): for register i with
+// direction dir[i] and sign sgn[i],
+//   v_i = sgn lam_c phi_c[cref[i]] - sum_k sgn (lam_f / r^2) sum_m phi_f[k][fref[i r + m]],
+// phi_c: the coarse level's exported fluxes of this step, phi_f: the finer
+// level's of its substeps k = 0 .. r-1 (nf4 values apart); a correction that
+// would leave a negative depth is clipped and the water added accumulated.
 template <int MODEL, typename Real>
-__global__ void k_amr_avg(Dev<Real> cd, Dev<Real> fd, const int* __restrict__ ci, const int* __restrict__ fi, int n,
-                          int cc, int fc, int r) {
+__global__ void k_amr_avg_reflux(Dev<Real> cd, Dev<Real> fd, const int* __restrict__ ci, const int* __restrict__ fi,
+                                 int navg, const int* __restrict__ cell, const int* __restrict__ first, int m,
+                                 const int* __restrict__ cref, const signed char* __restrict__ dir,
+                                 const signed char* __restrict__ sgn, const int* __restrict__ fref,
+                                 const Real* __restrict__ phic, const Real* __restrict__ phif, size_t nf4, int cc,
+                                 int fc, int r, double area, double* clipped) {
   constexpr int NV = MT<MODEL>::NV;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const size_t f0 = (size_t)fi[g];
-  // the surface (mass) is summed in FP64; the other fields in the bulk type
-  {
-    double s = 0.0;
-    for (int dj = 0; dj < r; dj++)
-      for (int di = 0; di < r; di++) s += (double)fd.q[fc][f0 + (size_t)dj * fd.pitch + di];
-    cd.q[cc][ci[g]] = (Real)(s / (double)(r * r));
-  }
+  if (g < navg) {
+    const size_t f0 = (size_t)fi[g];
+    {
+      double s = 0.0;
+      for (int dj = 0; dj < r; dj++)
+        for (int di = 0; di < r; di++) s += (double)fd.q[fc][f0 + (size_t)dj * fd.pitch + di];
+      cd.q[cc][ci[g]] = (Real)(s / (double)(r * r));
+    }
 #pragma unroll
-  for (int k = 1; k < NV; k++) {
-    Real s = Real(0);
-    for (int dj = 0; dj < r; dj++)
-      for (int di = 0; di < r; di++) s += fd.q[fc][k * fd.fs + f0 + (size_t)dj * fd.pitch + di];
-    cd.q[cc][k * cd.fs + ci[g]] = s / Real(r * r);
+    for (int k = 1; k < NV; k++) {
+      Real s = Real(0);
+      for (int dj = 0; dj < r; dj++)
+        for (int di = 0; di < r; di++) s += fd.q[fc][k * fd.fs + f0 + (size_t)dj * fd.pitch + di];
+      cd.q[cc][k * cd.fs + ci[g]] = s / Real(r * r);
+    }
+    return;
   }
-}
-
-template <typename Real>
-__global__ void k_amr_reflux(Dev<Real> d, const int* __restrict__ cell, const int* __restrict__ first,
-                             const double* __restrict__ val, int m, int cc, double area, double* clipped) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  g -= navg;
   if (g >= m) return;
   double corr = 0.0;
-  for (int i = first[g]; i < first[g + 1]; i++) corr += val[i];
+  for (int i = first[g]; i < first[g + 1]; i++) {
+    const int dr = dir[i];
+    double v = ((double)sgn[i] * cd.lam[dr]) * (double)phic[cref[i]];
+    const double coef = fd.lam[dr] / (double)(r * r);
+    for (int k = 0; k < r; k++) {
+      double s = 0.0;
+      for (int q = 0; q < r; q++) s += (double)phif[(size_t)k * nf4 + fref[(size_t)i * r + q]];
+      v -= ((double)sgn[i] * coef) * s;
+    }
+    corr += v;
+  }
   const size_t id = (size_t)cell[g];
-  double e = (double)d.q[cc][id] + corr;
-  const double b = (double)d.b[id];
+  double e = (double)cd.q[cc][id] + corr;
+  const double b = (double)cd.b[id];
   if (e < b) {
     atomicAdd(clipped, (b - e) * area);
     e = b;
   }
-  d.q[cc][id] = (Real)e;
+  cd.q[cc][id] = (Real)e;
 }
 
 // mass partials over uncovered patch interiors (kind == 1)
@@ -238,7 +263,7 @@ __global__ void k_amr_mass1(Dev<Real> d, int cur) {
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
     int i = (int)(c % d.nx), j = (int)(c / d.nx);
     size_t id = at(d.pitch, i + NG, j + NG);
-    if (d.kind[id] != 1) continue;
+    if ((d.kind[id] & 3) != 1) continue;
     double h = (double)d.q[cur][id] - (double)d.b[id];
     s += h > 0 ? h : 0.0;
   }
@@ -252,13 +277,13 @@ __global__ void k_amr_mass1(Dev<Real> d, int cur) {
 }
 
 // copy one patch interior between a dense nv x ny x nx buffer and the atlas;
-// (px, py): padded atlas index of the patch frame's corner
+// (px, py): padded atlas index of the patch's first interior cell
 template <int MODEL, typename Real>
 __global__ void k_amr_pack(Dev<Real> d, const double* qd, int px, int py, int nx, int ny, int cur) {
   constexpr int NV = MT<MODEL>::NV;
   int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= ny) return;
-  size_t id = at(d.pitch, px + NG + i, py + NG + j), n = (size_t)nx * ny, s = (size_t)j * nx + i;
+  size_t id = at(d.pitch, px + i, py + j), n = (size_t)nx * ny, s = (size_t)j * nx + i;
   Real q[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) q[k] = (Real)qd[k * n + s];
@@ -274,14 +299,14 @@ __global__ void k_amr_unpack(Dev<Real> d, double* qd, int px, int py, int nx, in
   constexpr int NV = MT<MODEL>::NV;
   int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= ny) return;
-  size_t id = at(d.pitch, px + NG + i, py + NG + j), n = (size_t)nx * ny, s = (size_t)j * nx + i;
+  size_t id = at(d.pitch, px + i, py + j), n = (size_t)nx * ny, s = (size_t)j * nx + i;
 #pragma unroll
   for (int k = 0; k < NV; k++) qd[k * n + s] = (double)d.q[cur][k * d.fs + id];
 }
 
 // Interior cells of every patch of a level into a dense device field
-// (fields [0, nf) of [field][NY][NX]); tab: px, py, nx, ny, i0, j0 per patch,
-// one patch per blockIdx.z.
+// (fields [0, nf) of [field][NY][NX]); tab: px, py (padded index of the first
+// interior cell), nx, ny, i0, j0 per patch, one patch per blockIdx.z.
 template <int MODEL, typename Real>
 __global__ void k_amr_scatter(Dev<Real> d, const int* __restrict__ tab, int nf, double* __restrict__ out, int NX,
                               int NY, int cur) {
@@ -289,7 +314,7 @@ __global__ void k_amr_scatter(Dev<Real> d, const int* __restrict__ tab, int nf, 
   const int px = t[0], py = t[1], nx = t[2], ny = t[3], i0 = t[4], j0 = t[5];
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= nx || j >= ny) return;
-  const size_t id = at(d.pitch, px + NG + i, py + NG + j);
+  const size_t id = at(d.pitch, px + i, py + j);
   const size_t o = (size_t)(j0 + j) * NX + (i0 + i), plane = (size_t)NX * NY;
   for (int k = 0; k < nf; k++) out[k * plane + o] = (double)d.q[cur][k * d.fs + id];
 }
@@ -411,7 +436,9 @@ AmrBase* make_amr_mixed(int model);
 
 // ---------------------------------------------------------------------------
 // host side: hierarchy geometry, atlas packing, tables
-struct Box { int i0, j0, nx, ny; int px, py; int parent; };   // (px, py): padded index of the frame corner
+// (px, py): padded atlas index of the frame corner (frame cell (0, 0); the
+// first interior cell is frame cell (G, G), G the frame depth)
+struct Box { int i0, j0, nx, ny; int px, py; int parent; };
 
 inline int bc_index(int X, int N, int lo, int hi, bool& flip) {
   flip = false;
@@ -450,6 +477,12 @@ struct Owner {
 template <int MODEL, typename Real>
 class Amr : public AmrBase {
   static constexpr int NV = MT<MODEL>::NV;
+  // ghost layers of a patch frame: three in mixed precision, where the
+  // one-pass kernel computes the positivity factors of sibling ghosts next to
+  // a patch edge itself (their faces' fluxes reach two cells further out); two
+  // where the kernel sequence copies them from the sibling
+  static constexpr int G = sizeof(Real) == 4 ? 3 : 2;
+  bool fused_ = false;   // every level stepped by the one-pass kernel
   int L_ = 1, r_ = 2;
   sgn_grid g0_{};
   sgn_params prm_{};
@@ -458,13 +491,17 @@ class Amr : public AmrBase {
   std::vector<int> NX_, NY_;
   std::vector<double> dx_;
   struct Tabs {
-    GEnt* fill = nullptr; int nfill = 0;      // SIB + PAR
+    GEnt* fill = nullptr; int4* fillnb = nullptr; int nfill = 0;   // SIB + PAR (and the PAR stencils)
     GEnt* bc = nullptr; int nbc = 0;
-    int* rface_c = nullptr; int* rface_f = nullptr; signed char* rdir = nullptr; signed char* rsgn = nullptr;
-    double* rval = nullptr; int nreg = 0;     // registers of this level (as the coarse side)
+    int* xcell = nullptr; int nxc = 0;        // exported cells of this level, by slot
+    Real* xphi = nullptr;                     // their face fluxes: (l ? r : 1) substeps x nxc x 4
+    // registers of this level as the coarse side, grouped by corrected cell
+    int* rcref = nullptr; int* rfref = nullptr; signed char* rdir = nullptr; signed char* rsgn = nullptr;
+    int nreg = 0;
     int* rcell = nullptr; int* rfirst = nullptr; int ncell = 0;
     int* acoarse = nullptr; int* afine = nullptr; int navg = 0;
   };
+  std::vector<Owner> own_;     // per level: box lookup by cell
   std::vector<Tabs> tb_;
   std::vector<long long> cells_, atlas_;
   CoarseBath bath_;            // bathymetry of levels 0 .. L-2
@@ -532,7 +569,8 @@ class Amr : public AmrBase {
       for (size_t k = 0; k + 3 < v.size(); k += 4) bx_[l].push_back(Box{v[k], v[k + 1], v[k + 2], v[k + 3], 0, 0, -1});
     }
     // validation (the rules of the header)
-    std::vector<Owner> own(L);
+    own_.assign(L, Owner{});
+    std::vector<Owner>& own = own_;
     for (int l = 1; l < L; l++)
       for (const Box& b : bx_[l])
         if (b.i0 < 0 || b.j0 < 0 || b.nx < 2 || b.ny < 2 || b.i0 + b.nx > NX_[l] || b.j0 + b.ny > NY_[l] ||
@@ -610,34 +648,37 @@ class Amr : public AmrBase {
     // atlases and level solvers
     lv_.assign(L, nullptr);
     cells_.assign(L, 0); atlas_.assign(L, 0);
+    std::vector<int> NXA(L), NYA(L);
     for (int l = 0; l < L; l++) {
       CreateArgs ca{};
       ca.prm = prm_; ca.model = a.model; ca.alloc = a.alloc; ca.stream = st_;
       ca.no_initial_state = a.prev != nullptr;   // a regrid fills every level from the old hierarchy
       std::vector<double> bd;
-      std::vector<unsigned char> pd, kd;
+      std::vector<unsigned char> pd;
       int nxa, nya;
       for (auto& b : bx_[l]) cells_[l] += (long long)b.nx * b.ny;
       if (l == 0) {
         nxa = g0_.nx; nya = g0_.ny;
         ca.grid = g0_;
         bd.assign(blev(0), blev(0) + (size_t)NX_[0] * NY_[0]);
+        bx_[0][0].px = NG - G;   // level 0's frame is the atlas's own
+        bx_[0][0].py = NG - G;
       } else {
-        // shelf packing of the (nx+4) x (ny+4) frames, tallest first
+        // shelf packing of the (nx + 2G) x (ny + 2G) frames, tallest first
         std::vector<int> ord(bx_[l].size());
         for (size_t k = 0; k < ord.size(); k++) ord[k] = (int)k;
         std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return bx_[l][u].ny > bx_[l][v].ny; });
         double area = 0;
         int maxw = 2;
-        for (auto& b : bx_[l]) { area += (double)(b.nx + 4) * (b.ny + 4); maxw = std::max(maxw, b.nx + 4); }
+        for (auto& b : bx_[l]) { area += (double)(b.nx + 2 * G) * (b.ny + 2 * G); maxw = std::max(maxw, b.nx + 2 * G); }
         nxa = std::max(maxw, (int)std::ceil(std::sqrt(area * 1.1)));
         int x = 0, y = 0, sh = 0;
         for (int k : ord) {
           Box& b = bx_[l][k];
-          if (x + b.nx + 4 > nxa) { x = 0; y += sh; sh = 0; }
+          if (x + b.nx + 2 * G > nxa) { x = 0; y += sh; sh = 0; }
           b.px = x + NG; b.py = y + NG;   // the atlas has its own two-cell frame
-          x += b.nx + 4;
-          sh = std::max(sh, b.ny + 4);
+          x += b.nx + 2 * G;
+          sh = std::max(sh, b.ny + 2 * G);
         }
         nya = std::max(2, y + sh);
         ca.grid = g0_;
@@ -647,14 +688,15 @@ class Amr : public AmrBase {
         bd.assign((size_t)nxa * nya, 1000.0);   // empty atlas cells: dry land
         pd.assign((size_t)nxa * nya, 0);
         for (auto& b : bx_[l])
-          for (int J = 0; J < b.ny + 4; J++)
-            for (int I = 0; I < b.nx + 4; I++) {
-              int X = b.i0 - 2 + I, Y = b.j0 - 2 + J;
+          for (int J = 0; J < b.ny + 2 * G; J++)
+            for (int I = 0; I < b.nx + 2 * G; I++) {
+              int X = b.i0 - G + I, Y = b.j0 - G + J;
               size_t o = (size_t)(b.py - NG + J) * nxa + (b.px - NG + I);
               bd[o] = bval(l, X, Y);
               pd[o] = phival(l, X, Y);
             }
       }
+      NXA[l] = nxa; NYA[l] = nya;
       atlas_[l] = (long long)(nxa + 4) * (nya + 4);
       if ((long long)((nxa + 5 + 31) / 32 * 32) * (nya + 5) >= (1LL << 31)) return SGN_EINVAL;
       ca.b = bd.data();
@@ -662,66 +704,88 @@ class Amr : public AmrBase {
       lv_[l] = new Solver<MODEL, Real>();
       int rc = lv_[l]->init(ca);
       if (rc) return rc;
-      // kind: 1 interior, +2 covered by the next level; interior cell (i, j) of
-      // a box is dense atlas cell (px - NG + 2 + i, py - NG + 2 + j)
-      kd.assign((size_t)nxa * nya, 0);
+    }
+    // kind planes (bit 0 interior, 1 covered by the next level, 2 sibling
+    // ghost next to a patch edge, 3 exported cell) and export slots, dense
+    // over each atlas; frame cell (I, J) of box b is dense atlas cell
+    // (px - NG + I, py - NG + J)
+    std::vector<std::vector<unsigned char>> kd(L);
+    std::vector<std::vector<int>> xs(L);
+    std::vector<std::vector<int>> xcells(L);
+    auto dense = [&](int l, const Box& b, int I, int J) {
+      return (size_t)(b.py - NG + J) * NXA[l] + (size_t)(b.px - NG + I);
+    };
+    for (int l = 0; l < L; l++) {
+      kd[l].assign((size_t)NXA[l] * NYA[l], 0);
+      xs[l].assign((size_t)NXA[l] * NYA[l], -1);
       for (int k = 0; k < (int)bx_[l].size(); k++) {
         const Box& b = bx_[l][k];
         for (int j = 0; j < b.ny; j++)
           for (int i = 0; i < b.nx; i++) {
             unsigned char v = 1;
             if (l + 1 < L && own[l + 1].find((b.i0 + i) * r, (b.j0 + j) * r) >= 0) v |= 2;
-            kd[(size_t)(b.py + j) * nxa + (b.px + i)] = v;
+            kd[l][dense(l, b, G + i, G + j)] = v;
           }
       }
-      rc = lv_[l]->set_kind(kd.data());
-      if (rc) return rc;
     }
-    tb_.assign(L, Tabs{});
-    // padded atlas index of frame cell (I, J) of box b on level l
-    auto pidx = [&](int l, const Box& b, int I, int J) {
-      return (int)((size_t)(b.py + J) * lv_[l]->dev().pitch + (b.px + I));
+    // export slot of a cell (assigned on first use)
+    auto slot_of = [&](int l, const Box& b, int I, int J) {
+      const size_t o = dense(l, b, I, J);
+      if (xs[l][o] < 0) {
+        xs[l][o] = (int)xcells[l].size();
+        xcells[l].push_back(pidx(l, b, I, J));
+        kd[l][o] |= 8;
+      }
+      return xs[l][o];
     };
+    tb_.assign(L, Tabs{});
     for (int l = 1; l < L; l++) {
       std::vector<GEnt> fill, bcs;
+      std::vector<int4> fnb;
       for (int k = 0; k < (int)bx_[l].size(); k++) {
         const Box& b = bx_[l][k];
-        const Box& P = bx_[l - 1][b.parent];
-        for (int J = 0; J < b.ny + 4; J++)
-          for (int I = 0; I < b.nx + 4; I++) {
-            if (I >= 2 && I < b.nx + 2 && J >= 2 && J < b.ny + 2) continue;
-            int X = b.i0 - 2 + I, Y = b.j0 - 2 + J;
+        for (int J = 0; J < b.ny + 2 * G; J++)
+          for (int I = 0; I < b.nx + 2 * G; I++) {
+            if (I >= G && I < b.nx + G && J >= G && J < b.ny + G) continue;
+            int X = b.i0 - G + I, Y = b.j0 - G + J;
             int dst = pidx(l, b, I, J);
             if (X < 0 || Y < 0 || X >= NX_[l] || Y >= NY_[l]) {
               bool fx, fy;
               int Xs = bc_index(X, NX_[l], g0_.bc[0], g0_.bc[1], fx);
               int Ys = bc_index(Y, NY_[l], g0_.bc[2], g0_.bc[3], fy);
-              int Is = Xs - b.i0 + 2, Js = Ys - b.j0 + 2;
-              if (Is < 0 || Js < 0 || Is >= b.nx + 4 || Js >= b.ny + 4) return SGN_EINVAL;
+              int Is = Xs - b.i0 + G, Js = Ys - b.j0 + G;
+              if (Is < 0 || Js < 0 || Is >= b.nx + 2 * G || Js >= b.ny + 2 * G) return SGN_EINVAL;
               bcs.push_back(GEnt{dst, pidx(l, b, Is, Js), GE_BC | (fx ? 4 : 0) | (fy ? 8 : 0)});
               continue;
             }
             int o = own[l].find(X, Y, k);
             if (o >= 0) {
               const Box& s = bx_[l][o];
-              fill.push_back(GEnt{dst, pidx(l, s, X - s.i0 + 2, Y - s.j0 + 2), GE_SIB});
+              fill.push_back(GEnt{dst, pidx(l, s, X - s.i0 + G, Y - s.j0 + G), GE_SIB});
+              fnb.push_back(make_int4(-1, -1, -1, -1));
+              // a sibling ghost sharing a face with an interior cell
+              const bool side = ((I == G - 1 || I == G + b.nx) && J >= G && J < G + b.ny) ||
+                                ((J == G - 1 || J == G + b.ny) && I >= G && I < G + b.nx);
+              if (side) kd[l][dense(l, b, I, J)] |= 4;
               continue;
             }
-            int ic = X / r, jc = Y / r;
-            int nb = (ic - 1 >= 0 ? 1 : 0) | (ic + 1 < NX_[l - 1] ? 2 : 0) | (jc - 1 >= 0 ? 4 : 0) |
-                     (jc + 1 < NY_[l - 1] ? 8 : 0);
-            int Ip = ic - P.i0 + 2, Jp = jc - P.j0 + 2;
-            if (Ip - 1 < 0 || Jp - 1 < 0 || Ip + 1 >= P.nx + 4 || Jp + 1 >= P.ny + 4) return SGN_EINVAL;
-            fill.push_back(GEnt{dst, pidx(l - 1, P, Ip, Jp), GE_PAR | ((X % r) << 8) | ((Y % r) << 16) | (nb << 24)});
+            GEnt e;
+            int4 nv;
+            if (!par_entry(l, b, X, Y, dst, e, nv)) return SGN_EINVAL;
+            fill.push_back(e);
+            fnb.push_back(nv);
           }
       }
-      tb_[l].fill = up(fill); tb_[l].nfill = (int)fill.size();
+      tb_[l].fill = up(fill); tb_[l].fillnb = up(fnb); tb_[l].nfill = (int)fill.size();
       tb_[l].bc = up(bcs); tb_[l].nbc = (int)bcs.size();
-      if ((tb_[l].nfill && !tb_[l].fill) || (tb_[l].nbc && !tb_[l].bc)) return SGN_ENOMEM;
+      if ((tb_[l].nfill && (!tb_[l].fill || !tb_[l].fillnb)) || (tb_[l].nbc && !tb_[l].bc)) return SGN_ENOMEM;
     }
-    // registers and average-down maps of level l (coarse side)
+    // registers and average-down maps of level l (coarse side).  A register
+    // is a coarse face between an uncovered cell u and a covered one: its
+    // coarse flux is exported by u (the face of u it is), its r fine fluxes by
+    // the fine interior cells along the patch edge.
     for (int l = 0; l + 1 < L; l++) {
-      std::vector<int> fc, ff, af, ac, cellof;
+      std::vector<int> af, ac, cellof, cref, fref;
       std::vector<signed char> dr, sg;
       for (int ci = 0; ci < (int)bx_[l + 1].size(); ci++) {
         const Box& c = bx_[l + 1][ci];
@@ -729,49 +793,54 @@ class Amr : public AmrBase {
         int c0 = c.i0 / r, d0 = c.j0 / r, cw = c.nx / r, ch = c.ny / r;
         for (int jc = d0; jc < d0 + ch; jc++)
           for (int ic = c0; ic < c0 + cw; ic++) {
-            ac.push_back(pidx(l, P, ic - P.i0 + 2, jc - P.j0 + 2));
-            af.push_back(pidx(l + 1, c, (ic - c0) * r + 2, (jc - d0) * r + 2));
+            ac.push_back(pidx(l, P, ic - P.i0 + G, jc - P.j0 + G));
+            af.push_back(pidx(l + 1, c, (ic - c0) * r + G, (jc - d0) * r + G));
           }
-        struct Cand { int d, ux, uy, fx, fy, s, fI, fJ; };
+        // d: direction; (ux, uy): the uncovered coarse cell; s: sign; fu: the
+        // face of u; (fI, fJ): frame index of the first fine cell along the
+        // edge, (sI, sJ) the step to the next; ff: their face on the edge
+        struct Cand { int d, ux, uy, s, fu, fI, fJ, sI, sJ, ff; };
         std::vector<Cand> cand;
         for (int jc = d0; jc < d0 + ch; jc++) {
-          cand.push_back(Cand{0, c0 - 1, jc, c0, jc, +1, 2, (jc - d0) * r + 2});
-          cand.push_back(Cand{0, c0 + cw, jc, c0 + cw, jc, -1, c.nx + 2, (jc - d0) * r + 2});
+          cand.push_back(Cand{0, c0 - 1, jc, +1, 1, G, (jc - d0) * r + G, 0, 1, 0});
+          cand.push_back(Cand{0, c0 + cw, jc, -1, 0, G + c.nx - 1, (jc - d0) * r + G, 0, 1, 1});
         }
         for (int ic = c0; ic < c0 + cw; ic++) {
-          cand.push_back(Cand{1, ic, d0 - 1, ic, d0, +1, (ic - c0) * r + 2, 2});
-          cand.push_back(Cand{1, ic, d0 + ch, ic, d0 + ch, -1, (ic - c0) * r + 2, c.ny + 2});
+          cand.push_back(Cand{1, ic, d0 - 1, +1, 3, (ic - c0) * r + G, G, 1, 0, 2});
+          cand.push_back(Cand{1, ic, d0 + ch, -1, 2, (ic - c0) * r + G, G + c.ny - 1, 1, 0, 3});
         }
         for (const Cand& q : cand) {
           if (q.ux < 0 || q.uy < 0 || q.ux >= NX_[l] || q.uy >= NY_[l]) continue;
           if (own[l + 1].find(q.ux * r, q.uy * r) >= 0) continue;   // covered: a sibling face
-          fc.push_back(pidx(l, P, q.fx - P.i0 + 2, q.fy - P.j0 + 2));
-          ff.push_back(pidx(l + 1, c, q.fI, q.fJ));
+          const int uI = q.ux - P.i0 + G, uJ = q.uy - P.j0 + G;
+          cref.push_back(4 * slot_of(l, P, uI, uJ) + q.fu);
+          for (int m = 0; m < r; m++) fref.push_back(4 * slot_of(l + 1, c, q.fI + m * q.sI, q.fJ + m * q.sJ) + q.ff);
           dr.push_back((signed char)q.d);
           sg.push_back((signed char)q.s);
-          cellof.push_back(pidx(l, P, q.ux - P.i0 + 2, q.uy - P.j0 + 2));
+          cellof.push_back(pidx(l, P, uI, uJ));
         }
       }
       // group the registers by corrected cell (creation order within a cell)
       std::vector<int> order(cellof.size());
       for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
       std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return cellof[u] < cellof[v]; });
-      std::vector<int> fc2, ff2, cells, first;
+      std::vector<int> cref2, fref2, cells, first;
       std::vector<signed char> dr2, sg2;
       for (size_t i = 0; i < order.size(); i++) {
         int g = order[i];
         if (i == 0 || cellof[g] != cellof[order[i - 1]]) { cells.push_back(cellof[g]); first.push_back((int)i); }
-        fc2.push_back(fc[g]); ff2.push_back(ff[g]); dr2.push_back(dr[g]); sg2.push_back(sg[g]);
+        cref2.push_back(cref[g]);
+        for (int m = 0; m < r; m++) fref2.push_back(fref[(size_t)g * r + m]);
+        dr2.push_back(dr[g]); sg2.push_back(sg[g]);
       }
       first.push_back((int)order.size());
       Tabs& t = tb_[l];
-      t.nreg = (int)fc2.size();
+      t.nreg = (int)cref2.size();
       if (t.nreg) {
-        t.rface_c = up(fc2); t.rface_f = up(ff2); t.rdir = up(dr2); t.rsgn = up(sg2);
-        t.rval = lv_[0]->template alloc_dev<double>(t.nreg);
+        t.rcref = up(cref2); t.rfref = up(fref2); t.rdir = up(dr2); t.rsgn = up(sg2);
         t.ncell = (int)cells.size();
         t.rcell = up(cells); t.rfirst = up(first);
-        if (!t.rface_c || !t.rface_f || !t.rdir || !t.rsgn || !t.rval || !t.rcell || !t.rfirst) return SGN_ENOMEM;
+        if (!t.rcref || !t.rfref || !t.rdir || !t.rsgn || !t.rcell || !t.rfirst) return SGN_ENOMEM;
       }
       t.navg = (int)ac.size();
       if (t.navg) {
@@ -779,6 +848,23 @@ class Amr : public AmrBase {
         if (!t.acoarse || !t.afine) return SGN_ENOMEM;
       }
     }
+    for (int l = 0; l < L; l++) {
+      Tabs& t = tb_[l];
+      t.nxc = (int)xcells[l].size();
+      if (t.nxc) {
+        t.xcell = up(xcells[l]);
+        t.xphi = lv_[0]->template alloc_dev<Real>((size_t)(l ? r : 1) * t.nxc * 4);
+        if (!t.xcell || !t.xphi) return SGN_ENOMEM;
+        SGN_CK(cudaMemsetAsync(t.xphi, 0, (size_t)(l ? r : 1) * t.nxc * 4 * sizeof(Real), st_));
+      }
+      int rc = lv_[l]->set_kind(kd[l].data());
+      if (rc) return rc;
+      rc = lv_[l]->set_xslot(xs[l].data());
+      if (rc) return rc;
+    }
+    // mixed precision: every level by the one-pass kernel
+    fused_ = sizeof(Real) == 4;
+    for (int l = 0; l < L; l++) lv_[l]->set_schedule(fused_ ? SCHED_FUSED : SCHED_SERIAL);
     sc_ = lv_[0]->template alloc_dev<double>(8);
     if (!sc_) return SGN_ENOMEM;
     SGN_CK(cudaMemsetAsync(sc_, 0, 8 * sizeof(double), st_));
@@ -807,13 +893,39 @@ class Amr : public AmrBase {
     return SGN_OK;
   }
 
+  // padded atlas index of frame cell (I, J) of box b on level l
+  int pidx(int l, const Box& b, int I, int J) const {
+    return (int)((size_t)(b.py + J) * lv_[l]->dev().pitch + (b.px + I));
+  }
+
+  // Ghost cell (X, Y) of a level-l patch b (inside the domain, no level-l
+  // patch holds it): limited interpolation from its parent cell, which lies in
+  // b's parent box P; the stencil cells come from whichever level-(l-1) patch
+  // holds them (-1: none, or outside the domain).  False if the parent cell is
+  // not inside P (the box rules exclude this).
+  bool par_entry(int l, const Box& b, int X, int Y, int dst, GEnt& e, int4& nv) const {
+    const int r = r_, ic = X / r, jc = Y / r;
+    const Box& P = bx_[l - 1][b.parent];
+    if (ic < P.i0 || ic >= P.i0 + P.nx || jc < P.j0 || jc >= P.j0 + P.ny) return false;
+    e = GEnt{dst, pidx(l - 1, P, ic - P.i0 + G, jc - P.j0 + G), GE_PAR | ((X % r) << 8) | ((Y % r) << 16)};
+    auto nb = [&](int x, int y) -> int {
+      if (x < 0 || y < 0 || x >= NX_[l - 1] || y >= NY_[l - 1]) return -1;
+      const int o = own_[l - 1].find(x, y);
+      if (o < 0) return -1;
+      const Box& Q = bx_[l - 1][o];
+      return pidx(l - 1, Q, x - Q.i0 + G, y - Q.j0 + G);
+    };
+    nv = make_int4(nb(ic - 1, jc), nb(ic + 1, jc), nb(ic, jc - 1), nb(ic, jc + 1));
+    return true;
+  }
+
   int set_patch(int l, int k, const double* q) override {
     if (l < 0 || l >= L_ || k < 0 || k >= (int)bx_[l].size() || !q) return SGN_EINVAL;
     const Box& b = bx_[l][k];
     size_t n = (size_t)b.nx * b.ny * NV;
     SGN_CK(cudaMemcpyAsync(staging_, q, n * sizeof(double), cudaMemcpyHostToDevice, st_));
     dim3 gr((b.nx + 31) / 32, (b.ny + 7) / 8);
-    k_amr_pack<MODEL, Real><<<gr, dim3(32, 8), 0, st_>>>(lv_[l]->dev(), staging_, b.px, b.py, b.nx, b.ny,
+    k_amr_pack<MODEL, Real><<<gr, dim3(32, 8), 0, st_>>>(lv_[l]->dev(), staging_, b.px + G, b.py + G, b.nx, b.ny,
                                                           lv_[l]->cur());
     SGN_CK(cudaGetLastError());
     SGN_CK(cudaStreamSynchronize(st_));
@@ -826,8 +938,8 @@ class Amr : public AmrBase {
     const Box& b = bx_[l][k];
     size_t n = (size_t)b.nx * b.ny * NV;
     dim3 gr((b.nx + 31) / 32, (b.ny + 7) / 8);
-    k_amr_unpack<MODEL, Real><<<gr, dim3(32, 8), 0, st_>>>(lv_[l]->dev(), staging_, b.px, b.py, b.nx, b.ny,
-                                                            lv_[l]->cur());
+    k_amr_unpack<MODEL, Real><<<gr, dim3(32, 8), 0, st_>>>(lv_[l]->dev(), staging_, b.px + G, b.py + G, b.nx,
+                                                            b.ny, lv_[l]->cur());
     SGN_CK(cudaGetLastError());
     SGN_CK(cudaMemcpyAsync(q, staging_, n * sizeof(double), cudaMemcpyDeviceToHost, st_));
     SGN_CK(cudaStreamSynchronize(st_));
@@ -859,37 +971,34 @@ class Amr : public AmrBase {
       Solver<MODEL, Real>* P = lv_[l - 1];
       const int pnew = P->cur(), pold = 1 - pnew;   // the parent has stepped already
       if (t.nfill) {
-        k_amr_fill<MODEL, Real><<<grid1(t.nfill), 256, 0, s>>>(S->dev(), P->dev(), t.fill, t.nfill, c, pold, pnew,
-                                                                 (double)ksub / r_, r_);
+        k_amr_fill<MODEL, Real><<<grid1(t.nfill), 256, 0, s>>>(S->dev(), P->dev(), t.fill, t.fillnb, t.nfill, c, pold,
+                                                                 pnew, (double)ksub / r_, r_);
         nl++;
       }
       if (t.nbc) { k_amr_fill_bc<MODEL, Real><<<grid1(t.nbc), 256, 0, s>>>(S->dev(), t.bc, t.nbc, c); nl++; }
     }
-    S->launch_phase1(s, c);
-    nl += 6;
-    if (l > 0 && t.nfill) { k_amr_theta<Real><<<grid1(t.nfill), 256, 0, s>>>(S->dev(), t.fill, t.nfill); nl++; }
-    if (l + 1 < L_ && t.nreg) {
-      k_amr_reg_coarse<Real><<<grid1(t.nreg), 256, 0, s>>>(S->dev(), t.rface_c, t.rdir, t.rsgn, t.rval, t.nreg);
+    // this step's slice of the level's export buffer
+    Real* xp = t.nxc ? t.xphi + (size_t)ksub * t.nxc * 4 : nullptr;
+    if (fused_) {
+      S->launch_fused(s, c, xp);
+      nl++;
+    } else {
+      S->launch_phase1(s, c);
+      nl += 6;
+      if (l > 0 && t.nfill) { k_amr_theta<Real><<<grid1(t.nfill), 256, 0, s>>>(S->dev(), t.fill, t.nfill); nl++; }
+      if (t.nxc) { k_amr_export<Real><<<grid1(t.nxc), 256, 0, s>>>(S->dev(), t.xcell, t.nxc, xp); nl++; }
+      S->launch_phase2(s, c);
       nl++;
     }
-    if (l > 0 && tb_[l - 1].nreg) {
-      Tabs& u = tb_[l - 1];
-      k_amr_reg_fine<Real><<<grid1(u.nreg), 256, 0, s>>>(S->dev(), u.rface_f, u.rdir, u.rsgn, u.rval, u.nreg, r_);
-      nl++;
-    }
-    S->launch_phase2(s, c);
-    nl++;
     S->flip();
     if (l + 1 < L_) {
       for (int k = 0; k < r_; k++) run_level(s, l + 1, k, nl);
-      if (t.navg) {
-        k_amr_avg<MODEL, Real><<<grid1(t.navg), 256, 0, s>>>(S->dev(), lv_[l + 1]->dev(), t.acoarse, t.afine,
-                                                              t.navg, S->cur(), lv_[l + 1]->cur(), r_);
-        nl++;
-      }
-      if (t.ncell) {
-        k_amr_reflux<Real><<<grid1(t.ncell), 256, 0, s>>>(S->dev(), t.rcell, t.rfirst, t.rval, t.ncell, S->cur(),
-                                                          dx_[l] * dx_[l], sc_ + 4);
+      if (t.navg || t.ncell) {
+        const Tabs& u = tb_[l + 1];
+        k_amr_avg_reflux<MODEL, Real><<<grid1(t.navg + t.ncell), 256, 0, s>>>(
+            S->dev(), lv_[l + 1]->dev(), t.acoarse, t.afine, t.navg, t.rcell, t.rfirst, t.ncell, t.rcref, t.rdir,
+            t.rsgn, t.rfref, xp, u.xphi, (size_t)u.nxc * 4, S->cur(), lv_[l + 1]->cur(), r_, dx_[l] * dx_[l],
+            sc_ + 4);
         nl++;
       }
     }
@@ -991,25 +1100,36 @@ class Amr : public AmrBase {
     graphs_.clear();
   }
 
+  // Tunes each level within the hierarchy's mode: the one-pass kernel's row
+  // option per level, or the sequence kernels' shapes and schedules.
   int autotune(int reps, int* ch, double* ms) override {
     if (reps < 1 || reps > 10000) return SGN_EINVAL;
     SGN_CK(cudaStreamSynchronize(st_));
     for (int l = 0; l < L_; l++) {
-      int rc = lv_[l]->autotune(reps, ch ? ch + l * TU_N : nullptr, ms ? ms + l * TU_N * TU_OPTS : nullptr);
+      int rc = lv_[l]->autotune_mode(reps, ch ? ch + l * TU_N : nullptr, ms ? ms + l * TU_N * TU_OPTS : nullptr,
+                                     fused_ ? 2 : 1);
       if (rc) return rc;
     }
     drop_amr_graphs();
     return SGN_OK;
   }
 
+  // One tuning per level; the one-pass schedule (mixed precision) on every
+  // level or on none.
   int set_tuning(const int* ch) override {
-    for (int l = 0; l < L_; l++)
+    if (!ch) return SGN_EINVAL;
+    int nfused = 0;
+    for (int l = 0; l < L_; l++) {
       for (int k = 0; k < TU_N; k++)
-        if (ch[l * TU_N + k] < 0 || ch[l * TU_N + k] >= (k == TU_SCHED ? 2 : TU_OPTS)) return SGN_EINVAL;
+        if (ch[l * TU_N + k] < 0 || ch[l * TU_N + k] >= (k == TU_SCHED ? SCHED_N : TU_OPTS)) return SGN_EINVAL;
+      nfused += ch[l * TU_N + TU_SCHED] == SCHED_FUSED;
+    }
+    if (nfused != 0 && (nfused != L_ || sizeof(Real) != 4)) return SGN_EINVAL;
     for (int l = 0; l < L_; l++) {
       int rc = lv_[l]->set_tuning(ch + l * TU_N);
       if (rc) return rc;
     }
+    fused_ = nfused == L_;
     drop_amr_graphs();
     return SGN_OK;
   }
@@ -1027,7 +1147,7 @@ class Amr : public AmrBase {
       for (int k = 0; k < nb; k++) {
         const Box& b = bx_[l][k];
         int* e = &t[6 * (size_t)k];
-        e[0] = b.px; e[1] = b.py; e[2] = b.nx; e[3] = b.ny; e[4] = b.i0; e[5] = b.j0;
+        e[0] = b.px + G; e[1] = b.py + G; e[2] = b.nx; e[3] = b.ny; e[4] = b.i0; e[5] = b.j0;
         mx = std::max(mx, b.nx);
         my = std::max(my, b.ny);
       }
@@ -1075,15 +1195,10 @@ class Amr : public AmrBase {
       for (int j = 0; j < b.ny; j++)
         for (int i = 0; i < b.nx; i++) {
           const size_t o = (size_t)(b.j0 + j) * NX_[l] + (b.i0 + i);
-          flag[o] = atl[(size_t)pidx_of(l, b, i + 2, j + 2)];
+          flag[o] = atl[(size_t)pidx(l, b, i + G, j + G)];
           have[o] = 1;
         }
     return SGN_OK;
-  }
-
-  // padded atlas index of frame cell (I, J) of box b on level l
-  int pidx_of(int l, const Box& b, int I, int J) const {
-    return (int)((size_t)(b.py + J) * lv_[l]->dev().pitch + (b.px + I));
   }
 
   // Regridding (reading A11 of the refinement oracle): this hierarchy, just
@@ -1110,23 +1225,23 @@ class Amr : public AmrBase {
       oo.build(o->bx_[l], NX_[l], NY_[l]);
       std::vector<int> cd, cs;
       std::vector<GEnt> par;
+      std::vector<int4> pnb;
       for (const Box& b : bx_[l]) {
-        const Box& P = bx_[l - 1][b.parent];
         for (int j = 0; j < b.ny; j++)
           for (int i = 0; i < b.nx; i++) {
-            const int X = b.i0 + i, Y = b.j0 + j, dst = pidx_of(l, b, i + 2, j + 2);
+            const int X = b.i0 + i, Y = b.j0 + j, dst = pidx(l, b, i + G, j + G);
             const int k = oo.find(X, Y);
             if (k >= 0) {
               const Box& s = o->bx_[l][k];
               cd.push_back(dst);
-              cs.push_back(o->pidx_of(l, s, X - s.i0 + 2, Y - s.j0 + 2));
+              cs.push_back(o->pidx(l, s, X - s.i0 + G, Y - s.j0 + G));
               continue;
             }
-            const int ic = X / r, jc = Y / r;
-            const int nb = (ic - 1 >= 0 ? 1 : 0) | (ic + 1 < NX_[l - 1] ? 2 : 0) | (jc - 1 >= 0 ? 4 : 0) |
-                           (jc + 1 < NY_[l - 1] ? 8 : 0);
-            par.push_back(GEnt{dst, pidx_of(l - 1, P, ic - P.i0 + 2, jc - P.j0 + 2),
-                               GE_PAR | ((X % r) << 8) | ((Y % r) << 16) | (nb << 24)});
+            GEnt e;
+            int4 nv;
+            if (!par_entry(l, b, X, Y, dst, e, nv)) return SGN_EINVAL;
+            par.push_back(e);
+            pnb.push_back(nv);
           }
       }
       if (!cd.empty()) {
@@ -1138,9 +1253,10 @@ class Amr : public AmrBase {
       }
       if (!par.empty()) {
         GEnt* dp = up(par);
-        if (!dp) return SGN_ENOMEM;
+        int4* dn = up(pnb);
+        if (!dp || !dn) return SGN_ENOMEM;
         const int pc = lv_[l - 1]->cur();
-        k_amr_fill<MODEL, Real><<<grid1((int)par.size()), 256, 0, st_>>>(lv_[l]->dev(), lv_[l - 1]->dev(), dp,
+        k_amr_fill<MODEL, Real><<<grid1((int)par.size()), 256, 0, st_>>>(lv_[l]->dev(), lv_[l - 1]->dev(), dp, dn,
                                                                           (int)par.size(), lv_[l]->cur(), pc, pc,
                                                                           0.0, r);
       }
@@ -1148,9 +1264,9 @@ class Amr : public AmrBase {
     }
     for (int l = L_ - 2; l >= 0; l--)
       if (tb_[l].navg)
-        k_amr_avg<MODEL, Real><<<grid1(tb_[l].navg), 256, 0, st_>>>(lv_[l]->dev(), lv_[l + 1]->dev(), tb_[l].acoarse,
-                                                                     tb_[l].afine, tb_[l].navg, lv_[l]->cur(),
-                                                                     lv_[l + 1]->cur(), r);
+        k_amr_avg_reflux<MODEL, Real><<<grid1(tb_[l].navg), 256, 0, st_>>>(
+            lv_[l]->dev(), lv_[l + 1]->dev(), tb_[l].acoarse, tb_[l].afine, tb_[l].navg, nullptr, nullptr, 0, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, 0, lv_[l]->cur(), lv_[l + 1]->cur(), r, 0.0, nullptr);
     SGN_CK(cudaGetLastError());
     int rc = begin();
     if (rc) return rc;

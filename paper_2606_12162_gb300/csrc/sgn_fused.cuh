@@ -71,6 +71,7 @@ template <int MODEL, typename Real> struct Rec {
   Real b, c2, hr, sqh, C, psx;
   double g2, e64;   // FP64 g h / 2 and eta
   bool wet;
+  unsigned char kind;   // refined levels: the cell's kind bits (else unused)
 };
 
 // Primitives of a record from its W, b and c^2 (the mixed path's load_side
@@ -270,6 +271,7 @@ template <int MODEL, typename Real> struct FusedSmem {
   double g2[FUSED_NT];
   double e64[FUSED_NT];
   unsigned char wet[FUSED_NT];
+  unsigned char kind[FUSED_NT];           // kind bits of the record (refined levels)
   Real xw[WR_N][FUSED_NT];                // x-face wave records of the row being limited
   Real lx[NV][FUSED_NT];                  // A^- + Ftil of each x face (for the transverse sums)
   Real uy[NV][FUSED_NT];                  // sum of the y fluctuations entering each cell
@@ -306,9 +308,21 @@ inline FusedPlan fused_plan(int nx, int ny, int H) {
 
 // One tile: the strip `sx` by the output rows [r0, r0 + nr) (interior row
 // indices), marched by the block.
-template <int MODEL, typename Real>
+//
+// KD: the grid is the atlas of a refined level, with a kind plane (bit 0 patch
+// interior, bit 1 covered by a finer patch, bit 2 ghost cell copied from a
+// sibling patch next to a patch edge, bit 3 cell whose four face mass fluxes
+// are exported for the coarse/fine flux correction).  Then only interior
+// cells are updated, the Courant number is taken over faces of interior
+// cells, positivity factors are computed for interior cells and for bit-2
+// ghosts (whose frame is deep enough that the factor equals the sibling's own,
+// so that both sides of a sibling face move the same mass) and are 1 for
+// every other ghost, and the theta-weighted mass fluxes of the four faces of
+// every bit-3 cell go to xphi[4 * xslot[cell] + {left, right, bottom, top}]
+// (nothing is exported when xphi is null).
+template <int MODEL, typename Real, bool KD>
 __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, Real>& sm, int cur, int sx, int r0,
-                                           int nr, Real& courmax, Real& spmax) {
+                                           int nr, Real& courmax, Real& spmax, Real* __restrict__ xphi) {
   typedef MT<MODEL> M;
   constexpr int NV = M::NV;
   const int t = threadIdx.x;
@@ -368,6 +382,8 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
   rp.b = rp.c2 = rp.hr = rp.sqh = rp.C = rp.psx = Real(0);
   rp.g2 = rp.e64 = 0.0;
   rp.wet = false;
+  rp.kind = 0;
+  unsigned ka = 0, kb = 0;        // kind bits of cells (I, r - 2), (I, r - 3)
   fxE.un = fxE.ut = fxE.w = fxE.sg = fxE.pb = fxE.K = fxE.gh = fxE.C = Real(0);
 
   // outputs of this thread: strip columns, inside the grid
@@ -404,6 +420,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
 #pragma unroll
       for (int k = 0; k < NV; k++) rc.W[k] = q[k];
       rc.b = b; rc.c2 = c2;
+      if (KD) rc.kind = ok ? d.kind[at(d.pitch, I, r)] : (unsigned char)0;
       rc.g2 = d.half_g * h;
       rc.e64 = e64;
       rec_prims<MODEL, Real>(d, rc);
@@ -428,7 +445,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
         auto nb = [&](int f, bool below) -> Real { return below ? y2[f] : wr_get(y0, f); };
         face_out<MODEL, Real, 1>(d, y1, nb, d.lamr[1], fyL, fyR, fyM);
         fyE = roe_of(y1);
-        if (J <= NG + ny && I >= NG && I < NG + nx && y1.active)
+        if (J <= NG + ny && I >= NG && I < NG + nx && y1.active && (!KD || ((rp.kind | ka) & 1u)))
           courmax = fmax(courmax, fmax(fabs(y1.s1), fabs(y1.sN)) * d.lamr[1]);
       } else {
 #pragma unroll
@@ -452,6 +469,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
       sm.rec[2 * NV + 2][t] = rp.sqh;
       sm.rec[2 * NV + 3][t] = rp.C;
       sm.wet[t] = rp.wet ? 1 : 0;
+      if (KD) sm.kind[t] = rp.kind;
       sm.g2[t] = rp.g2;
       sm.e64[t] = rp.e64;
     }
@@ -493,7 +511,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
         auto nb = [&](int f, bool left) -> Real { return sm.xw[f][left ? t - 1 : t + 1]; };
         face_out<MODEL, Real, 0>(d, xv, nb, d.lamr[0], nL, nR, nM);
         nE = roe_of(xv);
-        if (I <= NG + nx && J >= NG && J < NG + ny && xv.active)
+        if (I <= NG + nx && J >= NG && J < NG + ny && xv.active && (!KD || ((rp.kind | sm.kind[t - 1]) & 1u)))
           courmax = fmax(courmax, fmax(fabs(xv.s1), fabs(xv.sN)) * d.lamr[0]);
       } else {
 #pragma unroll
@@ -561,7 +579,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
     {
       const int J = r - 2;
       const bool go = t >= 2 && t <= FUSED_NT - 3 && I >= NG && I < NG + nx && J >= NG && J < NG + ny &&
-                      J - 2 >= rs;
+                      J - 2 >= rs && (!KD || (ka & 5u));
       if (go) {
         const Real fl = mxn, fr = sm.gx[par][0][t + 1], fb = my2, ft = myn;
         bool done = false;
@@ -583,7 +601,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
     }
     {
       const int J = r - 3;
-      if (outcol && J >= b0 && J < b1) {
+      if (outcol && J >= b0 && J < b1 && (!KD || (kb & 1u))) {
         const int po = par ^ 1;
         const Real Ml = mx3, Mr = sm.gx[po][0][t + 1], Mb = my3, Mt = my2;
         const Real th = th3;
@@ -592,6 +610,13 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
         const Real tb = Mb > Real(0) ? th4 : (Mb < Real(0) ? th : Real(1));
         const Real tt = Mt > Real(0) ? th : (Mt < Real(0) ? thn : Real(1));
         const Real lx = d.lamr[0], ly = d.lamr[1];   // the FP64 factors rounded once (the same values)
+        if (KD && (kb & 8u) && xphi) {
+          Real* o = xphi + 4 * (size_t)d.xslot[at(d.pitch, I, J)];
+          o[0] = tl * Ml;
+          o[1] = tr * Mr;
+          o[2] = tb * Mb;
+          o[3] = tt * Mt;
+        }
         Real en = wb[0] - lx * (tr * Mr - tl * Ml) - ly * (tt * Mt - tb * Mb);
         Real q[NV];
         bool bad = !isfinite(en);
@@ -637,6 +662,7 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
     my3 = my2; my2 = myn;
     mx3 = mxn;
     th4 = th3; th3 = thn;
+    if (KD) { kb = ka; ka = rp.kind; }
     fxM = nM; fxE = nE;
 #pragma unroll
     for (int f = 0; f < WR_N; f++) y2[f] = wr_get(y1, f);
@@ -651,8 +677,9 @@ __device__ __forceinline__ void fused_tile(const Dev<Real>& d, FusedSmem<MODEL, 
 // flight work on neighbouring strips of the same rows (their halo columns meet
 // in L2) and wet and dry tiles, whose costs differ, balance over the SMs.  The
 // last block to finish clears the counters for the next launch.
-template <int MODEL, typename Real>
-__global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Real> d, int cur, FusedPlan p) {
+template <int MODEL, typename Real, bool KD>
+__global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB)
+    k_step_fused(Dev<Real> d, int cur, FusedPlan p, Real* __restrict__ xphi) {
   typedef FusedSmem<MODEL, Real> SM;
   extern __shared__ __align__(16) unsigned char smraw[];
   SM& sm = *reinterpret_cast<SM*>(smraw);
@@ -672,7 +699,7 @@ __global__ void __launch_bounds__(FUSED_NT, SGN_FUSED_MINB) k_step_fused(Dev<Rea
       u -= p.n2;
       r0 = p.R2 + u / p.nsx * p.H3; nr = p.H3;
     }
-    fused_tile<MODEL, Real>(d, sm, cur, tile % p.nsx, r0, nr, courmax, spmax);
+    fused_tile<MODEL, Real, KD>(d, sm, cur, tile % p.nsx, r0, nr, courmax, spmax, xphi);
   }
   warp_max_to(d.cmax, courmax);
   warp_max_to(d.smax, spmax);

@@ -268,9 +268,12 @@ class Solver : public SolverBase {
     SGN_CK(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
     if constexpr (kFusedBuilt) {
       const int smb = (int)sizeof(FusedSmem<MODEL, Real>);
-      SGN_CK(cudaFuncSetAttribute(k_step_fused<MODEL, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
-      int per_sm = 0, nsm = 0;
-      SGN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<MODEL, Real>, FUSED_NT, smb));
+      SGN_CK(cudaFuncSetAttribute(k_step_fused<MODEL, Real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+      SGN_CK(cudaFuncSetAttribute(k_step_fused<MODEL, Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+      int per_sm = 0, per_sm_kd = 0, nsm = 0;
+      SGN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<MODEL, Real, false>, FUSED_NT, smb));
+      SGN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_kd, k_step_fused<MODEL, Real, true>, FUSED_NT, smb));
+      if (per_sm_kd < per_sm) per_sm = per_sm_kd;
       SGN_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       fused_resident_ = (per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
       // the default schedule of the mixed path on a single grid, unless the grid
@@ -382,7 +385,7 @@ class Solver : public SolverBase {
   // The one-pass step (k_step_fused): strips of FUSED_OUT columns by chunks of
   // fused_rows() rows (the long chunks), one block each.
   static constexpr bool kFusedBuilt = sizeof(Real) == 4;
-  bool fused_ok() const { return kFusedBuilt && !d_.kind; }
+  bool fused_ok() const { return kFusedBuilt; }
   int fused_resident_ = 0;   // blocks of the one-pass kernel resident on the device
   // rows of the long chunks: the option's, halved (not below 32) while the grid
   // would give fewer tiles than there are resident blocks
@@ -391,11 +394,14 @@ class Solver : public SolverBase {
     while (H > 32 && fused_plan(d_.nx, d_.ny, H).ntiles < fused_resident_) H /= 2;
     return H;
   }
-  void launch_fused(cudaStream_t s, int c) {
+  // xphi: a refined level's export buffer for this step (see fused_tile).
+  void launch_fused(cudaStream_t s, int c, Real* xphi = nullptr) {
     if constexpr (kFusedBuilt) {
       const FusedPlan p = fused_plan(d_.nx, d_.ny, fused_rows());
       const int nb = p.ntiles < fused_resident_ ? p.ntiles : fused_resident_;
-      k_step_fused<MODEL, Real><<<nb, FUSED_NT, sizeof(FusedSmem<MODEL, Real>), s>>>(d_, c, p);
+      const size_t smb = sizeof(FusedSmem<MODEL, Real>);
+      if (d_.kind) k_step_fused<MODEL, Real, true><<<nb, FUSED_NT, smb, s>>>(d_, c, p, xphi);
+      else k_step_fused<MODEL, Real, false><<<nb, FUSED_NT, smb, s>>>(d_, c, p, xphi);
     }
   }
 
@@ -464,9 +470,30 @@ class Solver : public SolverBase {
     SGN_CK(cudaMemcpyAsync(kp, h.data(), d_.fs, cudaMemcpyHostToDevice, st_));
     SGN_CK(cudaStreamSynchronize(st_));
     d_.kind = kp;
-    if (tune_[TU_SCHED] == SCHED_FUSED) tune_[TU_SCHED] = SCHED_SERIAL;   // uniform grids only
     drop_graphs();
     return SGN_OK;
+  }
+  // export slots of a refined level (dense ny*nx host array, -1: none)
+  int set_xslot(const int* slot_dense) {
+    int* sp = dnew<int>(d_.fs);
+    if (!sp) return SGN_ENOMEM;
+    std::vector<int> h(d_.fs, -1);
+    for (int j = 0; j < d_.ny; j++)
+      for (int i = 0; i < d_.nx; i++) h[(size_t)(j + NG) * d_.pitch + (i + NG)] = slot_dense[(size_t)j * d_.nx + i];
+    SGN_CK(cudaMemcpyAsync(sp, h.data(), d_.fs * sizeof(int), cudaMemcpyHostToDevice, st_));
+    SGN_CK(cudaStreamSynchronize(st_));
+    d_.xslot = sp;
+    drop_graphs();
+    return SGN_OK;
+  }
+  int schedule() const { return tune_[TU_SCHED]; }
+  // the one-pass schedule with the row option the last autotune found best
+  // (refined levels), or a kernel-sequence schedule
+  void set_schedule(int sched) {
+    tune_[TU_SCHED] = sched;
+    if (sched == SCHED_FUSED) tune_[TU_UPDATE] = fused_best_u_;
+    set_geometry();
+    drop_graphs();
   }
 
   int launches_per_step() override {
@@ -716,7 +743,14 @@ class Solver : public SolverBase {
   // scratch planes or q[1 - cur].  The speed and Courant maxima and the status
   // word are saved first and put back at the end, so the next step is the one
   // that would have run without tuning (on the schedule kept).
-  int autotune(int reps, int* ch, double* ms) override {
+  int autotune(int reps, int* ch, double* ms) override { return autotune_mode(reps, ch, ms, 0); }
+
+  // mode 0: every kernel's shapes and every schedule (a uniform grid); mode 1
+  // (a refined level stepped by the kernel sequence): shapes and the two
+  // sequence schedules; mode 2 (a refined level stepped by the one-pass
+  // kernel): only the one-pass kernel's row options.
+  int fused_best_u_ = 0;
+  int autotune_mode(int reps, int* ch, double* ms, int mode) {
     if (reps < 1 || reps > 10000) return SGN_EINVAL;
     if (ms)
       for (int i = 0; i < TU_N * TU_OPTS; i++) ms[i] = -1.0;
@@ -741,7 +775,7 @@ class Solver : public SolverBase {
       *out = t / reps;
       return SGN_OK;
     };
-    for (int k = 0; k < TU_SCHED && rc == SGN_OK; k++) {
+    for (int k = 0; k < TU_SCHED && rc == SGN_OK && mode != 2; k++) {
       float best = 0.f;
       int bo = 0;
       for (int o = 0; o < TU_OPTS && rc == SGN_OK; o++) {
@@ -762,7 +796,8 @@ class Solver : public SolverBase {
       float best = 0.f;
       int bo = -1, bu = upd0;
       for (int o = 0; o < SCHED_N && rc == SGN_OK; o++) {
-        if (o == SCHED_FUSED && !fused_ok()) continue;
+        if (o == SCHED_FUSED && (!fused_ok() || mode == 1)) continue;
+        if (o != SCHED_FUSED && mode == 2) continue;
         const int nu = o == SCHED_FUSED ? TU_OPTS : 1;
         for (int u = 0; u < nu && rc == SGN_OK; u++) {
           tune_[TU_SCHED] = o;
@@ -782,7 +817,10 @@ class Solver : public SolverBase {
           cudaGraphExecDestroy(gx);
           if (rc) break;
           float& slot = ms_sched_[o];
-          if (u == 0 || t < slot) slot = t;
+          if (u == 0 || t < slot) {
+            slot = t;
+            if (o == SCHED_FUSED) fused_best_u_ = u;
+          }
           if (bo < 0 || t < best) { best = t; bo = o; bu = tune_[TU_UPDATE]; }
         }
         if (ms && rc == SGN_OK) ms[TU_SCHED * TU_OPTS + o] = ms_sched_[o];

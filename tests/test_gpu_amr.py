@@ -115,6 +115,78 @@ def test_mixed_hierarchy_against_fp64_oracle(M, A):
             assert err[0] <= 1e-5 and err[1] <= 1e-3 and err[2] <= 1e-3, (l, k, err)
 
 
+def seq_choice(L, sched=0):
+    """Kernel-sequence tuning of every level (default shapes)."""
+    ch = [0] * 8
+    ch[7] = sched
+    return [ch] * L
+
+
+@pytest.mark.parametrize("model,nx0,ny0,r,boxes,seed,steps", [
+    (2, 24, 20, 2, W.amr_boxes_small(), 11, 10),
+    (1, 16, 12, 4, BOXES_R4, 12, 6),
+    (0, 24, 20, 2, W.amr_boxes_small(), 13, 10),
+])
+def test_mixed_one_pass_hierarchy_equals_kernel_sequence(M, A, model, nx0, ny0, r, boxes, seed, steps):
+    """Mixed precision steps every level with ONE launch of the one-pass kernel
+    (the default): three-cell frames, the positivity factors of sibling ghosts
+    computed in the frame, the coarse/fine face fluxes exported by the kernel.
+    Against the same hierarchy stepped by the kernel sequence (sibling factors
+    copied, fluxes read from the face planes): every patch within 1e-5 of its
+    field's largest magnitude, the next step to 1e-6, mass up to the clipped
+    water to FP32 rounding in both (a positivity factor that differed between
+    the two sides of a sibling face would move mass), against the FP64 oracle
+    within the mixed tolerances, and fewer launches per level-0 step."""
+    L = len(boxes) + 1
+    b, qs = W.amr_small_case(model, nx0, ny0, r, L, seed=seed, wetdry=True, amp=0.2)
+
+    def run(choice):
+        g = M.Hierarchy(b, nx0, ny0, 0.2, r, boxes, model=model, precision=1, **CFG)
+        if choice is not None:
+            g.set_tuning(choice)
+        g.set_state(qs)
+        m0, _ = g.mass()
+        g.step(steps)
+        return g, m0
+
+    f, m0 = run(None)
+    q, _ = run(seq_choice(L))
+    for l in range(L):
+        for k in range(len(f.boxes[l])):
+            pf, pq = f.get_patch(l, k), q.get_patch(l, k)
+            scale = np.abs(pq).max(axis=(1, 2)) + 1e-30
+            assert (np.abs(pf - pq).max(axis=(1, 2)) <= 1e-5 * scale).all(), (l, k)
+    assert abs(f.next_dt() - q.next_dt()) <= 1e-6 * q.next_dt()
+    for g in (f, q):
+        m, c = g.mass()
+        assert abs(m - m0 - c) <= 2e-6 * m0, (m, m0, c)
+        assert g.status() == 0
+    assert f.launches_per_step() < q.launches_per_step()
+    o = A.AmrOracle(b, nx0, ny0, 0.2, r, boxes, model=model, bc=(0, 0, 0, 0), **CFG)
+    o.set_state(qs)
+    assert o.step(steps) == 0
+    for l in range(L):
+        for k in range(len(f.boxes[l])):
+            err = rel_l2(f.get_patch(l, k)[:3], o.patch_state(l, k)[:3])
+            assert err[0] <= 1e-5 and err[1] <= 1e-3 and err[2] <= 1e-3, (l, k, err)
+
+
+def test_hierarchy_modes_by_tuning(M):
+    """The one-pass kernel runs on every level or on none: a tuning that mixes
+    it with the kernel sequence is rejected, as is the one-pass kernel in
+    FP64; a whole-hierarchy switch is accepted both ways."""
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=14)
+    fused = [0] * 7 + [2]
+    g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, precision=1, **CFG)
+    with pytest.raises(Exception):
+        g.set_tuning([fused, [0] * 8, fused])
+    g.set_tuning(seq_choice(3))
+    g.set_tuning([fused] * 3)
+    d = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, precision=0, **CFG)
+    with pytest.raises(Exception):
+        d.set_tuning([fused] * 3)
+
+
 def test_lake_at_rest_and_mass(M, A):
     b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
     rest = []

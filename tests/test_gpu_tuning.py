@@ -177,7 +177,9 @@ def test_hierarchy_autotune_and_options(S):
         assert ch.shape == (L, S.TUNE_N)
         tuned.step(4)
         forced = hier(precision)
-        forced.set_tuning([[2] * (S.TUNE_N - 1) + [1]] * L)
+        # FP64: the forked kernel sequence with the third shape of every kernel;
+        # mixed: the one-pass kernel (its default on every level) with 256-row chunks
+        forced.set_tuning([[2] * (S.TUNE_N - 1) + [1 if precision == 0 else 2]] * L)
         forced.step(6)
         for g in (tuned, forced):
             got = patches(g)
