@@ -38,34 +38,52 @@ namespace sgn {
 constexpr int AMR_MAXL = 8;
 
 // ghost-table entry: dst/src padded indices; info: bits 0-1 type, BC: bit 2/3
-// flip hu/hv; PAR: bits 8-15 / 16-23 sub-cell offsets.  A PAR entry's stencil
-// (the parent-level cells W, E, S, N of its parent cell) is a separate int4 of
-// padded indices into the parent level's atlas, -1 where the level has no patch
-// there or the cell is outside the domain: each stencil cell is read from the
-// patch that holds it, so a ghost's value depends only on where it is, not on
-// which patch's frame holds it.
+// flip hu/hv.
 struct GEnt { int dst, src, info; };
 enum { GE_SIB = 0, GE_PAR = 1, GE_BC = 2 };
 
+// Ghost cells filled from the parent level, grouped by parent cell: group g
+// holds the padded index of the parent cell (src[g]), its stencil W, E, S, N
+// (nb[g]: padded indices into the parent level's atlas, -1 where the level
+// has no patch there or the cell is outside the domain -- each stencil cell is
+// read from the patch that holds it, so a ghost's value depends only on where
+// it is, not on which patch's frame holds it) and its ghost cells first[g] ..
+// first[g+1]-1: padded index dst and sub-cell offsets sub = sx | sy << 8.
+struct ParTab {
+  const int* src;
+  const int4* nb;
+  const int* first;
+  const int* dst;
+  const int* sub;
+  int n;
+};
+
+// Ghost fill of a level before its step (one launch).  Threads [0, par.n):
+// one parent cell each -- its surface and primitives at the substep's time
+// weight a and the minmod slopes of its stencil, once -- then the limited
+// interpolation of each of its ghost cells (depth from the surface, conserved
+// values no larger than the parent cell's own).  Threads [par.n, par.n + ns):
+// copies from sibling patches (sib, type GE_SIB).
 template <int MODEL, typename Real>
-__global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t, const int4* __restrict__ nbt, int n,
-                           int cc, int pold, int pnew, double a, int r) {
+__global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, ParTab par, const GEnt* __restrict__ sib, int ns, int cc,
+                           int pold, int pnew, double a, int r) {
   constexpr int NV = MT<MODEL>::NV;
   // the interpolation runs in the bulk type (the depth of a parent cell, which
   // decides dry or wet, in FP64): a ghost value is an input of the step, not
   // one of its balanced or positivity-critical terms
   typedef Real A;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const GEnt g = t[e];
   Real* qc = c.q[cc];
-  if ((g.info & 3) == GE_SIB) {
+  if (e >= par.n) {
+    e -= par.n;
+    if (e >= ns) return;
+    const GEnt g = sib[e];
 #pragma unroll
     for (int k = 0; k < NV; k++) qc[k * c.fs + g.dst] = qc[k * c.fs + g.src];
     return;
   }
-  const int sx = (g.info >> 8) & 255, sy = (g.info >> 16) & 255;
-  const int4 nv = nbt[e];
+  const int4 nv = par.nb[e];
+  const int c0 = par.first[e], c1 = par.first[e + 1];
   const Real* qo = p.q[pold];
   const Real* qn = p.q[pnew];
   const A a1 = A(a), a0 = A(1.0 - a);
@@ -82,36 +100,46 @@ __global__ void k_amr_fill(Dev<Real> c, Dev<Real> p, const GEnt* __restrict__ t,
     for (int k = 1; k < NV; k++) o[k] = v[k] * ih;
     return true;
   };
-  const double bf = (double)c.b[g.dst];
-  A pc[NV], pw[NV], pe[NV], ps[NV], pn[NV], out[NV];
-  const size_t ic = (size_t)g.src;
+  A pc[NV], pw[NV], pe[NV], ps[NV], pn[NV], slx[NV], sly[NV], cv[NV];
+  const size_t ic = (size_t)par.src[e];
   if (!prim(ic, pc)) {
-    qc[g.dst] = (Real)(bf > 0.0 ? bf : 0.0);
+    for (int ch = c0; ch < c1; ch++) {
+      const size_t d = (size_t)par.dst[ch];
+      const double bf = (double)c.b[d];
+      qc[d] = (Real)(bf > 0.0 ? bf : 0.0);
 #pragma unroll
-    for (int k = 1; k < NV; k++) qc[k * c.fs + g.dst] = Real(0);
+      for (int k = 1; k < NV; k++) qc[k * c.fs + d] = Real(0);
+    }
     return;
   }
   const bool hx = nv.x >= 0 && nv.y >= 0 && prim((size_t)nv.x, pw) && prim((size_t)nv.y, pe);
   const bool hy = nv.z >= 0 && nv.w >= 0 && prim((size_t)nv.z, ps) && prim((size_t)nv.w, pn);
-  const A xi = A((sx + 0.5) / r - 0.5), yi = A((sy + 0.5) / r - 0.5);
   auto mm = [](A u, A v) -> A { return u * v <= A(0) ? A(0) : (fabs(u) < fabs(v) ? u : v); };
 #pragma unroll
   for (int k = 0; k < NV; k++) {
-    A slx = hx ? mm(pc[k] - pw[k], pe[k] - pc[k]) : A(0);
-    A sly = hy ? mm(pc[k] - ps[k], pn[k] - pc[k]) : A(0);
-    out[k] = pc[k] + xi * slx + yi * sly;
+    slx[k] = hx ? mm(pc[k] - pw[k], pe[k] - pc[k]) : A(0);
+    sly[k] = hy ? mm(pc[k] - ps[k], pn[k] - pc[k]) : A(0);
+    cv[k] = a0 * (A)qo[k * p.fs + ic] + a1 * (A)qn[k * p.fs + ic];   // conserved values of the parent cell
   }
-  double eta = (double)out[0];
-  if (eta < bf) eta = bf;
-  const double hf = eta - bf;
-  qc[g.dst] = (Real)eta;
+  for (int ch = c0; ch < c1; ch++) {
+    const size_t d = (size_t)par.dst[ch];
+    const int sx = par.sub[ch] & 255, sy = par.sub[ch] >> 8;
+    const A xi = A((sx + 0.5) / r - 0.5), yi = A((sy + 0.5) / r - 0.5);
+    const double bf = (double)c.b[d];
+    A out[NV];
 #pragma unroll
-  for (int k = 1; k < NV; k++) {
-    // depth x primitive, no larger than the parent cell's own conserved value
-    // (a mostly dry parent has a small mean depth and an unreliable velocity)
-    const A v = hf > c.dry_tol ? A(hf) * out[k] : A(0);
-    const A cv = a0 * (A)qo[k * p.fs + ic] + a1 * (A)qn[k * p.fs + ic];
-    qc[k * c.fs + g.dst] = (Real)(v * cv > A(0) ? (fabs(v) <= fabs(cv) ? v : cv) : A(0));
+    for (int k = 0; k < NV; k++) out[k] = pc[k] + xi * slx[k] + yi * sly[k];
+    double eta = (double)out[0];
+    if (eta < bf) eta = bf;
+    const double hf = eta - bf;
+    qc[d] = (Real)eta;
+#pragma unroll
+    for (int k = 1; k < NV; k++) {
+      // depth x primitive, no larger than the parent cell's own conserved value
+      // (a mostly dry parent has a small mean depth and an unreliable velocity)
+      const A v = hf > c.dry_tol ? A(hf) * out[k] : A(0);
+      qc[k * c.fs + d] = (Real)(v * cv[k] > A(0) ? (fabs(v) <= fabs(cv[k]) ? v : cv[k]) : A(0));
+    }
   }
 }
 
@@ -491,7 +519,8 @@ class Amr : public AmrBase {
   std::vector<int> NX_, NY_;
   std::vector<double> dx_;
   struct Tabs {
-    GEnt* fill = nullptr; int4* fillnb = nullptr; int nfill = 0;   // SIB + PAR (and the PAR stencils)
+    GEnt* fill = nullptr; int nfill = 0;      // copies from sibling patches (GE_SIB)
+    ParTab par{};                             // ghosts from the parent level, by parent cell
     GEnt* bc = nullptr; int nbc = 0;
     int* xcell = nullptr; int nxc = 0;        // exported cells of this level, by slot
     Real* xphi = nullptr;                     // their face fluxes: (l ? r : 1) substeps x nxc x 4
@@ -741,7 +770,7 @@ class Amr : public AmrBase {
     tb_.assign(L, Tabs{});
     for (int l = 1; l < L; l++) {
       std::vector<GEnt> fill, bcs;
-      std::vector<int4> fnb;
+      std::vector<ParEnt> pe;
       for (int k = 0; k < (int)bx_[l].size(); k++) {
         const Box& b = bx_[l][k];
         for (int J = 0; J < b.ny + 2 * G; J++)
@@ -762,23 +791,21 @@ class Amr : public AmrBase {
             if (o >= 0) {
               const Box& s = bx_[l][o];
               fill.push_back(GEnt{dst, pidx(l, s, X - s.i0 + G, Y - s.j0 + G), GE_SIB});
-              fnb.push_back(make_int4(-1, -1, -1, -1));
               // a sibling ghost sharing a face with an interior cell
               const bool side = ((I == G - 1 || I == G + b.nx) && J >= G && J < G + b.ny) ||
                                 ((J == G - 1 || J == G + b.ny) && I >= G && I < G + b.nx);
               if (side) kd[l][dense(l, b, I, J)] |= 4;
               continue;
             }
-            GEnt e;
-            int4 nv;
-            if (!par_entry(l, b, X, Y, dst, e, nv)) return SGN_EINVAL;
-            fill.push_back(e);
-            fnb.push_back(nv);
+            ParEnt q;
+            if (!par_entry(l, b, X, Y, dst, q)) return SGN_EINVAL;
+            pe.push_back(q);
           }
       }
-      tb_[l].fill = up(fill); tb_[l].fillnb = up(fnb); tb_[l].nfill = (int)fill.size();
+      tb_[l].fill = up(fill); tb_[l].nfill = (int)fill.size();
       tb_[l].bc = up(bcs); tb_[l].nbc = (int)bcs.size();
-      if ((tb_[l].nfill && (!tb_[l].fill || !tb_[l].fillnb)) || (tb_[l].nbc && !tb_[l].bc)) return SGN_ENOMEM;
+      if ((tb_[l].nfill && !tb_[l].fill) || (tb_[l].nbc && !tb_[l].bc)) return SGN_ENOMEM;
+      if (!upload_par(pe, tb_[l].par)) return SGN_ENOMEM;
     }
     // registers and average-down maps of level l (coarse side).  A register
     // is a coarse face between an uncovered cell u and a covered one: its
@@ -898,16 +925,22 @@ class Amr : public AmrBase {
     return (int)((size_t)(b.py + J) * lv_[l]->dev().pitch + (b.px + I));
   }
 
+  // a cell filled from the parent level: parent cell (padded), its stencil,
+  // the cell (padded) and its sub-cell offsets sx | sy << 8
+  struct ParEnt { int src; int4 nb; int dst, sub; };
+
   // Ghost cell (X, Y) of a level-l patch b (inside the domain, no level-l
   // patch holds it): limited interpolation from its parent cell, which lies in
   // b's parent box P; the stencil cells come from whichever level-(l-1) patch
   // holds them (-1: none, or outside the domain).  False if the parent cell is
   // not inside P (the box rules exclude this).
-  bool par_entry(int l, const Box& b, int X, int Y, int dst, GEnt& e, int4& nv) const {
+  bool par_entry(int l, const Box& b, int X, int Y, int dst, ParEnt& e) const {
     const int r = r_, ic = X / r, jc = Y / r;
     const Box& P = bx_[l - 1][b.parent];
     if (ic < P.i0 || ic >= P.i0 + P.nx || jc < P.j0 || jc >= P.j0 + P.ny) return false;
-    e = GEnt{dst, pidx(l - 1, P, ic - P.i0 + G, jc - P.j0 + G), GE_PAR | ((X % r) << 8) | ((Y % r) << 16)};
+    e.src = pidx(l - 1, P, ic - P.i0 + G, jc - P.j0 + G);
+    e.dst = dst;
+    e.sub = (X % r) | ((Y % r) << 8);
     auto nb = [&](int x, int y) -> int {
       if (x < 0 || y < 0 || x >= NX_[l - 1] || y >= NY_[l - 1]) return -1;
       const int o = own_[l - 1].find(x, y);
@@ -915,8 +948,34 @@ class Amr : public AmrBase {
       const Box& Q = bx_[l - 1][o];
       return pidx(l - 1, Q, x - Q.i0 + G, y - Q.j0 + G);
     };
-    nv = make_int4(nb(ic - 1, jc), nb(ic + 1, jc), nb(ic, jc - 1), nb(ic, jc + 1));
+    e.nb = make_int4(nb(ic - 1, jc), nb(ic + 1, jc), nb(ic, jc - 1), nb(ic, jc + 1));
     return true;
+  }
+
+  // groups of parent-filled cells by parent cell (parent order, cells in
+  // creation order), uploaded; false: out of device memory
+  bool upload_par(const std::vector<ParEnt>& v, ParTab& t) {
+    t = ParTab{};
+    if (v.empty()) return true;
+    std::vector<int> ord(v.size());
+    for (size_t i = 0; i < ord.size(); i++) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return v[a].src < v[b].src; });
+    std::vector<int> src, first, dst, sub;
+    std::vector<int4> nb;
+    for (size_t i = 0; i < ord.size(); i++) {
+      const ParEnt& e = v[ord[i]];
+      if (i == 0 || e.src != v[ord[i - 1]].src) {
+        src.push_back(e.src);
+        nb.push_back(e.nb);
+        first.push_back((int)dst.size());
+      }
+      dst.push_back(e.dst);
+      sub.push_back(e.sub);
+    }
+    first.push_back((int)dst.size());
+    t.src = up(src); t.nb = up(nb); t.first = up(first); t.dst = up(dst); t.sub = up(sub);
+    t.n = (int)src.size();
+    return t.src && t.nb && t.first && t.dst && t.sub;
   }
 
   int set_patch(int l, int k, const double* q) override {
@@ -970,9 +1029,9 @@ class Amr : public AmrBase {
     if (l > 0) {
       Solver<MODEL, Real>* P = lv_[l - 1];
       const int pnew = P->cur(), pold = 1 - pnew;   // the parent has stepped already
-      if (t.nfill) {
-        k_amr_fill<MODEL, Real><<<grid1(t.nfill), 256, 0, s>>>(S->dev(), P->dev(), t.fill, t.fillnb, t.nfill, c, pold,
-                                                                 pnew, (double)ksub / r_, r_);
+      if (t.nfill || t.par.n) {
+        k_amr_fill<MODEL, Real><<<grid1(t.par.n + t.nfill), 256, 0, s>>>(S->dev(), P->dev(), t.par, t.fill, t.nfill,
+                                                                           c, pold, pnew, (double)ksub / r_, r_);
         nl++;
       }
       if (t.nbc) { k_amr_fill_bc<MODEL, Real><<<grid1(t.nbc), 256, 0, s>>>(S->dev(), t.bc, t.nbc, c); nl++; }
@@ -1224,8 +1283,7 @@ class Amr : public AmrBase {
       Owner oo;
       oo.build(o->bx_[l], NX_[l], NY_[l]);
       std::vector<int> cd, cs;
-      std::vector<GEnt> par;
-      std::vector<int4> pnb;
+      std::vector<ParEnt> par;
       for (const Box& b : bx_[l]) {
         for (int j = 0; j < b.ny; j++)
           for (int i = 0; i < b.nx; i++) {
@@ -1237,11 +1295,9 @@ class Amr : public AmrBase {
               cs.push_back(o->pidx(l, s, X - s.i0 + G, Y - s.j0 + G));
               continue;
             }
-            GEnt e;
-            int4 nv;
-            if (!par_entry(l, b, X, Y, dst, e, nv)) return SGN_EINVAL;
+            ParEnt e;
+            if (!par_entry(l, b, X, Y, dst, e)) return SGN_EINVAL;
             par.push_back(e);
-            pnb.push_back(nv);
           }
       }
       if (!cd.empty()) {
@@ -1252,13 +1308,11 @@ class Amr : public AmrBase {
             lv_[l]->dev(), o->lv_[l]->dev(), dd, ds, (int)cd.size(), lv_[l]->cur(), o->lv_[l]->cur());
       }
       if (!par.empty()) {
-        GEnt* dp = up(par);
-        int4* dn = up(pnb);
-        if (!dp || !dn) return SGN_ENOMEM;
+        ParTab pt;
+        if (!upload_par(par, pt)) return SGN_ENOMEM;
         const int pc = lv_[l - 1]->cur();
-        k_amr_fill<MODEL, Real><<<grid1((int)par.size()), 256, 0, st_>>>(lv_[l]->dev(), lv_[l - 1]->dev(), dp, dn,
-                                                                          (int)par.size(), lv_[l]->cur(), pc, pc,
-                                                                          0.0, r);
+        k_amr_fill<MODEL, Real><<<grid1(pt.n), 256, 0, st_>>>(lv_[l]->dev(), lv_[l - 1]->dev(), pt, nullptr, 0,
+                                                               lv_[l]->cur(), pc, pc, 0.0, r);
       }
       SGN_CK(cudaGetLastError());
     }
