@@ -510,7 +510,6 @@ class Amr : public AmrBase {
   // a patch edge itself (their faces' fluxes reach two cells further out); two
   // where the kernel sequence copies them from the sibling
   static constexpr int G = sizeof(Real) == 4 ? 3 : 2;
-  bool fused_ = false;   // every level stepped by the one-pass kernel
   int L_ = 1, r_ = 2;
   sgn_grid g0_{};
   sgn_params prm_{};
@@ -889,9 +888,10 @@ class Amr : public AmrBase {
       rc = lv_[l]->set_xslot(xs[l].data());
       if (rc) return rc;
     }
-    // mixed precision: every level by the one-pass kernel
-    fused_ = sizeof(Real) == 4;
-    for (int l = 0; l < L; l++) lv_[l]->set_schedule(fused_ ? SCHED_FUSED : SCHED_SERIAL);
+    // each level keeps its solver's default schedule: the one-pass kernel in
+    // mixed precision where the atlas gives the resident blocks enough tiles,
+    // else the kernel sequence (both export the same fluxes and give sibling
+    // ghosts the same positivity factors, so the levels may differ)
     sc_ = lv_[0]->template alloc_dev<double>(8);
     if (!sc_) return SGN_ENOMEM;
     SGN_CK(cudaMemsetAsync(sc_, 0, 8 * sizeof(double), st_));
@@ -953,7 +953,10 @@ class Amr : public AmrBase {
   }
 
   // groups of parent-filled cells by parent cell (parent order, cells in
-  // creation order), uploaded; false: out of device memory
+  // creation order), at most kParChunk cells a group -- a parent cell with
+  // more starts another group, so that small fills keep enough threads --
+  // uploaded; false: out of device memory
+  static constexpr int kParChunk = 4;
   bool upload_par(const std::vector<ParEnt>& v, ParTab& t) {
     t = ParTab{};
     if (v.empty()) return true;
@@ -964,7 +967,7 @@ class Amr : public AmrBase {
     std::vector<int4> nb;
     for (size_t i = 0; i < ord.size(); i++) {
       const ParEnt& e = v[ord[i]];
-      if (i == 0 || e.src != v[ord[i - 1]].src) {
+      if (i == 0 || e.src != v[ord[i - 1]].src || (int)dst.size() - first.back() >= kParChunk) {
         src.push_back(e.src);
         nb.push_back(e.nb);
         first.push_back((int)dst.size());
@@ -1038,7 +1041,7 @@ class Amr : public AmrBase {
     }
     // this step's slice of the level's export buffer
     Real* xp = t.nxc ? t.xphi + (size_t)ksub * t.nxc * 4 : nullptr;
-    if (fused_) {
+    if (S->schedule() == SCHED_FUSED) {
       S->launch_fused(s, c, xp);
       nl++;
     } else {
@@ -1159,36 +1162,31 @@ class Amr : public AmrBase {
     graphs_.clear();
   }
 
-  // Tunes each level within the hierarchy's mode: the one-pass kernel's row
-  // option per level, or the sequence kernels' shapes and schedules.
+  // Tunes each level (launch shapes and schedule, the one-pass kernel among
+  // them in mixed precision) on its own atlas.
   int autotune(int reps, int* ch, double* ms) override {
     if (reps < 1 || reps > 10000) return SGN_EINVAL;
     SGN_CK(cudaStreamSynchronize(st_));
     for (int l = 0; l < L_; l++) {
-      int rc = lv_[l]->autotune_mode(reps, ch ? ch + l * TU_N : nullptr, ms ? ms + l * TU_N * TU_OPTS : nullptr,
-                                     fused_ ? 2 : 1);
+      int rc = lv_[l]->autotune(reps, ch ? ch + l * TU_N : nullptr, ms ? ms + l * TU_N * TU_OPTS : nullptr);
       if (rc) return rc;
     }
     drop_amr_graphs();
     return SGN_OK;
   }
 
-  // One tuning per level; the one-pass schedule (mixed precision) on every
-  // level or on none.
+  // One tuning per level (the one-pass schedule only in mixed precision).
   int set_tuning(const int* ch) override {
     if (!ch) return SGN_EINVAL;
-    int nfused = 0;
-    for (int l = 0; l < L_; l++) {
+    for (int l = 0; l < L_; l++)
       for (int k = 0; k < TU_N; k++)
         if (ch[l * TU_N + k] < 0 || ch[l * TU_N + k] >= (k == TU_SCHED ? SCHED_N : TU_OPTS)) return SGN_EINVAL;
-      nfused += ch[l * TU_N + TU_SCHED] == SCHED_FUSED;
-    }
-    if (nfused != 0 && (nfused != L_ || sizeof(Real) != 4)) return SGN_EINVAL;
+    for (int l = 0; l < L_; l++)
+      if (ch[l * TU_N + TU_SCHED] == SCHED_FUSED && sizeof(Real) != 4) return SGN_EINVAL;
     for (int l = 0; l < L_; l++) {
       int rc = lv_[l]->set_tuning(ch + l * TU_N);
       if (rc) return rc;
     }
-    fused_ = nfused == L_;
     drop_amr_graphs();
     return SGN_OK;
   }

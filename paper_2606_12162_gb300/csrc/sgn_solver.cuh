@@ -487,14 +487,6 @@ class Solver : public SolverBase {
     return SGN_OK;
   }
   int schedule() const { return tune_[TU_SCHED]; }
-  // the one-pass schedule with the row option the last autotune found best
-  // (refined levels), or a kernel-sequence schedule
-  void set_schedule(int sched) {
-    tune_[TU_SCHED] = sched;
-    if (sched == SCHED_FUSED) tune_[TU_UPDATE] = fused_best_u_;
-    set_geometry();
-    drop_graphs();
-  }
 
   int launches_per_step() override {
     const int n = tune_[TU_SCHED] == SCHED_FUSED ? 2 : 8;
@@ -743,14 +735,7 @@ class Solver : public SolverBase {
   // scratch planes or q[1 - cur].  The speed and Courant maxima and the status
   // word are saved first and put back at the end, so the next step is the one
   // that would have run without tuning (on the schedule kept).
-  int autotune(int reps, int* ch, double* ms) override { return autotune_mode(reps, ch, ms, 0); }
-
-  // mode 0: every kernel's shapes and every schedule (a uniform grid); mode 1
-  // (a refined level stepped by the kernel sequence): shapes and the two
-  // sequence schedules; mode 2 (a refined level stepped by the one-pass
-  // kernel): only the one-pass kernel's row options.
-  int fused_best_u_ = 0;
-  int autotune_mode(int reps, int* ch, double* ms, int mode) {
+  int autotune(int reps, int* ch, double* ms) override {
     if (reps < 1 || reps > 10000) return SGN_EINVAL;
     if (ms)
       for (int i = 0; i < TU_N * TU_OPTS; i++) ms[i] = -1.0;
@@ -775,7 +760,7 @@ class Solver : public SolverBase {
       *out = t / reps;
       return SGN_OK;
     };
-    for (int k = 0; k < TU_SCHED && rc == SGN_OK && mode != 2; k++) {
+    for (int k = 0; k < TU_SCHED && rc == SGN_OK; k++) {
       float best = 0.f;
       int bo = 0;
       for (int o = 0; o < TU_OPTS && rc == SGN_OK; o++) {
@@ -796,8 +781,7 @@ class Solver : public SolverBase {
       float best = 0.f;
       int bo = -1, bu = upd0;
       for (int o = 0; o < SCHED_N && rc == SGN_OK; o++) {
-        if (o == SCHED_FUSED && (!fused_ok() || mode == 1)) continue;
-        if (o != SCHED_FUSED && mode == 2) continue;
+        if (o == SCHED_FUSED && !fused_ok()) continue;
         const int nu = o == SCHED_FUSED ? TU_OPTS : 1;
         for (int u = 0; u < nu && rc == SGN_OK; u++) {
           tune_[TU_SCHED] = o;
@@ -817,10 +801,7 @@ class Solver : public SolverBase {
           cudaGraphExecDestroy(gx);
           if (rc) break;
           float& slot = ms_sched_[o];
-          if (u == 0 || t < slot) {
-            slot = t;
-            if (o == SCHED_FUSED) fused_best_u_ = u;
-          }
+          if (u == 0 || t < slot) slot = t;
           if (bo < 0 || t < best) { best = t; bo = o; bu = tune_[TU_UPDATE]; }
         }
         if (ms && rc == SGN_OK) ms[TU_SCHED * TU_OPTS + o] = ms_sched_[o];

@@ -116,7 +116,8 @@ def test_mixed_hierarchy_against_fp64_oracle(M, A):
 
 
 def seq_choice(L, sched=0):
-    """Kernel-sequence tuning of every level (default shapes)."""
+    """The same schedule on every level (default shapes): 0 the kernel
+    sequence, 2 the one-pass kernel."""
     ch = [0] * 8
     ch[7] = sched
     return [ch] * L
@@ -128,9 +129,10 @@ def seq_choice(L, sched=0):
     (0, 24, 20, 2, W.amr_boxes_small(), 13, 10),
 ])
 def test_mixed_one_pass_hierarchy_equals_kernel_sequence(M, A, model, nx0, ny0, r, boxes, seed, steps):
-    """Mixed precision steps every level with ONE launch of the one-pass kernel
-    (the default): three-cell frames, the positivity factors of sibling ghosts
-    computed in the frame, the coarse/fine face fluxes exported by the kernel.
+    """Mixed precision steps a level with ONE launch of the one-pass kernel
+    (the default where the level's atlas is large enough; forced on every level
+    here): three-cell frames, the positivity factors of sibling ghosts computed
+    in the frame, the coarse/fine face fluxes exported by the kernel.
     Against the same hierarchy stepped by the kernel sequence (sibling factors
     copied, fluxes read from the face planes): every patch within 1e-5 of its
     field's largest magnitude, the next step to 1e-6, mass up to the clipped
@@ -149,7 +151,7 @@ def test_mixed_one_pass_hierarchy_equals_kernel_sequence(M, A, model, nx0, ny0, 
         g.step(steps)
         return g, m0
 
-    f, m0 = run(None)
+    f, m0 = run(seq_choice(L, 2))
     q, _ = run(seq_choice(L))
     for l in range(L):
         for k in range(len(f.boxes[l])):
@@ -171,20 +173,30 @@ def test_mixed_one_pass_hierarchy_equals_kernel_sequence(M, A, model, nx0, ny0, 
             assert err[0] <= 1e-5 and err[1] <= 1e-3 and err[2] <= 1e-3, (l, k, err)
 
 
-def test_hierarchy_modes_by_tuning(M):
-    """The one-pass kernel runs on every level or on none: a tuning that mixes
-    it with the kernel sequence is rejected, as is the one-pass kernel in
-    FP64; a whole-hierarchy switch is accepted both ways."""
+def test_hierarchy_levels_mix_schedules(M):
+    """Each level runs its own schedule: the one-pass kernel on some levels and
+    the kernel sequence on others (both export the same coarse/fine fluxes and
+    give sibling ghosts the same positivity factors) agrees with either alone
+    to FP32 rounding; FP64 rejects the one-pass kernel on any level."""
     b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=14)
     fused = [0] * 7 + [2]
-    g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, precision=1, **CFG)
-    with pytest.raises(Exception):
-        g.set_tuning([fused, [0] * 8, fused])
-    g.set_tuning(seq_choice(3))
-    g.set_tuning([fused] * 3)
+
+    def run(choice):
+        g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, precision=1, **CFG)
+        g.set_tuning(choice)
+        g.set_state(qs)
+        g.step(8)
+        return [g.get_patch(l, k) for l in range(3) for k in range(len(g.boxes[l]))]
+
+    ref = run(seq_choice(3))
+    for choice in ([fused, [0] * 8, fused], [[0] * 8, fused, [0] * 8]):
+        got = run(choice)
+        for x, y in zip(got, ref):
+            scale = np.abs(y).max(axis=(1, 2)) + 1e-30
+            assert (np.abs(x - y).max(axis=(1, 2)) <= 1e-5 * scale).all()
     d = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, precision=0, **CFG)
     with pytest.raises(Exception):
-        d.set_tuning([fused] * 3)
+        d.set_tuning([[0] * 8, [0] * 8, fused])
 
 
 def test_lake_at_rest_and_mass(M, A):

