@@ -141,6 +141,26 @@ int sgn_amr_get_boxes(const sgn_amr* a, int level, int* boxes, int cap);
 int sgn_amr_autotune(sgn_amr* a, int reps, int* choice, double* ms);
 int sgn_amr_set_tuning(sgn_amr* a, const int* choice);
 
+/* Retaking of level-0 steps that break the CFL limit.  The level-0 step is
+ * fixed for all substeps of a level-0 step (Sec. 4: CFL step from the global
+ * maximum wave speeds, subcycling in time across levels), but the speeds can
+ * grow within it, most of all on fine levels; the paper's step-size
+ * controller (Sec. 7) then takes a smaller step.  With max_retakes > 0 every
+ * level-0 step of sgn_amr_step and sgn_amr_step_dt whose largest face Courant
+ * number on any level exceeded 1 is undone (the states of all levels, the
+ * time, the clipped water and the status words as before it) and taken again
+ * with dt0 * CFL / (that Courant number), up to max_retakes times; a step still
+ * over the limit stays taken and the call returns SGN_ECFL as without
+ * retaking.  sgn_amr_step_dt may so advance by less than dt0 (the time
+ * returned by sgn_amr_step tells by how much).  Each level-0 step then
+ * synchronises the stream once, and the states of levels >= 1 are copied
+ * once per step into buffers held by the hierarchy (allocated at the first
+ * call with max_retakes > 0).  max_retakes in 0 (off, the default) .. 16; the
+ * setting carries over regrids.  Errors: EINVAL, ENOMEM.
+ * sgn_amr_retakes: the number of level-0 steps retaken since creation. */
+int sgn_amr_set_retake(sgn_amr* a, int max_retakes);
+int sgn_amr_retakes(const sgn_amr* a, long long* count);
+
 #ifdef __cplusplus
 }
 #endif

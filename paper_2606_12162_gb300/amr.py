@@ -33,6 +33,8 @@ AMR_SIGS = [
                                          ctypes.c_int]),
     ("sgn_amr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), DP]),
     ("sgn_amr_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("sgn_amr_set_retake", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sgn_amr_retakes", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
 ]
 _ready = False
 
@@ -210,6 +212,15 @@ class Hierarchy:
 
     def launches_per_step(self):
         return lib().sgn_amr_launches_per_step(self.h)
+
+    def set_retake(self, max_retakes):
+        """Retake level-0 steps that break the CFL limit (0: off)."""
+        _ck(lib().sgn_amr_set_retake(self.h, int(max_retakes)), "sgn_amr_set_retake")
+
+    def retakes(self):
+        n = ctypes.c_longlong()
+        _ck(lib().sgn_amr_retakes(self.h, ctypes.byref(n)), "sgn_amr_retakes")
+        return n.value
 
     def autotune(self, reps=20):
         """Tune every level's launch shapes and schedule (state unchanged).

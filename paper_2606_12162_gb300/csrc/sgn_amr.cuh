@@ -457,6 +457,10 @@ struct AmrBase {
   // fields [0, nf) of every patch of level l into out (device, [nf][NY][NX] of
   // the level's full grid); cells without a patch are left as they are
   virtual int get_level_device(int l, int nf, double* out) = 0;
+  // retaking of level-0 steps that break the CFL limit (0: off), and the
+  // number of steps retaken so far
+  virtual int set_retake(int max_retakes) = 0;
+  virtual long long retakes() const = 0;
 };
 
 AmrBase* make_amr_f64(int model);
@@ -546,6 +550,13 @@ class Amr : public AmrBase {
   bool fresh_ = true;
   int launches_ = 0;
   AmrDt dt_{};
+  // step retaking: the states of levels >= 1 before a level-0 step (level 0
+  // keeps its own in the buffer the step does not write), and the scalars and
+  // status words (device)
+  int retake_max_ = 0;
+  long long retakes_ = 0;
+  std::vector<Real*> bak_;
+  double* bsc_ = nullptr;      // 8 scalars, then AMR_MAXL status words
 
   template <typename T> T* up(const std::vector<T>& h) {
     if (h.empty()) return nullptr;
@@ -1115,10 +1126,88 @@ class Amr : public AmrBase {
     return status_to_error(st);
   }
 
+  int set_retake(int max_retakes) override {
+    if (max_retakes < 0 || max_retakes > 16) return SGN_EINVAL;
+    if (max_retakes > 0 && !bsc_) {
+      bsc_ = lv_[0]->template alloc_dev<double>(8 + AMR_MAXL);
+      if (!bsc_) return SGN_ENOMEM;
+      bak_.assign(L_, nullptr);
+      for (int l = 1; l < L_; l++) {
+        bak_[l] = lv_[0]->template alloc_dev<Real>((size_t)NV * lv_[l]->dev().fs);
+        if (!bak_[l]) return SGN_ENOMEM;
+      }
+    }
+    retake_max_ = max_retakes;
+    return SGN_OK;
+  }
+  long long retakes() const override { return retakes_; }
+
+  // the scalars, status words and finer states before a level-0 step
+  void backup() {
+    cudaMemcpyAsync(bsc_, sc_, 8 * sizeof(double), cudaMemcpyDeviceToDevice, st_);
+    for (int l = 0; l < L_; l++)
+      cudaMemcpyAsync((unsigned*)(bsc_ + 8) + l, lv_[l]->dev().status, sizeof(unsigned), cudaMemcpyDeviceToDevice,
+                      st_);
+    for (int l = 1; l < L_; l++) {
+      const Dev<Real>& d = lv_[l]->dev();
+      cudaMemcpyAsync(bak_[l], d.q[lv_[l]->cur()], (size_t)NV * d.fs * sizeof(Real), cudaMemcpyDeviceToDevice, st_);
+    }
+  }
+  void restore(unsigned key) {
+    setcur(key);
+    cudaMemcpyAsync(sc_, bsc_, 8 * sizeof(double), cudaMemcpyDeviceToDevice, st_);
+    for (int l = 0; l < L_; l++)
+      cudaMemcpyAsync(lv_[l]->dev().status, (unsigned*)(bsc_ + 8) + l, sizeof(unsigned), cudaMemcpyDeviceToDevice,
+                      st_);
+    for (int l = 1; l < L_; l++) {
+      const Dev<Real>& d = lv_[l]->dev();
+      cudaMemcpyAsync(d.q[lv_[l]->cur()], bak_[l], (size_t)NV * d.fs * sizeof(Real), cudaMemcpyDeviceToDevice, st_);
+    }
+  }
+
+  // One level-0 step (its dt already on the device) with retaking: a step
+  // whose largest face Courant number exceeded 1 on any level is undone and
+  // taken again with dt0 * CFL / Courant, up to retake_max_ times (Sec. 4:
+  // CFL step with subcycling; the step-size controller of Sec. 7 acts on wave
+  // speeds that can grow within a level-0 step).
+  int step_retake() {
+    const unsigned key = curbits();
+    backup();
+    for (int k = 0;; k++) {
+      int rc = launch_one();
+      if (rc) return rc;
+      SGN_CK(cudaMemcpyAsync(hsc_ + 10, sc_ + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st_));
+      for (int l = 0; l < L_; l++) {
+        SGN_CK(cudaMemcpyAsync((unsigned*)(hsc_ + 2) + l, lv_[l]->dev().status, sizeof(unsigned),
+                               cudaMemcpyDeviceToHost, st_));
+        SGN_CK(cudaMemcpyAsync((unsigned*)(hsc_ + 12) + l, (unsigned*)(bsc_ + 8) + l, sizeof(unsigned),
+                               cudaMemcpyDeviceToHost, st_));
+      }
+      SGN_CK(cudaStreamSynchronize(st_));
+      unsigned now = 0, before = 0;
+      for (int l = 0; l < L_; l++) {
+        now |= ((unsigned*)(hsc_ + 2))[l];
+        before |= ((unsigned*)(hsc_ + 12))[l];
+      }
+      // only a CFL flag this step raised, on a step that stayed finite
+      if (!(now & ST_CFL) || (before & ST_CFL) || (now & (ST_NONFINITE | ST_NEGDEPTH))) return SGN_OK;
+      const double dt_used = hsc_[10], courant = hsc_[11];
+      if (k >= retake_max_ || !(courant > 1.0) || !(dt_used > 0.0)) return SGN_ECFL;
+      restore(key);
+      k_amr_setdt<<<1, 32, 0, st_>>>(dt_, dt_used * prm_.cfl / courant);
+      SGN_CK(cudaGetLastError());
+      retakes_++;
+    }
+  }
+
   int step(int n, double* t_out) override {
     if (n < 0) return SGN_EINVAL;
     if (fresh_) { int rc = begin(); if (rc) return rc; }
-    for (int i = 0; i < n; i++) { int rc = launch_one(); if (rc) return rc; }
+    for (int i = 0; i < n; i++) {
+      int rc = retake_max_ > 0 ? step_retake() : launch_one();
+      if (rc == SGN_ECFL) break;
+      if (rc) return rc;
+    }
     return finish(t_out);
   }
 
@@ -1126,8 +1215,8 @@ class Amr : public AmrBase {
     if (!(dt0 > 0)) return SGN_EINVAL;
     if (fresh_) { int rc = begin(); if (rc) return rc; }
     k_amr_setdt<<<1, 32, 0, st_>>>(dt_, dt0);
-    int rc = launch_one();
-    if (rc) return rc;
+    int rc = retake_max_ > 0 ? step_retake() : launch_one();
+    if (rc && rc != SGN_ECFL) return rc;
     return finish(nullptr);
   }
 

@@ -273,6 +273,8 @@ struct sgn_amr {
   sgn::AmrArgs args;        // creation arguments (boxes and bathymetry pointer not kept)
   sgn_allocator alloc;
   bool has_alloc;
+  int retake = 0;           // retakes per level-0 step (kept across regrids)
+  long long retaken = 0;    // steps retaken by the hierarchies that regrids replaced
 };
 
 // a hierarchy from creation arguments and a box list (validated by init)
@@ -421,10 +423,12 @@ int sgn_amr_regrid(sgn_amr* h, const double* b_finest, const int* nboxes, const 
   h->args.boxes.clear();
   if (r) return r;
   r = impl->take_state(h->impl);
+  if (!r && h->retake) r = impl->set_retake(h->retake);
   if (r) {
     delete impl;
     return r;
   }
+  h->retaken += h->impl->retakes();
   delete h->impl;
   h->impl = impl;
   return SGN_OK;
@@ -507,6 +511,19 @@ int sgn_amr_autotune(sgn_amr* a, int reps, int* choice, double* ms) {
 
 int sgn_amr_set_tuning(sgn_amr* a, const int* choice) {
   return (a && choice) ? a->impl->set_tuning(choice) : SGN_EINVAL;
+}
+
+int sgn_amr_set_retake(sgn_amr* a, int max_retakes) {
+  if (!a) return SGN_EINVAL;
+  const int r = a->impl->set_retake(max_retakes);
+  if (!r) a->retake = max_retakes;
+  return r;
+}
+
+int sgn_amr_retakes(const sgn_amr* a, long long* count) {
+  if (!a || !count) return SGN_EINVAL;
+  *count = a->retaken + a->impl->retakes();
+  return SGN_OK;
 }
 
 }  // extern "C"

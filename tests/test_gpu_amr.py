@@ -199,6 +199,50 @@ def test_hierarchy_levels_mix_schedules(M):
         d.set_tuning([[0] * 8, [0] * 8, fused])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_retake_of_a_level0_step_over_the_cfl_limit(M, precision):
+    """A level-0 step of 2.5 times the CFL step breaks the limit (SGN_ECFL
+    without retaking).  With retaking the step is undone -- the states of all
+    levels, time, clipped water and status as before it -- and taken again with
+    dt0 * CFL / Courant: the result equals a direct step of that size bit for
+    bit (FP64, and mixed precision with the one-pass kernel on every level),
+    the time advances by that step, and the run goes on; the setting and the
+    count carry over a regrid."""
+    from paper_2606_12162_gb300 import sgn
+    b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=15)
+
+    def mk():
+        g = M.Hierarchy(b, 24, 20, 0.2, 2, W.amr_boxes_small(), model=2, precision=precision, **CFG)
+        if precision == 1:
+            g.set_tuning(seq_choice(3, 2))
+        g.set_state(qs)
+        return g
+
+    g0 = mk()
+    dt = g0.next_dt()
+    with pytest.raises(sgn.SGNError):
+        g0.step_dt(2.5 * dt)
+    g1 = mk()
+    with pytest.raises(sgn.SGNError):
+        g1.set_retake(17)
+    g1.set_retake(4)
+    g1.step_dt(2.5 * dt)
+    t1 = g1.step(0)
+    assert 0.0 < t1 < 1.2 * dt and g1.retakes() >= 1 and g1.status() == 0
+    g2 = mk()
+    g2.step_dt(t1)
+    assert g2.step(0) == t1
+    for l in range(3):
+        for k in range(len(g1.boxes[l])):
+            assert np.array_equal(g1.get_patch(l, k), g2.get_patch(l, k)), (l, k)
+    assert g1.mass() == g2.mass() and g1.next_dt() == g2.next_dt()
+    n = g1.retakes()
+    g1.regrid(b, W.amr_boxes_small())
+    assert g1.retakes() == n
+    g1.step(3)
+    assert g1.status() == 0
+
+
 def test_lake_at_rest_and_mass(M, A):
     b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
     rest = []
