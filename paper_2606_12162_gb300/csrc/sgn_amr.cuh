@@ -534,6 +534,9 @@ class Amr : public AmrBase {
     int* acoarse = nullptr; int* afine = nullptr; int navg = 0;
   };
   std::vector<Owner> own_;     // per level: box lookup by cell
+  // per level >= 1: the regions of the atlas (runs of boxes of equal rows that
+  // abut in x), each with one frame; Box::parent holds the region's first box
+  std::vector<std::vector<Box>> rg_;
   std::vector<Tabs> tb_;
   std::vector<long long> cells_, atlas_;
   CoarseBath bath_;            // bathymetry of levels 0 .. L-2
@@ -686,6 +689,7 @@ class Amr : public AmrBase {
     };
     // atlases and level solvers
     lv_.assign(L, nullptr);
+    rg_.assign(L, {});
     cells_.assign(L, 0); atlas_.assign(L, 0);
     std::vector<int> NXA(L), NYA(L);
     for (int l = 0; l < L; l++) {
@@ -703,30 +707,67 @@ class Amr : public AmrBase {
         bx_[0][0].px = NG - G;   // level 0's frame is the atlas's own
         bx_[0][0].py = NG - G;
       } else {
-        // shelf packing of the (nx + 2G) x (ny + 2G) frames, tallest first
-        std::vector<int> ord(bx_[l].size());
+        // regions: runs of boxes of equal rows that abut in x share one frame
+        // (the faces between them are interior faces of the atlas, without
+        // ghost cells); each box keeps its place inside its region
+        std::vector<Box>& rg = rg_[l];
+        std::vector<int> byrow(bx_[l].size());
+        for (size_t k = 0; k < byrow.size(); k++) byrow[k] = (int)k;
+        std::stable_sort(byrow.begin(), byrow.end(), [&](int u, int v) {
+          const Box &a = bx_[l][u], &b = bx_[l][v];
+          return a.j0 != b.j0 ? a.j0 < b.j0 : (a.ny != b.ny ? a.ny < b.ny : a.i0 < b.i0);
+        });
+        std::vector<int> regof(bx_[l].size());
+        for (int k : byrow) {
+          const Box& b = bx_[l][k];
+          if (!rg.empty() && rg.back().j0 == b.j0 && rg.back().ny == b.ny && rg.back().i0 + rg.back().nx == b.i0) {
+            rg.back().nx += b.nx;
+          } else {
+            rg.push_back(Box{b.i0, b.j0, b.nx, b.ny, 0, 0, k});   // parent: the region's first box
+          }
+          regof[k] = (int)rg.size() - 1;
+        }
+        // shelf packing of the (nx + 2G) x (ny + 2G) region frames, tallest
+        // first, at the shelf width (from 0.6 to 1.8 x sqrt(area)) that gives
+        // the smallest atlas
+        std::vector<int> ord(rg.size());
         for (size_t k = 0; k < ord.size(); k++) ord[k] = (int)k;
-        std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return bx_[l][u].ny > bx_[l][v].ny; });
+        std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return rg[u].ny > rg[v].ny; });
         double area = 0;
         int maxw = 2;
-        for (auto& b : bx_[l]) { area += (double)(b.nx + 2 * G) * (b.ny + 2 * G); maxw = std::max(maxw, b.nx + 2 * G); }
+        for (auto& b : rg) { area += (double)(b.nx + 2 * G) * (b.ny + 2 * G); maxw = std::max(maxw, b.nx + 2 * G); }
+        auto shelves = [&](int w, bool place) {
+          int x = 0, y = 0, sh = 0;
+          for (int k : ord) {
+            Box& b = rg[k];
+            if (x + b.nx + 2 * G > w) { x = 0; y += sh; sh = 0; }
+            if (place) { b.px = x + NG; b.py = y + NG; }   // the atlas has its own two-cell frame
+            x += b.nx + 2 * G;
+            sh = std::max(sh, b.ny + 2 * G);
+          }
+          return std::max(2, y + sh);
+        };
         nxa = std::max(maxw, (int)std::ceil(std::sqrt(area * 1.1)));
-        int x = 0, y = 0, sh = 0;
-        for (int k : ord) {
-          Box& b = bx_[l][k];
-          if (x + b.nx + 2 * G > nxa) { x = 0; y += sh; sh = 0; }
-          b.px = x + NG; b.py = y + NG;   // the atlas has its own two-cell frame
-          x += b.nx + 2 * G;
-          sh = std::max(sh, b.ny + 2 * G);
+        long long best = (long long)nxa * shelves(nxa, false);
+        for (int i = 0; i <= 60; i++) {
+          const int w = std::max(maxw, (int)(std::sqrt(area) * (0.6 + 0.02 * i)));
+          const long long a = (long long)w * shelves(w, false);
+          if (a < best) { best = a; nxa = w; }
         }
-        nya = std::max(2, y + sh);
+        nya = shelves(nxa, true);
+        for (int k = 0; k < (int)bx_[l].size(); k++) {
+          Box& b = bx_[l][k];
+          const Box& R = rg[regof[k]];
+          b.px = R.px + (b.i0 - R.i0);
+          b.py = R.py;
+        }
         ca.grid = g0_;
         ca.grid.nx = nxa; ca.grid.ny = nya;
         ca.grid.dx = dx_[l]; ca.grid.dy = dx_[l];
         for (int s = 0; s < 4; s++) ca.grid.bc[s] = SGN_BC_EXTRAP;
         bd.assign((size_t)nxa * nya, 1000.0);   // empty atlas cells: dry land
         pd.assign((size_t)nxa * nya, 0);
-        for (auto& b : bx_[l])
+        for (auto& b : rg)
           for (int J = 0; J < b.ny + 2 * G; J++)
             for (int I = 0; I < b.nx + 2 * G; I++) {
               int X = b.i0 - G + I, Y = b.j0 - G + J;
@@ -781,8 +822,8 @@ class Amr : public AmrBase {
     for (int l = 1; l < L; l++) {
       std::vector<GEnt> fill, bcs;
       std::vector<ParEnt> pe;
-      for (int k = 0; k < (int)bx_[l].size(); k++) {
-        const Box& b = bx_[l][k];
+      // the ghost cells of every region's frame (b: the region)
+      for (const Box& b : rg_[l]) {
         for (int J = 0; J < b.ny + 2 * G; J++)
           for (int I = 0; I < b.nx + 2 * G; I++) {
             if (I >= G && I < b.nx + G && J >= G && J < b.ny + G) continue;
@@ -797,7 +838,7 @@ class Amr : public AmrBase {
               bcs.push_back(GEnt{dst, pidx(l, b, Is, Js), GE_BC | (fx ? 4 : 0) | (fy ? 8 : 0)});
               continue;
             }
-            int o = own[l].find(X, Y, k);
+            int o = own[l].find(X, Y);
             if (o >= 0) {
               const Box& s = bx_[l][o];
               fill.push_back(GEnt{dst, pidx(l, s, X - s.i0 + G, Y - s.j0 + G), GE_SIB});
@@ -807,8 +848,10 @@ class Amr : public AmrBase {
               if (side) kd[l][dense(l, b, I, J)] |= 4;
               continue;
             }
+            // interpolated from the parent of the region's box nearest in x
+            const int kb = own[l].find(std::min(std::max(X, b.i0), b.i0 + b.nx - 1), b.j0);
             ParEnt q;
-            if (!par_entry(l, b, X, Y, dst, q)) return SGN_EINVAL;
+            if (kb < 0 || !par_entry(l, bx_[l][kb], X, Y, dst, q)) return SGN_EINVAL;
             pe.push_back(q);
           }
       }
