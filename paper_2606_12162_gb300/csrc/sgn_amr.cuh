@@ -767,14 +767,42 @@ class Amr : public AmrBase {
         for (int s = 0; s < 4; s++) ca.grid.bc[s] = SGN_BC_EXTRAP;
         bd.assign((size_t)nxa * nya, 1000.0);   // empty atlas cells: dry land
         pd.assign((size_t)nxa * nya, 0);
-        for (auto& b : rg)
+        // bathymetry and phi_T of every region's frame: b read once per cell
+        // of the frame and an n-cell margin, phi_T from those values (the
+        // boundary-mapped rule of phival where a cell lies outside the domain)
+        const int n = prm_.n_transition;
+        std::vector<std::pair<int, int>> nbh;
+        {
+          const double dxl = dx_[l], r2 = (n * dxl) * (n * dxl);
+          for (int dj = -n; dj <= n; dj++)
+            for (int di = -n; di <= n; di++)
+              if ((di * dxl) * (di * dxl) + (dj * dxl) * (dj * dxl) <= r2) nbh.push_back(std::make_pair(di, dj));
+        }
+        std::vector<double> loc;
+        for (auto& b : rg) {
+          const int Wl = b.nx + 2 * G + 2 * n, Hl = b.ny + 2 * G + 2 * n;
+          loc.resize((size_t)Wl * Hl);
+          for (int JJ = 0; JJ < Hl; JJ++)
+            for (int II = 0; II < Wl; II++) loc[(size_t)JJ * Wl + II] = bval(l, b.i0 - G - n + II, b.j0 - G - n + JJ);
           for (int J = 0; J < b.ny + 2 * G; J++)
             for (int I = 0; I < b.nx + 2 * G; I++) {
-              int X = b.i0 - G + I, Y = b.j0 - G + J;
-              size_t o = (size_t)(b.py - NG + J) * nxa + (b.px - NG + I);
-              bd[o] = bval(l, X, Y);
-              pd[o] = phival(l, X, Y);
+              const int X = b.i0 - G + I, Y = b.j0 - G + J;
+              const size_t o = (size_t)(b.py - NG + J) * nxa + (b.px - NG + I);
+              const size_t c = (size_t)(J + n) * Wl + (I + n);
+              bd[o] = loc[c];
+              if (X < 0 || Y < 0 || X >= NX_[l] || Y >= NY_[l]) {
+                pd[o] = phival(l, X, Y);
+                continue;
+              }
+              double mn = 1e300;
+              for (const auto& q : nbh) {
+                double H = -loc[c + (long)q.second * Wl + q.first];
+                H = H > 0.0 ? H : 0.0;
+                mn = H < mn ? H : mn;
+              }
+              pd[o] = mn > prm_.h_star ? 1 : 0;
             }
+        }
       }
       NXA[l] = nxa; NYA[l] = nya;
       atlas_[l] = (long long)(nxa + 4) * (nya + 4);
@@ -800,13 +828,18 @@ class Amr : public AmrBase {
       xs[l].assign((size_t)NXA[l] * NYA[l], -1);
       for (int k = 0; k < (int)bx_[l].size(); k++) {
         const Box& b = bx_[l][k];
-        for (int j = 0; j < b.ny; j++)
-          for (int i = 0; i < b.nx; i++) {
-            unsigned char v = 1;
-            if (l + 1 < L && own[l + 1].find((b.i0 + i) * r, (b.j0 + j) * r) >= 0) v |= 2;
-            kd[l][dense(l, b, G + i, G + j)] = v;
-          }
+        for (int j = 0; j < b.ny; j++) {
+          unsigned char* row = &kd[l][dense(l, b, G, G + j)];
+          std::fill(row, row + b.nx, (unsigned char)1);
+        }
       }
+      // covered: the footprint of every box of the next level, in its parent
+      if (l + 1 < L)
+        for (const Box& c : bx_[l + 1]) {
+          const Box& P = bx_[l][c.parent];
+          for (int jc = c.j0 / r; jc < (c.j0 + c.ny) / r; jc++)
+            for (int ic = c.i0 / r; ic < (c.i0 + c.nx) / r; ic++) kd[l][dense(l, P, G + ic - P.i0, G + jc - P.j0)] |= 2;
+        }
     }
     // export slot of a cell (assigned on first use)
     auto slot_of = [&](int l, const Box& b, int I, int J) {
@@ -1416,18 +1449,25 @@ class Amr : public AmrBase {
       std::vector<ParEnt> par;
       for (const Box& b : bx_[l]) {
         for (int j = 0; j < b.ny; j++)
-          for (int i = 0; i < b.nx; i++) {
+          for (int i = 0; i < b.nx;) {
             const int X = b.i0 + i, Y = b.j0 + j, dst = pidx(l, b, i + G, j + G);
             const int k = oo.find(X, Y);
             if (k >= 0) {
+              // the run of this row that the old box covers
               const Box& s = o->bx_[l][k];
-              cd.push_back(dst);
-              cs.push_back(o->pidx(l, s, X - s.i0 + G, Y - s.j0 + G));
+              const int m = std::min(b.nx - i, s.i0 + s.nx - X);
+              const int src = o->pidx(l, s, X - s.i0 + G, Y - s.j0 + G);
+              for (int q = 0; q < m; q++) {
+                cd.push_back(dst + q);
+                cs.push_back(src + q);
+              }
+              i += m;
               continue;
             }
             ParEnt e;
             if (!par_entry(l, b, X, Y, dst, e)) return SGN_EINVAL;
             par.push_back(e);
+            i++;
           }
       }
       if (!cd.empty()) {
