@@ -424,6 +424,32 @@ def test_config2_full_size_mixed_against_fp64_1000_steps(sgn):
     assert np.nanmax(np.abs(ta[ok] - tb[ok])) <= dt * 1.0001
 
 
+def test_config3_full_size_mixed_against_fp64(sgn):
+    """Full 8192 x 8192 third configuration (fractal bathymetry, 2 m uplift),
+    400 steps, each path on its own CFL steps: the mixed path (one-pass kernel,
+    the default on this grid) against the (oracle-checked) FP64 GPU path, at
+    the configuration's bar: relative L2 over wet cells of eta, hu, hv <= 1e-3
+    and max |eta| error <= 1e-2 of the 2 m uplift; both runs without a status
+    flag.  (The 2000-step run of the configuration measures 1.7e-6 and 7.6e-6;
+    the FP64 path takes about 0.13 s a step here, so the test keeps to 400.)"""
+    c = W.config3(model=2)
+    cfg = dict(dx=c["dx"], model=2, bc=c["bc"], h_star=c["h_star"], alpha=3.0, cfl=c["cfl"],
+               dry_tol=c["dry_tol"])
+    out = []
+    for prec in (0, 1):
+        s = sgn.Solver(c["b"], precision=prec, **cfg)
+        s.set_state(c["q"])
+        s.step(400)
+        assert s.status()[0] == 0
+        out.append(s.get_state()[0])
+        del s
+    q64, qm = out
+    wet = (q64[0] - c["b"]) > 1e-3
+    err = rel_l2(qm[:3], q64[:3], wet)
+    assert err[0] <= 1e-3 and err[1] <= 1e-3 and err[2] <= 1e-3, err
+    assert np.abs(qm[0] - q64[0]).max() <= 1e-2 * 2.0
+
+
 def test_c2_override_matches_oracle(sgn, oracle_mod):
     """A prescribed relaxation field (sgn_set_c2; the constant-c^2 setting of
     the Sec. 5.3 steady-state test, here a varying positive field) gives the
