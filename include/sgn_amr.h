@@ -5,10 +5,13 @@
  * subcycling in time; refinement along the advancing front, Sec. 6.3).
  *
  * Every patch of a level is laid out in one padded "atlas" grid of that level
- * (each patch with its own frame of two ghost layers), so that every stage of
+ * (runs of patches with the same rows that abut in x share one frame of ghost
+ * cells: three layers in mixed precision, two in FP64), so that every stage of
  * the step runs as ONE launch over all patches of the level, whatever their
- * number and sizes; a level-0 step with all finer substeps is replayed as one
- * CUDA graph.
+ * number and sizes: in mixed precision a level step is one launch of the
+ * one-pass kernel of the uniform grid (on every level large enough to fill
+ * the GPU), after one ghost-fill launch; a level-0 step with all finer
+ * substeps is replayed as one CUDA graph.
  *
  * Definitions the paper leaves to GeoClaw (they are the library's readings):
  *  - level 0 is one patch covering the grid; level l >= 1 holds disjoint boxes
@@ -22,7 +25,8 @@
  *    from the parent at the substep's time weight (a dry parent cell gives a
  *    ghost at the still level; a conserved ghost value never exceeds the
  *    parent cell's own in magnitude);
- *  - positivity factors of ghost cells copied from a patch are taken from it;
+ *  - positivity factors of ghost cells copied from a patch are the patch's
+ *    own (copied, or computed in the three-layer frame, to the same value);
  *  - mass is refluxed at coarse faces between covered and uncovered cells (a
  *    correction that would leave a negative depth is clipped to zero depth and
  *    the water added is reported); covered coarse cells hold the mean of their
