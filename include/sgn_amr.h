@@ -107,10 +107,12 @@ int sgn_amr_launches_per_step(const sgn_amr* a);
  * at the current time; then every covered coarse cell becomes the mean of its
  * children (average-down, finest level first).  The time and the clipped water
  * carry over; the next step is recomputed from the new states; the status
- * starts clear; launch shapes return to their defaults (tune again with
- * sgn_amr_autotune).  The new hierarchy is built before the old one is
- * released (both are held on the device for the duration of the call).  On an
- * error the old hierarchy is left as it was.  Synchronises the stream.
+ * starts clear; the launch shapes of levels >= 1 return to their defaults
+ * (tune again with sgn_amr_autotune; level 0 keeps its solver, tuning and
+ * state, which the new hierarchy takes over).  The new hierarchy is built
+ * before the old one is released (both are held on the device for the
+ * duration of the call).  On an error other than ECUDA the old hierarchy is
+ * left as it was (level 0 handed back).  Synchronises the stream.
  * Errors: EINVAL (arguments, box rules), ENOMEM, ECUDA. */
 int sgn_amr_regrid(sgn_amr* a, const double* b_finest, const int* nboxes, const int* boxes);
 

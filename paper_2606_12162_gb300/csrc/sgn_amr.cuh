@@ -561,9 +561,30 @@ class Amr : public AmrBase {
   std::vector<Real*> bak_;
   double* bsc_ = nullptr;      // 8 scalars, then AMR_MAXL status words
 
+  // device memory of the hierarchy's own tables and buffers (the level
+  // solvers hold their planes), from the caller's allocator or cudaMalloc,
+  // freed with the hierarchy
+  sgn_allocator al_{};
+  bool has_al_ = false;
+  std::vector<void*> mine_;
+  // a regrid's hierarchy takes over the level-0 solver of the one it
+  // replaces (level 0 does not change); until it is committed the donor
+  // gets it back if this hierarchy is destroyed
+  Amr* donor_ = nullptr;
+  std::vector<unsigned char> kd0_;   // level 0's kind plane (dense) ...
+  std::vector<int> xs0_;             // ... and export slots, as this hierarchy set them
+  template <typename T> T* adev(size_t n) {
+    const size_t bytes = n * sizeof(T) + 256;
+    void* p = nullptr;
+    if (has_al_) p = al_.alloc(bytes, al_.ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) mine_.push_back(p);
+    return (T*)p;
+  }
+
   template <typename T> T* up(const std::vector<T>& h) {
     if (h.empty()) return nullptr;
-    T* d = lv_[0]->template alloc_dev<T>(h.size());
+    T* d = adev<T>(h.size());
     if (!d) return nullptr;
     if (cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st_) != cudaSuccess) return nullptr;
     return d;
@@ -575,7 +596,17 @@ class Amr : public AmrBase {
   ~Amr() override {
     if (st_) cudaStreamSynchronize(st_);
     for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second.first);
+    if (donor_ && !lv_.empty() && lv_[0] && donor_->lv_.size() && !donor_->lv_[0]) {
+      donor_->lv_[0] = lv_[0];
+      lv_[0] = nullptr;
+      if (!donor_->kd0_.empty()) donor_->lv_[0]->set_kind(donor_->kd0_.data());
+      if (!donor_->xs0_.empty()) donor_->lv_[0]->set_xslot(donor_->xs0_.data());
+    }
     for (int l = (int)lv_.size() - 1; l >= 0; l--) delete lv_[l];
+    for (void* p : mine_) {
+      if (has_al_) al_.free(p, al_.ctx);
+      else cudaFree(p);
+    }
     if (hsc_) cudaFreeHost(hsc_);
     if (cap_) cudaStreamDestroy(cap_);
   }
@@ -593,6 +624,7 @@ class Amr : public AmrBase {
 
   int init(const AmrArgs& a) override {
     L_ = a.L; r_ = a.r; g0_ = a.grid; prm_ = a.prm; st_ = a.stream;
+    if (a.alloc && a.alloc->alloc && a.alloc->free) { al_ = *a.alloc; has_al_ = true; }
     const int r = r_, L = L_;
     SGN_CK(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
     SGN_CK(cudaMallocHost((void**)&hsc_, 16 * sizeof(double)));
@@ -703,9 +735,21 @@ class Amr : public AmrBase {
       if (l == 0) {
         nxa = g0_.nx; nya = g0_.ny;
         ca.grid = g0_;
-        bd.assign(blev(0), blev(0) + (size_t)NX_[0] * NY_[0]);
         bx_[0][0].px = NG - G;   // level 0's frame is the atlas's own
         bx_[0][0].py = NG - G;
+        if (a.prev) {
+          // a regrid: level 0 is the replaced hierarchy's, state included
+          auto* o = dynamic_cast<Amr<MODEL, Real>*>(const_cast<AmrBase*>(a.prev));
+          if (o && !o->lv_.empty() && o->lv_[0] && !o->NX_.empty() && o->NX_[0] == NX_[0] && o->NY_[0] == NY_[0]) {
+            lv_[0] = o->lv_[0];
+            o->lv_[0] = nullptr;
+            donor_ = o;
+            NXA[0] = nxa; NYA[0] = nya;
+            atlas_[0] = (long long)(nxa + 4) * (nya + 4);
+            continue;
+          }
+        }
+        bd.assign(blev(0), blev(0) + (size_t)NX_[0] * NY_[0]);
       } else {
         // regions: runs of boxes of equal rows that abut in x share one frame
         // (the faces between them are interior faces of the atlas, without
@@ -966,7 +1010,7 @@ class Amr : public AmrBase {
       t.nxc = (int)xcells[l].size();
       if (t.nxc) {
         t.xcell = up(xcells[l]);
-        t.xphi = lv_[0]->template alloc_dev<Real>((size_t)(l ? r : 1) * t.nxc * 4);
+        t.xphi = adev<Real>((size_t)(l ? r : 1) * t.nxc * 4);
         if (!t.xcell || !t.xphi) return SGN_ENOMEM;
         SGN_CK(cudaMemsetAsync(t.xphi, 0, (size_t)(l ? r : 1) * t.nxc * 4 * sizeof(Real), st_));
       }
@@ -975,17 +1019,21 @@ class Amr : public AmrBase {
       rc = lv_[l]->set_xslot(xs[l].data());
       if (rc) return rc;
     }
+    // level 0's planes, to give them back if a regrid's hierarchy that took
+    // over this level 0 is deleted before it is committed
+    kd0_ = std::move(kd[0]);
+    xs0_ = std::move(xs[0]);
     // each level keeps its solver's default schedule: the one-pass kernel in
     // mixed precision where the atlas gives the resident blocks enough tiles,
     // else the kernel sequence (both export the same fluxes and give sibling
     // ghosts the same positivity factors, so the levels may differ)
-    sc_ = lv_[0]->template alloc_dev<double>(8);
+    sc_ = adev<double>(8);
     if (!sc_) return SGN_ENOMEM;
     SGN_CK(cudaMemsetAsync(sc_, 0, 8 * sizeof(double), st_));
     size_t mx = 0;
     for (auto& v : bx_)
       for (auto& b : v) mx = std::max(mx, (size_t)b.nx * b.ny);
-    staging_ = lv_[0]->template alloc_dev<double>(mx * NV);
+    staging_ = adev<double>(mx * NV);
     if (!staging_) return SGN_ENOMEM;
     stage_bytes_ = mx * NV * sizeof(double);
     // step bookkeeping
@@ -1205,11 +1253,11 @@ class Amr : public AmrBase {
   int set_retake(int max_retakes) override {
     if (max_retakes < 0 || max_retakes > 16) return SGN_EINVAL;
     if (max_retakes > 0 && !bsc_) {
-      bsc_ = lv_[0]->template alloc_dev<double>(8 + AMR_MAXL);
+      bsc_ = adev<double>(8 + AMR_MAXL);
       if (!bsc_) return SGN_ENOMEM;
       bak_.assign(L_, nullptr);
       for (int l = 1; l < L_; l++) {
-        bak_[l] = lv_[0]->template alloc_dev<Real>((size_t)NV * lv_[l]->dev().fs);
+        bak_[l] = adev<Real>((size_t)NV * lv_[l]->dev().fs);
         if (!bak_[l]) return SGN_ENOMEM;
       }
     }
@@ -1373,7 +1421,7 @@ class Amr : public AmrBase {
         mx = std::max(mx, b.nx);
         my = std::max(my, b.ny);
       }
-      int* dt = lv_[0]->template alloc_dev<int>(t.size());
+      int* dt = adev<int>(t.size());
       if (!dt) return SGN_ENOMEM;
       SGN_CK(cudaMemcpyAsync(dt, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice, st_));
       SGN_CK(cudaStreamSynchronize(st_));
@@ -1400,7 +1448,7 @@ class Amr : public AmrBase {
     std::vector<unsigned char> atl(d.fs);
     if ((size_t)d.fs > stage_bytes_) {
       if (!flag_buf_ || flag_cap_ < d.fs) {
-        flag_buf_ = lv_[0]->template alloc_dev<unsigned char>(d.fs);
+        flag_buf_ = adev<unsigned char>(d.fs);
         if (!flag_buf_) return SGN_ENOMEM;
         flag_cap_ = d.fs;
       }
@@ -1437,11 +1485,13 @@ class Amr : public AmrBase {
     const int r = r_;
     SGN_CK(cudaStreamSynchronize(o->st_));
     SGN_CK(cudaStreamSynchronize(st_));
-    Dev<Real>& n0 = lv_[0]->dev();
-    Dev<Real>& o0 = o->lv_[0]->dev();
-    if (n0.fs != o0.fs || n0.pitch != o0.pitch) return SGN_EINVAL;
-    SGN_CK(cudaMemcpyAsync(n0.q[lv_[0]->cur()], o0.q[o->lv_[0]->cur()], (size_t)NV * n0.fs * sizeof(Real),
-                           cudaMemcpyDeviceToDevice, st_));
+    if (o->lv_[0]) {   // level 0 not taken over: copy its state
+      Dev<Real>& n0 = lv_[0]->dev();
+      Dev<Real>& o0 = o->lv_[0]->dev();
+      if (n0.fs != o0.fs || n0.pitch != o0.pitch) return SGN_EINVAL;
+      SGN_CK(cudaMemcpyAsync(n0.q[lv_[0]->cur()], o0.q[o->lv_[0]->cur()], (size_t)NV * n0.fs * sizeof(Real),
+                             cudaMemcpyDeviceToDevice, st_));
+    }
     for (int l = 1; l < L_; l++) {
       Owner oo;
       oo.build(o->bx_[l], NX_[l], NY_[l]);
@@ -1497,6 +1547,7 @@ class Amr : public AmrBase {
     SGN_CK(cudaMemcpyAsync(sc_ + 1, o->sc_ + 1, sizeof(double), cudaMemcpyDeviceToDevice, st_));
     SGN_CK(cudaMemcpyAsync(sc_ + 4, o->sc_ + 4, sizeof(double), cudaMemcpyDeviceToDevice, st_));
     SGN_CK(cudaStreamSynchronize(st_));
+    donor_ = nullptr;   // committed: the level-0 solver is this hierarchy's
     return SGN_OK;
   }
 

@@ -422,8 +422,10 @@ int sgn_amr_regrid(sgn_amr* h, const double* b_finest, const int* nboxes, const 
   h->args.prev = nullptr;
   h->args.boxes.clear();
   if (r) return r;
-  r = impl->take_state(h->impl);
-  if (!r && h->retake) r = impl->set_retake(h->retake);
+  // (the new hierarchy may take over the old one's level 0: it hands it
+  // back if it is deleted before take_state has succeeded)
+  if (h->retake) r = impl->set_retake(h->retake);
+  if (!r) r = impl->take_state(h->impl);
   if (r) {
     delete impl;
     return r;

@@ -460,9 +460,12 @@ class Solver : public SolverBase {
   dim3 grid_interior() const { return gInt_; }
   template <typename T> T* alloc_dev(size_t n) { return dnew<T>(n); }
   // kind plane from a dense ny*nx host array (ghost frame 0)
+  unsigned char* kind_buf_ = nullptr;   // the kind plane (kept across calls)
+  int* xslot_buf_ = nullptr;            // the export slot plane (likewise)
   int set_kind(const unsigned char* kind_dense) {
-    unsigned char* kp = dnew<unsigned char>(d_.fs);
+    unsigned char* kp = kind_buf_ ? kind_buf_ : dnew<unsigned char>(d_.fs);
     if (!kp) return SGN_ENOMEM;
+    kind_buf_ = kp;
     std::vector<unsigned char> h(d_.fs, 0);
     for (int j = 0; j < d_.ny; j++)
       for (int i = 0; i < d_.nx; i++)
@@ -475,8 +478,9 @@ class Solver : public SolverBase {
   }
   // export slots of a refined level (dense ny*nx host array, -1: none)
   int set_xslot(const int* slot_dense) {
-    int* sp = dnew<int>(d_.fs);
+    int* sp = xslot_buf_ ? xslot_buf_ : dnew<int>(d_.fs);
     if (!sp) return SGN_ENOMEM;
+    xslot_buf_ = sp;
     std::vector<int> h(d_.fs, -1);
     for (int j = 0; j < d_.ny; j++)
       for (int i = 0; i < d_.nx; i++) h[(size_t)(j + NG) * d_.pitch + (i + NG)] = slot_dense[(size_t)j * d_.nx + i];

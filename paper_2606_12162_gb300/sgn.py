@@ -158,11 +158,18 @@ class _TorchAllocator:
         self.torch = torch
         self.device = device
         self.live = {}
+        # allocations still granted (None: no limit) -- lets a test make the
+        # library run out of device memory at a chosen point
+        self.allow = None
         self.c_alloc = ALLOC_FN(self._alloc)
         self.c_free = FREE_FN(self._free)
         self.struct = Allocator(self.c_alloc, self.c_free, None)
 
     def _alloc(self, nbytes, ctx):
+        if self.allow is not None:
+            if self.allow <= 0:
+                return None
+            self.allow -= 1
         try:
             t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
         except Exception:

@@ -313,6 +313,46 @@ def test_regrid_against_oracle(M, A, model, seed, wetdry):
     assert g.status() == 0
 
 
+def test_regrid_out_of_device_memory_keeps_the_hierarchy(M):
+    """A regrid's new hierarchy takes over the old one's level-0 solver (level
+    0 does not change).  If it then runs out of device memory -- the allocator
+    refuses after the first n allocations of the regrid, for several n, so the
+    failure comes at different points of its set-up and state transfer -- the
+    call returns SGN_ENOMEM and gives level 0 back with its own kind and
+    export planes: the old hierarchy steps on exactly as one that never tried
+    the regrid."""
+    from paper_2606_12162_gb300 import sgn
+    nx0, ny0, r = 24, 20, 2
+    b, qs = W.amr_small_case(2, nx0, ny0, r, 3, seed=24, amp=0.25)
+    moved = W.amr_boxes_small_moved()
+
+    def make():
+        g = M.Hierarchy(b, nx0, ny0, 0.2, r, W.amr_boxes_small(), model=2, precision=1, **CFG)
+        g.set_state(qs)
+        return g
+    ref = make()
+    ref.step(6)
+    failed = 0
+    for n in (0, 3, 12, 30, 60, 120):
+        g = make()
+        g.step(3)
+        g._alloc.allow = n
+        try:
+            g.regrid(b, moved)
+            g._alloc.allow = None
+            continue                      # enough memory: the regrid went through
+        except sgn.SGNError as e:
+            assert e.code == -2           # SGN_ENOMEM
+        g._alloc.allow = None
+        failed += 1
+        g.step(3)
+        for l in range(3):
+            for k in range(len(g.boxes[l])):
+                assert np.array_equal(g.get_patch(l, k), ref.get_patch(l, k)), (n, l, k)
+        assert g.next_dt() == ref.next_dt() and g.mass() == ref.mass() and g.status() == 0
+    assert failed >= 3
+
+
 def test_regrid_same_boxes_bitwise_and_invalid_rejected(M):
     from paper_2606_12162_gb300 import sgn
     nx0, ny0, r = 24, 20, 2
