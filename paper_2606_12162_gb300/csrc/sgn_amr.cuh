@@ -1,23 +1,26 @@
 // sgn_amr.cuh -- refined hierarchy (block-structured AMR, Sec. 4 of the paper:
 // patches, refinement ratio r, subcycling in time).
 //
-// Each level is one padded "atlas" grid holding all of its patches (each with
-// its own ghost frame, packed on shelves), stepped with a kind mask (patch
+// Each level is one padded "atlas" grid holding all of its patches (runs of
+// patches with the same rows that abut in x share one ghost frame; the
+// regions' frames are packed on shelves), stepped with a kind mask (patch
 // interior / covered / sibling ghost / exported cell): every stage is one
 // launch over all patches of the level.
 //
-// Mixed precision (the default): the frames are three cells deep and each
-// level step is ONE launch of the one-pass kernel k_step_fused over the atlas:
-// it computes the positivity factors of the sibling ghosts next to a patch
-// edge itself (the third layer makes them equal to the sibling's own) and
-// writes the theta-weighted mass fluxes of the cells beside coarse/fine faces
-// to the level's export buffer.  FP64 (and the mixed kernel-sequence
-// schedules): two-layer frames, the seven-kernel sequence, k_amr_theta copies
-// the sibling ghosts' positivity factors and k_amr_export reads the exported
-// fluxes from the face planes.  Around the step, per level:
+// Mixed precision: the frames are three cells deep and each level step (on a
+// level whose atlas is large enough to fill the GPU) is ONE launch of the
+// one-pass kernel k_step_fused over the atlas: it computes the positivity
+// factors of the sibling ghosts next to a patch edge itself (the third layer
+// makes them equal to the sibling's own) and writes the theta-weighted mass
+// fluxes of the cells beside coarse/fine faces to the level's export buffer.
+// FP64, and mixed levels on the kernel sequence: the seven-kernel sequence
+// (two-layer frames in FP64), k_amr_theta copies the sibling ghosts'
+// positivity factors and k_amr_export reads the exported fluxes from the face
+// planes.  Around the step, per level:
 //   k_amr_fill       ghost cells from siblings (copy) and the parent (limited
 //                    interpolation in space of the surface and primitives,
-//                    linear in time), k_amr_fill_bc the boundary-condition ghosts,
+//                    linear in time; one thread per parent cell and up to four
+//                    of its ghosts), k_amr_fill_bc the boundary-condition ghosts,
 //   k_amr_avg_reflux average-down and the mass correction at coarse/fine faces
 //                    from the exported fluxes of both levels (one launch),
 //   k_amr_finalize   the level-0 step from the speeds of all levels.
