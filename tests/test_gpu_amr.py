@@ -243,6 +243,43 @@ def test_retake_of_a_level0_step_over_the_cfl_limit(M, precision):
     assert g1.status() == 0
 
 
+def test_config4_kind_hierarchy_mixed_against_fp64(M):
+    """Config 4 at a quarter of its level-0 size (256^2 at 2 km, ratio 4, three
+    levels over the fractal bathymetry and coast strip) with the patches on the
+    source (a disk of 60 km around the 2 m uplift: 14 + 197 patches of
+    16..128 cells in regions): the mixed hierarchy, every level on the one-pass
+    kernel, against the FP64 hierarchy (oracle-equal on the small cases) over
+    six level-0 steps of the same dt.  Per level over all patches: relative L2
+    of eta <= 1e-5 and of hu, hv <= 1e-3, largest eta difference <= 1e-3 of
+    the uplift; masses within 1e-6; no status flag."""
+    boxes = W.config4_boxes(256, 4, 3, centre=(0.45, 0.5), radius=30e3, width=60e3, dx0=2000.0)
+    c = W.config4(n0=256, boxes=boxes)
+
+    def hier(precision):
+        g = M.Hierarchy(c["b"], 256, 256, c["dx0"], 4, c["boxes"], model=2, bc=c["bc"], precision=precision,
+                        alpha=c["alpha"], h_star=c["h_star"], cfl=c["cfl"], dry_tol=c["dry_tol"])
+        for l, lv in enumerate(c["states"]):
+            for k, q in enumerate(lv):
+                g.set_patch(l, k, q)
+        return g
+    g64, gm = hier(0), hier(1)
+    gm.set_tuning([[0] * 7 + [2]] * 3)
+    for _ in range(6):
+        dt = g64.next_dt()
+        g64.step_dt(dt)
+        gm.step_dt(dt)
+    assert g64.status() == 0 and gm.status() == 0
+    assert gm.launches_per_step() < g64.launches_per_step()
+    for l in range(3):
+        a = np.concatenate([g64.get_patch(l, k).reshape(7, -1) for k in range(g64.npatches(l))], axis=1)
+        m = np.concatenate([gm.get_patch(l, k).reshape(7, -1) for k in range(gm.npatches(l))], axis=1)
+        err = [np.linalg.norm(m[f] - a[f]) / np.linalg.norm(a[f]) for f in range(3)]
+        assert err[0] <= 1e-5 and err[1] <= 1e-3 and err[2] <= 1e-3, (l, err)
+        assert np.abs(m[0] - a[0]).max() <= 1e-3 * 2.0, l
+    m64, mm = g64.mass()[0], gm.mass()[0]
+    assert abs(mm - m64) <= 1e-6 * m64
+
+
 def test_lake_at_rest_and_mass(M, A):
     b, qs = W.amr_small_case(2, 24, 20, 2, 3, seed=3, wetdry=False)
     rest = []
