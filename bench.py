@@ -45,8 +45,8 @@ ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
 # or code that these captures did not see reports null.
 # FP64 flops (dadd + dmul + 2 dfma thread instructions / cells), FP64 path:
 FLOPS_PER_CELL = {
-    ("hsgn", "fp64", "k_prep", "32x8"): 133.2, ("hsgn", "fp64", "k_face_x", "64x4"): 306.8,
-    ("hsgn", "fp64", "k_face_y", "16x16"): 320.1, ("hsgn", "fp64", "k_theta", "32x8"): 29.4,
+    ("hsgn", "fp64", "k_prep", "32x8"): 133.2, ("hsgn", "fp64", "k_face_x", "64x4"): 312.9,
+    ("hsgn", "fp64", "k_face_y", "16x16"): 326.3, ("hsgn", "fp64", "k_theta", "32x8"): 29.4,
     ("hsgn", "fp64", "k_update", "32x8"): 217.4,
 }
 # Issue slots per cell-update (ncu smsp__inst_executed x 32: thread instructions
