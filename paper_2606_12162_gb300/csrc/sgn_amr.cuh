@@ -185,7 +185,8 @@ __global__ void k_amr_copy(Dev<Real> c, Dev<Real> o, const int* __restrict__ dst
 // refinement flag (Sec. 6.3: the surface jump between neighbouring cells
 // exceeds tol), over the wet patch interiors of a level's atlas; neighbours
 // that are dry or not interior cells of the same patch are not compared (a dry
-// cell's eta is its bathymetry, not a free surface)
+// cell's eta is its bathymetry, not a free surface; kind bit 5 marks a cell
+// whose left neighbour in the atlas is another patch of its region)
 template <typename Real>
 __global__ void k_amr_flag(Dev<Real> d, int cur, double tol, unsigned char* __restrict__ out) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -197,9 +198,10 @@ __global__ void k_amr_flag(Dev<Real> d, int cur, double tol, unsigned char* __re
   if ((d.kind[id] & 1) && wet(id)) {
     const double c = (double)e[id];
     const size_t nb[4] = {id - 1, id + 1, id - d.pitch, id + d.pitch};
+    const bool other[4] = {(d.kind[id] & 32) != 0, (d.kind[id + 1] & 32) != 0, false, false};
 #pragma unroll
     for (int k = 0; k < 4; k++)
-      if ((d.kind[nb[k]] & 1) && wet(nb[k]) && fabs((double)e[nb[k]] - c) > tol) f = 1;
+      if (!other[k] && (d.kind[nb[k]] & 1) && wet(nb[k]) && fabs((double)e[nb[k]] - c) > tol) f = 1;
   }
   out[id] = f;
 }
@@ -880,6 +882,12 @@ class Amr : public AmrBase {
           std::fill(row, row + b.nx, (unsigned char)1);
         }
       }
+      // bit 5: the first column of a patch that follows another in its region
+      if (l > 0)
+        for (const Box& b : bx_[l])
+          for (const Box& R : rg_[l])
+            if (R.j0 == b.j0 && R.ny == b.ny && R.i0 < b.i0 && b.i0 < R.i0 + R.nx)
+              for (int j = 0; j < b.ny; j++) kd[l][dense(l, b, G, G + j)] |= 32;
       // covered: the footprint of every box of the next level, in its parent
       if (l + 1 < L)
         for (const Box& c : bx_[l + 1]) {

@@ -529,6 +529,11 @@ def test_flagged_boxes_with_remainders_match_the_oracle(M, A, seed, tol, tile, b
     for l in range(3):
         for k in range(len(g.boxes[l])):
             assert (rel_l2(g.get_patch(l, k), o.patch_state(l, k)) <= FP64_TOL).all(), (l, k)
+    # again from the tiled boxes, which abut in rows (one atlas region, one
+    # frame): the flags still compare neighbours within a patch only
+    want = o.flag_boxes(tol, tile, buffer)
+    g.regrid_flagged(b, tol, tile, buffer)
+    assert g.boxes[1] == want[0] and g.boxes[2] == want[1]
 
 
 def test_regrid_to_empty_levels_and_back(M, A):
